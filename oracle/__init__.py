@@ -1,0 +1,235 @@
+"""Plain FP64 CPU oracle for the MG-GLAM scalar-field solve (arXiv:2110.00328).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` are the only callers.  Nothing here is imported by
+the CUDA path and nothing here imports it.
+
+The arithmetic lives in ``mgoracle.c`` (loops written out from the paper, see its
+header); this module loads it with ctypes and adds the numpy-level references
+used to pin it: FFT solutions of the linearised and zero-coupling problems and a
+dense Newton solve of the full discrete system on tiny meshes.
+
+Parity status: every function is pinned by a ``-m "not gpu"`` test except the
+symmetron in sign-changing (domain-wall) regimes and CQ with the exp factor
+kept, which are "parity unpinned" (only self-consistency checks).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libmgoracle.so")
+_SRC = os.path.join(_HERE, "mgoracle.c")
+
+FR, SYMMETRON, CQ = 0, 1, 2
+KIND_NONLINEAR, KIND_NEWTON = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile mgoracle.c with gcc (OpenMP) into libmgoracle.so next to it."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                               "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("n", ctypes.c_int), ("keep_exp", ctypes.c_int),
+                ("pad0", ctypes.c_int),
+                ("fR0_abs", ctypes.c_double), ("omega_m", ctypes.c_double),
+                ("omega_l", ctypes.c_double), ("box", ctypes.c_double),
+                ("a_star", ctypes.c_double), ("xi", ctypes.c_double), ("beta_star", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("lam", ctypes.c_double),
+                ("phibar", ctypes.c_double), ("a", ctypes.c_double)]
+
+
+class CBackground(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("ctilde", "c2", "Rbar", "fRbar", "ubar", "K0", "K", "msym", "cq_src", "cq_pot")]
+
+
+@dataclass
+class Params:
+    """Model parameters in GLAM code units (box in Mpc/h)."""
+    model: int = FR
+    n: int = 1
+    fR0_abs: float = 1e-5
+    omega_m: float = 0.3
+    omega_l: float = 0.7
+    box: float = 64.0
+    a_star: float = 0.5
+    xi: float = 1e-3
+    beta_star: float = 1.0
+    alpha: float = 0.1
+    beta: float = -0.05
+    lam: float = 1.0
+    phibar: float = 1.0
+    a: float = 1.0
+    keep_exp: bool = False
+
+    def c(self) -> CParams:
+        return CParams(self.model, self.n, int(self.keep_exp), 0, self.fR0_abs, self.omega_m,
+                       self.omega_l, self.box, self.a_star, self.xi, self.beta_star, self.alpha,
+                       self.beta, self.lam, self.phibar, self.a)
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        P = ctypes.POINTER
+        d, i, ll = ctypes.c_double, ctypes.c_int, ctypes.c_longlong
+        dp = P(ctypes.c_double)
+        fp = P(ctypes.c_float)
+        _lib.or_compute_background.argtypes = [P(CParams), i, P(CBackground)]
+        _lib.or_residual.argtypes = [P(CParams), P(CBackground), i, d, dp, dp, dp, dp]
+        _lib.or_residual.restype = d
+        _lib.or_smooth.argtypes = [P(CParams), P(CBackground), i, d, dp, dp, dp, i, i]
+        _lib.or_restrict.argtypes = [i, dp, dp]
+        _lib.or_prolong.argtypes = [i, dp, dp]
+        _lib.or_prolong_correct.argtypes = [P(CParams), i, dp, dp, dp]
+        _lib.or_prolong_correct.restype = ctypes.c_long
+        _lib.or_solve.argtypes = [P(CParams), i, dp, dp, d, i, i, i, i, i, i, dp, dp,
+                                  P(ctypes.c_long)]
+        _lib.or_solve.restype = i
+        _lib.or_source_rms.argtypes = [P(CParams), i, dp]
+        _lib.or_source_rms.restype = d
+        _lib.or_deposit_cic.argtypes = [fp, ll, i, dp]
+        _lib.or_gather_force.argtypes = [P(CParams), i, dp, dp, fp, ll, d, dp]
+        _lib.or_num_threads.restype = i
+        _lib.or_local_root.argtypes = [i, i, d, d, d]
+        _lib.or_local_root.restype = d
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def background(p: Params, N: int) -> dict:
+    """Code-unit background scalars (c~, Rbar, fbar_R, ubar, ...) at p.a."""
+    b = CBackground()
+    lib().or_compute_background(ctypes.byref(p.c()), N, ctypes.byref(b))
+    return {k: getattr(b, k) for k, _ in CBackground._fields_}
+
+
+def residual(p: Params, u, rho, S=None, h: float = 1.0):
+    """Local residual d = N_h(u) - S on one periodic level (rho must have mean 1 on the fine level)."""
+    u, rho = _f64(u), _f64(rho)
+    n = u.shape[0]
+    b = CBackground()
+    cp = p.c()
+    lib().or_compute_background(ctypes.byref(cp), _fine_N(p, n, h), ctypes.byref(b))
+    d = np.empty_like(u)
+    S = _f64(S) if S is not None else None
+    lib().or_residual(ctypes.byref(cp), ctypes.byref(b), n, h, _dp(u), _dp(rho), _dp(S), _dp(d))
+    return d
+
+
+def _fine_N(p: Params, n: int, h: float) -> int:
+    # c~ is fixed by the finest mesh: N_fine = n * h
+    return int(round(n * h))
+
+
+def smooth(p: Params, u, rho, S=None, sweeps: int = 1, kind: int = KIND_NONLINEAR, h: float = 1.0):
+    """Red-black sweeps (black first) on one level; returns the relaxed field."""
+    u = _f64(u).copy()
+    rho = _f64(rho)
+    n = u.shape[0]
+    b = CBackground()
+    cp = p.c()
+    lib().or_compute_background(ctypes.byref(cp), _fine_N(p, n, h), ctypes.byref(b))
+    S = _f64(S) if S is not None else None
+    lib().or_smooth(ctypes.byref(cp), ctypes.byref(b), n, h, _dp(u), _dp(rho), _dp(S), sweeps, kind)
+    return u
+
+
+def restrict(f):
+    f = _f64(f)
+    n = f.shape[0]
+    out = np.empty((n // 2,) * 3)
+    lib().or_restrict(n, _dp(f), _dp(out))
+    return out
+
+
+def prolong(c):
+    c = _f64(c)
+    n = c.shape[0]
+    out = np.empty((2 * n,) * 3)
+    lib().or_prolong(n, _dp(c), _dp(out))
+    return out
+
+
+def prolong_correct(p: Params, uH, RuH, uh):
+    uh = _f64(uh).copy()
+    g = lib().or_prolong_correct(ctypes.byref(p.c()), _f64(uH).shape[0], _dp(_f64(uH)), _dp(_f64(RuH)), _dp(uh))
+    return uh, int(g)
+
+
+@dataclass
+class SolveResult:
+    u: np.ndarray
+    cycles: int
+    eps: float
+    hist: np.ndarray
+    guarded: int = 0
+
+
+def solve(p: Params, rho, u0=None, tol: float = 1e-10, max_cycles: int = 50, nu1: int = 2,
+          nu2: int = 2, coarse_sweeps: int = 16, kind: int = KIND_NONLINEAR, levels: int = 0) -> SolveResult:
+    """FAS V-cycles to relative residual tol (or max_cycles).  u0=None starts from the background."""
+    rho = _f64(rho)
+    N = rho.shape[0]
+    u = np.full(rho.shape, np.nan) if u0 is None else _f64(u0).copy()
+    hist = np.zeros(max_cycles + 1)
+    eps = ctypes.c_double()
+    g = ctypes.c_long()
+    cyc = lib().or_solve(ctypes.byref(p.c()), N, _dp(rho), _dp(u), tol, max_cycles, nu1, nu2,
+                         coarse_sweeps, kind, levels, _dp(hist), ctypes.byref(eps), ctypes.byref(g))
+    return SolveResult(u, cyc, eps.value, hist[: cyc + 1], g.value)
+
+
+def source_rms(p: Params, rho) -> float:
+    rho = _f64(rho)
+    return lib().or_source_rms(ctypes.byref(p.c()), rho.shape[0], _dp(rho))
+
+
+def deposit_cic(pos, N: int):
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    rho = np.empty((N, N, N))
+    lib().or_deposit_cic(pos.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), pos.shape[0], N, _dp(rho))
+    return rho
+
+
+def gather_force(p: Params, u, pos, prefactor: float = 1.0, phiN=None):
+    u = _f64(u)
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    out = np.empty((pos.shape[0], 3))
+    phiN = _f64(phiN) if phiN is not None else None
+    lib().or_gather_force(ctypes.byref(p.c()), u.shape[0], _dp(u), _dp(phiN),
+                          pos.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), pos.shape[0],
+                          prefactor, _dp(out))
+    return out
+
+
+def local_root(model: int, n: int, p: float, q: float, u_old: float = 1.0) -> float:
+    """The admissible root of the local polynomial (u^{n+2} or u^3) + p u + q = 0."""
+    return lib().or_local_root(model, n, p, q, u_old)
+
+
+def num_threads() -> int:
+    return lib().or_num_threads()

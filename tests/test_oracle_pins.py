@@ -1,0 +1,420 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test targets a plausible mistake in the oracle (a dropped term, a wrong
+sign, a wrong coefficient, a transposed index) with an independent reference:
+closed forms, the paper's manufactured solutions, FFT solutions of linear
+limits, library routines, brute force.
+"""
+import numpy as np
+import pytest
+from scipy import ndimage
+
+from paper_2110_00328_gb300 import inputs
+
+C_OVER_H0 = 2997.92458  # c / (100 km/s/Mpc) in Mpc/h
+
+
+def fr_params(orc, **kw):
+    base = dict(model=orc.FR, n=1, fR0_abs=1e-5, omega_m=0.3, omega_l=0.7, box=64.0, a=1.0)
+    base.update(kw)
+    return orc.Params(**base)
+
+
+def sym_params(orc, **kw):
+    # the homogeneous / sine tests of Sec. 4.2: a* = 0.5, xi = 1e-3, beta* = 0.1
+    base = dict(model=orc.SYMMETRON, a_star=0.5, xi=1e-3, beta_star=0.1, omega_m=0.3, box=256.0, a=1.0)
+    base.update(kw)
+    return orc.Params(**base)
+
+
+def cq_params(orc, **kw):
+    base = dict(model=orc.CQ, alpha=0.1, beta=-0.2, lam=1.0, phibar=0.5, omega_m=0.3, box=256.0, a=1.0)
+    base.update(kw)
+    return orc.Params(**base)
+
+
+def discrete_k2(N):
+    """Eigenvalues of minus the 7-point periodic Laplacian (h=1): sum 4 sin^2(k_i/2)."""
+    k = 2 * np.pi * np.fft.fftfreq(N)
+    s = 4 * np.sin(k / 2) ** 2
+    return s[:, None, None] + s[None, :, None] + s[None, None, :]
+
+
+# ---------------------------------------------------------------- background
+
+def test_background_closed_forms(orc):
+    # c~ = (N/L) c/H0 (Sec. 3.1.1); config 1: N=32, L=64 -> 1498.96
+    b = orc.background(fr_params(orc), 32)
+    assert b["ctilde"] == pytest.approx(0.5 * C_OVER_H0, rel=1e-15)
+    # R~bar(1) = 3 (Om + 4 OL) = 9.3 for Om=0.3 (Sec. 3.2.5); fbar_R(1) = -|fR0|
+    assert b["Rbar"] == pytest.approx(9.3, rel=1e-15)
+    assert b["fRbar"] == pytest.approx(-1e-5, rel=1e-15)
+    assert b["ubar"] == pytest.approx(np.sqrt(1e-5), rel=1e-15)  # u = (-f_R)^{1/(n+1)}
+    # at a = 0.5: Rbar = 3 (0.3*8 + 2.8) = 15.6, fbar_R = -|fR0| (9.3/15.6)^{n+1}
+    b = orc.background(fr_params(orc, a=0.5, n=2), 32)
+    assert b["fRbar"] == pytest.approx(-1e-5 * (9.3 / 15.6) ** 3, rel=1e-14)
+    assert b["ubar"] == pytest.approx((1e-5 * (9.3 / 15.6) ** 3) ** (1 / 3), rel=1e-14)
+    # symmetron phi_min/phi_* = sqrt(1 - (a*/a)^3), Eq. varphi_min_symm
+    b = orc.background(sym_params(orc), 256)
+    assert b["ubar"] == pytest.approx(np.sqrt(7 / 8), rel=1e-15)
+
+
+# ---------------------------------------------------------------- local roots
+
+@pytest.mark.parametrize("n", [0, 1, 2])
+def test_local_root_is_unique_positive_root(orc, n):
+    """f(R) local polynomial u^{n+2} + p u + q (q<0): the unique positive root (numpy.roots)."""
+    rng = np.random.default_rng(10 + n)
+    for _ in range(300):
+        p = rng.normal() * 10.0 ** rng.uniform(-4, 2)
+        q = -(10.0 ** rng.uniform(-8, 1))
+        r = orc.local_root(orc.FR, n, p, q, 1.0)
+        coeffs = np.zeros(n + 3)
+        coeffs[0], coeffs[-2], coeffs[-1] = 1.0, p, q
+        roots = np.roots(coeffs)
+        pos = [z.real for z in roots if abs(z.imag) < 1e-9 * max(1, abs(z)) and z.real > 0]
+        assert len(pos) == 1
+        assert r == pytest.approx(pos[0], rel=1e-9)
+        # the root satisfies the polynomial to rounding
+        assert abs(r ** (n + 2) + p * r + q) <= 1e-12 * max(r ** (n + 2), abs(p * r), abs(q))
+
+
+@pytest.mark.parametrize("n", [0, 1, 2])
+def test_local_root_p_zero(orc, n):
+    """p = 0 gives u = (-q)^{1/(n+2)} (the p->0 / Delta=0 cases of Sec. 3.2.5)."""
+    for q in (-1e-9, -0.3, -7.0):
+        assert orc.local_root(orc.FR, n, 0.0, q) == pytest.approx((-q) ** (1 / (n + 2)), rel=1e-14)
+
+
+def test_symmetron_root_sign_rule(orc):
+    """Cubic u^3 + p u + q: q<0 -> the positive root, q>0 -> its mirror (odd symmetry)."""
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        p = rng.normal() * 3
+        q = rng.normal()
+        r = orc.local_root(orc.SYMMETRON, 0, p, q, 0.5)
+        assert abs(r ** 3 + p * r + q) < 1e-12 * max(1.0, abs(p * r), abs(q))
+        assert np.sign(r) == -np.sign(q)
+        assert orc.local_root(orc.SYMMETRON, 0, p, -q, 0.5) == pytest.approx(-r, rel=1e-14)
+
+
+# ---------------------------------------------------------------- transfer operators
+
+def test_restriction_is_mean_of_children(orc):
+    rng = np.random.default_rng(0)
+    f = rng.normal(size=(8, 8, 8))
+    r = orc.restrict(f)
+    ref = f.reshape(4, 2, 4, 2, 4, 2).mean(axis=(1, 3, 5))
+    np.testing.assert_allclose(r, ref, rtol=0, atol=1e-15)
+
+
+def test_prolongation_is_cell_centred_trilinear(orc):
+    """27/9/3/1 weights = trilinear interpolation between coarse cell centres:
+    fine centre i sits at coarse index coordinate i/2 - 1/4 (scipy, periodic)."""
+    rng = np.random.default_rng(1)
+    c = rng.normal(size=(6, 6, 6))
+    fine = orc.prolong(c)
+    x = np.arange(12) / 2 - 0.25
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    ref = ndimage.map_coordinates(c, [X, Y, Z], order=1, mode="grid-wrap")
+    np.testing.assert_allclose(fine, ref, rtol=0, atol=1e-13)
+    # constants are reproduced exactly (weights sum to 64/64)
+    np.testing.assert_array_equal(orc.prolong(np.full((4, 4, 4), 3.25)), 3.25)
+
+
+def test_prolong_correct_adds_interpolated_error(orc):
+    rng = np.random.default_rng(2)
+    p = fr_params(orc)
+    uh = 1.0 + rng.random((8, 8, 8))
+    uH = rng.random((4, 4, 4))
+    RuH = rng.random((4, 4, 4))
+    out, g = orc.prolong_correct(p, uH, RuH, uh)
+    np.testing.assert_allclose(out, uh + orc.prolong(uH - RuH), atol=1e-14)
+    assert g == 0
+    # positivity reading: a non-positive result is replaced by half the old value
+    uH2 = uH.copy()
+    uH2[0, 0, 0] -= 100.0
+    out, g = orc.prolong_correct(p, uH2, RuH, uh)
+    assert g > 0
+    bad = (uh + orc.prolong(uH2 - RuH)) <= 0
+    np.testing.assert_allclose(out[bad], 0.5 * uh[bad])
+
+
+# ---------------------------------------------------------------- homogeneous density (Sec. 4.2.1)
+
+def test_homogeneous_residual_is_zero_at_background(orc):
+    N = 8
+    rho = np.ones((N,) * 3)
+    for p in (fr_params(orc, n=0), fr_params(orc, n=1), fr_params(orc, n=2, a=0.7),
+              sym_params(orc), cq_params(orc)):
+        ub = orc.background(p, N)["ubar"]
+        d = orc.residual(p, np.full((N,) * 3, ub), rho)
+        assert np.abs(d).max() < 1e-12
+
+
+@pytest.mark.parametrize("model", ["fr", "sym", "cq"])
+def test_homogeneous_random_initial_guess_relaxes_to_background(orc, model):
+    """Random initial guesses (ranges of Sec. 4.2.1) relax to the background value (Eq. field_uniform_dens_test)."""
+    N = 16
+    rho = np.ones((N,) * 3)
+    if model == "fr":
+        p = fr_params(orc, box=N * 0.5)
+        ub = orc.background(p, N)["ubar"]
+        # f_R / fbar_R uniform in [0, 2] -> u = ubar * ratio^{1/2} (n = 1); keep it positive
+        u0 = ub * np.sqrt(inputs.uniform_random_field(N, 0.01, 2.0, seed=5))
+        kind = orc.KIND_NONLINEAR
+    elif model == "sym":
+        p = sym_params(orc, box=float(N))
+        ub = orc.background(p, N)["ubar"]
+        u0 = inputs.uniform_random_field(N, 0.01, 1.0, seed=6)
+        kind = orc.KIND_NONLINEAR
+    else:
+        p = cq_params(orc, box=float(N))
+        ub = 0.0
+        u0 = inputs.uniform_random_field(N, -0.5, 0.5, seed=7)
+        kind = orc.KIND_NEWTON
+    r = orc.solve(p, rho, u0=u0, tol=0.0, max_cycles=60, kind=kind)
+    if model == "cq":
+        # Poisson-like with a tiny mass: the mean relaxes slowly; the fluctuations vanish
+        assert np.abs(r.u - r.u.mean()).max() < 1e-8
+    else:
+        np.testing.assert_allclose(r.u, ub, rtol=1e-10)
+
+
+# ---------------------------------------------------------------- 1D sine fields (Sec. 4.2.2)
+
+def _x_centres(N):
+    return np.arange(N) + 0.5
+
+
+@pytest.mark.parametrize("n", [0, 1, 2])
+def test_fr_sine_paper_density_gives_discretisation_residual(orc, n):
+    """The paper's sine density (Eq. sine_field_fR and the delta printed below it)
+    makes the discrete residual equal c^2 fbar_R A (k^2 - K_h^2) sin(kx), where
+    K_h^2 = 4 sin^2(k/2) is the 7-point Laplacian's eigenvalue (exact identity)."""
+    N, A, a = 32, 0.5, 1.0
+    p = fr_params(orc, n=n, box=64.0)
+    b = orc.background(p, N)
+    k = 2 * np.pi / N
+    s = np.sin(k * _x_centres(N))[:, None, None] * np.ones((1, N, N))
+    c2, fRb, K0 = b["c2"], b["fRbar"], b["K0"]
+    delta = (a / p.omega_m) * (c2 * fRb * k ** 2 * A * s + K0 * (1 + A * s) ** (-1 / (n + 1)) - K0)
+    u = (-fRb * (1 + A * s)) ** (1 / (n + 1))
+    d = orc.residual(p, u, 1.0 + delta)
+    expect = c2 * fRb * A * (k ** 2 - 4 * np.sin(k / 2) ** 2) * s
+    np.testing.assert_allclose(d, expect, rtol=0, atol=1e-12 * np.abs(K0))
+
+
+def test_symmetron_sine_paper_density_gives_discretisation_residual(orc):
+    """Eq. sine_field_sym with the delta printed below it."""
+    N, A, a = 32, 0.25, 1.0
+    p = sym_params(orc, box=32.0)
+    b = orc.background(p, N)
+    k = 2 * np.pi / N
+    s = np.sin(k * _x_centres(N))[:, None, None] * np.ones((1, N, N))
+    u = 0.5 + A * s
+    delta = (a ** 3 / p.a_star ** 3) * (1 - u ** 2 - (2 / a ** 2) * p.xi ** 2 * b["c2"] * A * k ** 2 * s / u) - 1
+    d = orc.residual(p, u, 1.0 + delta)
+    expect = b["c2"] * A * (k ** 2 - 4 * np.sin(k / 2) ** 2) * s
+    np.testing.assert_allclose(d, expect, rtol=0, atol=1e-9 * np.abs(expect).max())
+
+
+@pytest.mark.parametrize("n", [0, 1, 2])
+def test_fr_discrete_manufactured_solution_is_recovered(orc, n):
+    """Pick u (a smooth positive 3D field), build delta from the paper's rearranged
+    equation (Eq. fR_eom_codeunit2_CodeTestForm) with the discrete Laplacian, solve
+    from the background and recover u.  u is scaled so that mean(1/u) = 1/ubar,
+    which makes mean(delta) = 0 and the solver's mean-1 normalisation a no-op."""
+    N, a = 16, 1.0
+    p = fr_params(orc, n=n, box=32.0)
+    b = orc.background(p, N)
+    x = 2 * np.pi * _x_centres(N) / N
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    shape = 1 + 0.3 * np.sin(X) * np.cos(2 * Y) + 0.2 * np.cos(Z + 0.4)
+    u = b["ubar"] * np.mean(1 / shape) * shape
+    w = u ** (n + 1)
+    lap = sum(np.roll(w, s, ax) for ax in range(3) for s in (1, -1)) - 6 * w
+    K0 = b["K0"]
+    delta = -(a / p.omega_m) * (-b["c2"] * lap - K0 * (-b["fRbar"]) ** (1 / (n + 1)) / u + K0)
+    assert abs(delta.mean()) < 1e-12
+    r = orc.solve(p, 1 + delta, tol=1e-13, max_cycles=60)
+    assert r.eps < 1e-13
+    np.testing.assert_allclose(r.u, u, rtol=1e-10)
+
+
+# ---------------------------------------------------------------- linear regimes vs FFT
+
+def fft_solve(src_k_fn, rhs):
+    """Solve a constant-coefficient periodic linear problem given its symbol."""
+    N = rhs.shape[0]
+    K2 = discrete_k2(N)
+    sym = src_k_fn(K2)
+    sym[0, 0, 0] = 1.0
+    sol_k = np.fft.fftn(rhs) / sym
+    sol_k[0, 0, 0] = 0.0
+    return np.fft.ifftn(sol_k).real
+
+
+@pytest.mark.parametrize("n", [0, 1, 2])
+def test_fr_linear_regime_matches_yukawa_fft(orc, n):
+    """Small delta: delta w = -delta f_R solves (K_h^2 + mu^2) c^2 dw = -Om delta / a with
+    mu^2 = Rbar a^2 / (3 (n+1) c^2 (-fbar_R)) (the Yukawa / k^2/(k^2+a^2 m^2) response,
+    Sec. 2.3 and Sec. 4.2.3); the error falls like the square of the amplitude."""
+    N, a = 16, 1.0
+    p = fr_params(orc, n=n, box=64.0, a=a)
+    b = orc.background(p, N)
+    g = inputs.gaussian_field(N, seed=11, sigma=1.0)
+    mu2 = b["Rbar"] * a * a / (3 * (n + 1) * b["c2"] * (-b["fRbar"]))
+    errs = []
+    for A in (1e-3, 1e-4):
+        delta = A * g
+        rho = 1 + delta
+        r = orc.solve(p, rho, tol=1e-14, max_cycles=60)
+        dw = r.u ** (n + 1) - (-b["fRbar"])
+        lin = fft_solve(lambda K2: -(K2 + mu2) * b["c2"] * a / p.omega_m, delta)
+        errs.append(np.abs(dw - lin).max() / np.abs(lin).max())
+    assert errs[0] < 1e-2
+    # second-order: the relative error shrinks ~10x for a 10x smaller amplitude
+    assert errs[1] < 0.2 * errs[0]
+
+
+def test_cq_zero_coupling_potential_is_fft_poisson(orc):
+    """lambda = 0 (no potential): Eq. csf_eom_code is linear, grad_h^2 phi = 3 beta Om e^{beta phibar} delta / a,
+    solved exactly by FFT with the discrete Green's function -1/K_h^2."""
+    N = 16
+    p = cq_params(orc, lam=0.0, box=64.0)
+    rho = inputs.lognormal_density(N, 1.0, seed=12)
+    b = orc.background(p, N)
+    r = orc.solve(p, rho, u0=np.zeros((N,) * 3), tol=1e-14, max_cycles=80, kind=orc.KIND_NEWTON)
+    ref = fft_solve(lambda K2: -K2, b["cq_src"] * (rho - 1))
+    got = r.u - r.u.mean()
+    assert np.abs(got - ref).max() < 1e-10 * np.abs(ref).max()
+    assert b["cq_src"] == pytest.approx(3 * p.beta * p.omega_m * np.exp(p.beta * p.phibar) / p.a)
+
+
+def test_cq_linear_regime_mass_from_potential(orc):
+    """With the potential, small delta: (-K_h^2 - m^2) phi_k = src delta_k, where
+    m^2 = alpha (1+alpha) lambda^2 a^2 phibar^{-2-alpha} / c^2 is V''(phi)'s mass
+    for V = Lambda^4 / phi^alpha (Eq. csf_potential)."""
+    N = 16
+    p = cq_params(orc, box=N * C_OVER_H0, lam=1.0, phibar=0.3)   # c~ = 1: a visible mass
+    b = orc.background(p, N)
+    m2 = p.alpha * (1 + p.alpha) * p.lam ** 2 * p.a ** 2 * p.phibar ** (-2 - p.alpha) / b["c2"]
+    assert m2 > 1e-3
+    g = inputs.gaussian_field(N, seed=13, sigma=1.0)
+    A = 1e-6
+    rho = 1 + A * g
+    r = orc.solve(p, rho, u0=np.zeros((N,) * 3), tol=1e-14, max_cycles=80, kind=orc.KIND_NEWTON)
+    ref = fft_solve(lambda K2: -(K2 + m2), b["cq_src"] * A * g)
+    assert np.abs(r.u - ref).max() < 1e-4 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------- brute force
+
+def numpy_fr_residual(u, rho, c2, K0, K, omega_m, a, n):
+    """An independent vectorised restatement of Eq. fR_eom_codeunit2 (h = 1)."""
+    w = u ** (n + 1)
+    lap = sum(np.roll(w, s, ax) for ax in range(3) for s in (1, -1)) - 6 * w
+    return -c2 * lap + omega_m * (rho - 1) / a + K0 - K / u
+
+
+def dense_newton(F, u0, tol=1e-14, iters=50):
+    u = u0.copy()
+    n = u.size
+    for _ in range(iters):
+        r = F(u)
+        if np.abs(r).max() < tol:
+            break
+        J = np.empty((n, n))
+        eps = 1e-7 * np.maximum(np.abs(u.ravel()), 1e-12)
+        for j in range(n):
+            du = np.zeros(n)
+            du[j] = eps[j]
+            J[:, j] = (F(u + du.reshape(u.shape)) - F(u - du.reshape(u.shape))).ravel() / (2 * eps[j])
+        u = u - np.linalg.solve(J, r.ravel()).reshape(u.shape)
+    return u
+
+
+def test_multigrid_matches_dense_newton_8cubed(orc):
+    """8^3 = 512 unknowns: dense Newton (finite-difference Jacobian, LU) on an
+    independent numpy restatement of the operator; FAS must reach the same point."""
+    N = 8
+    p = fr_params(orc, box=16.0, fR0_abs=1e-5)
+    b = orc.background(p, N)
+    rho = inputs.lognormal_density(N, 0.8, seed=14)
+    F = lambda u: numpy_fr_residual(u, rho, b["c2"], b["K0"], b["K"], p.omega_m, p.a, 1)
+    ud = dense_newton(F, np.full((N,) * 3, b["ubar"]))
+    assert np.abs(F(ud)).max() < 1e-9
+    r = orc.solve(p, rho, tol=1e-14, max_cycles=60)
+    np.testing.assert_allclose(r.u, ud, rtol=1e-10)
+    # and the C residual agrees with the numpy restatement
+    np.testing.assert_allclose(orc.residual(p, ud, rho), F(ud), atol=1e-9)
+
+
+# ---------------------------------------------------------------- multigrid behaviour
+
+def test_vcycle_residual_contraction(orc):
+    """Textbook multigrid: the residual falls by a roughly constant factor per V-cycle (well below 1)."""
+    rho = inputs.lognormal_density(32, 1.0, seed=0)
+    r = orc.solve(fr_params(orc), rho, tol=1e-10, max_cycles=40, levels=5)
+    ratios = r.hist[1:] / r.hist[:-1]
+    assert r.eps < 1e-10
+    assert ratios.max() < 0.2
+    assert r.cycles <= 12
+
+
+# ---------------------------------------------------------------- CIC and forces
+
+def test_cic_particles_at_centres_is_a_histogram(orc):
+    """Particles exactly at cell centres deposit all their mass in that cell (NGP = histogram)."""
+    N = 8
+    rng = np.random.default_rng(4)
+    cells = rng.integers(0, N, size=(300, 3))
+    pos = (cells + 0.5).astype(np.float32)
+    rho = orc.deposit_cic(pos, N)
+    hist, _ = np.histogramdd(cells + 0.5, bins=(N, N, N), range=[(0, N)] * 3)
+    np.testing.assert_allclose(rho, hist * N ** 3 / 300, rtol=1e-14)
+
+
+def test_cic_conserves_mass_and_first_moment(orc):
+    """CIC weights sum to one and reproduce the particle position as the weighted
+    mean of the two cell centres along each axis (away from the periodic seam)."""
+    N = 8
+    rng = np.random.default_rng(5)
+    pos = rng.uniform(1.0, N - 1.0, size=(200, 3)).astype(np.float32)
+    rho = orc.deposit_cic(pos, N)
+    assert rho.sum() == pytest.approx(N ** 3, rel=1e-13)
+    for q in range(5):
+        one = orc.deposit_cic(pos[q:q + 1], N) / N ** 3
+        centres = np.arange(N) + 0.5
+        for ax in range(3):
+            marg = one.sum(axis=tuple(a for a in range(3) if a != ax))
+            assert (marg * centres).sum() == pytest.approx(float(pos[q, ax]), abs=1e-6)
+
+
+def test_cic_wraps_periodically(orc):
+    N = 4
+    rho = orc.deposit_cic(np.array([[0.25, 0.5, 3.75]], dtype=np.float32), N)
+    # x: 0.25 -> cells 3 (w 0.25) and 0 (w 0.75); y: centre of cell 0; z: 3.75 -> 3 (0.75), 0 (0.25)
+    m = N ** 3
+    assert rho[0, 0, 3] == pytest.approx(m * 0.75 * 0.75)
+    assert rho[3, 0, 0] == pytest.approx(m * 0.25 * 0.25)
+    assert rho.sum() == pytest.approx(m)
+
+
+def test_gather_force_single_mode(orc):
+    """For f_R = -u^2 carrying one Fourier mode, the three-point difference at a cell centre is
+    sin(k) times the mode's amplitude; a particle at a cell centre reads that cell's value."""
+    N = 16
+    p = fr_params(orc, box=32.0)
+    b = orc.background(p, N)
+    k = 2 * np.pi * 2 / N
+    x = _x_centres(N)
+    T = 1e-5 * (1 + 0.2 * np.cos(k * x))[:, None, None] * np.ones((1, N, N))   # T = -f_R = u^2
+    u = np.sqrt(T)
+    pos = np.array([[i + 0.5, 3.5, 7.5] for i in range(N)], dtype=np.float32)
+    F = orc.gather_force(p, u, pos, prefactor=2.0)
+    # f_R = -T; d/dx of -1e-5*0.2 cos(kx) three-point -> 1e-5*0.2*sin(k)*sin(kx); F = c^2/2 * that
+    expect = 2.0 * 0.5 * b["c2"] * 1e-5 * 0.2 * np.sin(k) * np.sin(k * x)
+    np.testing.assert_allclose(F[:, 0], expect, rtol=1e-9, atol=1e-12 * b["c2"])
+    np.testing.assert_allclose(F[:, 1:], 0.0, atol=1e-9 * np.abs(expect).max())
