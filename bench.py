@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of the MG-GLAM scalar-field hot path on GB300.
+
+One step = the whole per-time-step path on the 256^3 f(R) workload
+(Hu-Sawicki n=1, |f_R0| = 1e-6, box 256 Mpc/h, a = 1): CIC deposit of 256^3
+Zel'dovich particles (pixel sigma 1.5, seed 1 + rank), the mixed-precision FAS
+solve from the background field to relative residual 1e-8, and the fifth-force
+gather back to every particle.  Inputs are resident in HBM before timing
+starts; every step recomputes everything from the particle positions.
+
+Metric: cell updates per second (one nonlinear Gauss-Seidel relaxation of one
+cell on any multigrid level is one update), with time-to-tolerance and the
+fraction of the HBM roofline reported beside it.  With torchrun (N > 1) each
+rank solves its own independent realisation (weak scaling, no collective on
+the data path); the timings are reduced with a max over ranks.
+
+--impl reference times the FP64 CPU oracle (the test-suite reference) on the
+host cores over a bounded sample of the same workload (deposit, one V-cycle,
+gather per step).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_MESH = 256
+BOX = 256.0
+FR0 = 1e-6
+TOL = 1e-8
+SIGMA = 1.5
+WORKLOAD = "fR_HS_n1_fR0_1e-6_256cube_box256_zeldovich_sigma1.5_cic_tol1e-8"
+METRIC = "f(R) solve time-to-1e-8 residual at 256^3; Mcell-updates/s and % HBM peak"
+UNIT = "Mcell-updates/s"
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def level_sizes(N: int):
+    """Mesh sides of the multigrid levels (halve while even and the half is >= 4 and even)."""
+    ns = [N]
+    n = N
+    while n % 2 == 0 and n // 2 >= 4 and (n // 2) % 2 == 0:
+        n //= 2
+        ns.append(n)
+    return ns
+
+
+def updates_per_cycle(N: int, nu1=2, nu2=2, coarse=16) -> int:
+    ns = level_sizes(N)
+    return sum((nu1 + nu2) * n ** 3 for n in ns[:-1]) + coarse * ns[-1] ** 3
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.p = None
+        self.gpu = gpu_index
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        for row in csv.reader(io.StringIO(out)):
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1]))
+                smax.append(float(row[2]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for nm, v in zip(names, row[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(x: float, world: int, device) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_step(pos, cycles: int | None):
+    """Deposit, FAS solve (cycles=None: to tolerance; else that many V-cycles), gather."""
+    import oracle
+    rho = oracle.deposit_cic(pos, N_MESH)
+    p = oracle.Params(model=oracle.FR, n=1, fR0_abs=FR0, box=BOX)
+    r = oracle.solve(p, rho, tol=TOL if cycles is None else 0.0, max_cycles=cycles or 50)
+    oracle.gather_force(p, r.u, pos)
+    return r
+
+
+def run_oracle_baseline(pos) -> dict:
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    r = oracle_step(pos, None)
+    dt = time.perf_counter() - t0
+    ups = r.cycles * updates_per_cycle(N_MESH)
+    return {"value": ups / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one full step at 256^3 (deposit, {r.cycles} V-cycles to {r.eps:.1e}, gather) in {dt:.1f} s",
+            "seconds": dt, "time_to_tol_ms": dt * 1e3}
+
+
+def run_reference(args) -> None:
+    world, rank, _ = dist_init()
+    if rank != 0:
+        return
+    from paper_2110_00328_gb300 import inputs
+    import oracle
+    oracle.build()
+    pos = inputs.zeldovich_positions(N_MESH, seed=1, sigma=SIGMA)
+    for _ in range(args.warmup):
+        oracle_step(pos, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(pos, 1)
+    dt = time.perf_counter() - t0
+    ups = args.steps * updates_per_cycle(N_MESH)
+    value = ups / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "deposit + 1 V-cycle + gather"},
+            "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(),
+                             "sample": "per step: CIC deposit, one FAS V-cycle, gather at 256^3", "value": value,
+                             "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args) -> None:
+    import torch
+    from paper_2110_00328_gb300 import binding as mg
+    from paper_2110_00328_gb300 import build, inputs
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    build.build()
+    mg.load()
+
+    prec = mg.FP64 if args.precision == "fp64" else mg.MIXED
+    prm = mg.Params(model=mg.FR, n=1, fR0_abs=FR0, box=BOX, precision=prec, max_cycles=60,
+                    inner_cycles=args.inner_cycles)
+    pos_h = inputs.zeldovich_positions(N_MESH, seed=1 + rank, sigma=SIGMA)
+    npart = pos_h.shape[0]
+    pos = torch.from_numpy(pos_h).to(dev)
+    rho = torch.empty((N_MESH,) * 3, dtype=torch.float32, device=dev)
+    field = torch.empty((N_MESH,) * 3, dtype=torch.float64, device=dev)
+    force = torch.empty((npart, 3), dtype=torch.float32, device=dev)
+    nan1 = torch.tensor([float("nan")], dtype=torch.float64).pin_memory()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def step(stats_out):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        mg.deposit_cic(pos, N_MESH, rho)
+        ev[1].record(stream)
+        field.view(-1)[:1].copy_(nan1, non_blocking=True)  # start from the background field
+        st = mg.solve_scalar(prm, 1.0, rho, field, TOL)
+        ev[2].record(stream)
+        mg.gather_force(prm, 1.0, field, pos, 1.0, force)
+        ev[3].record(stream)
+        stats_out.append((st, ev))
+
+    warm = []
+    for _ in range(args.warmup):
+        step(warm)
+        flush.zero_()
+    torch.cuda.synchronize()
+    barrier(world)
+
+    clocks = ClockSampler(local) if rank == 0 else None
+    time.sleep(0.4 if rank == 0 else 0.0)
+    mg.profile_start()
+    n0 = mg.launch_count()
+    recs = []
+    torch.cuda.synchronize()
+    barrier(world)
+    for _ in range(args.steps):
+        step(recs)
+        torch.cuda.synchronize()
+        flush.zero_()  # L2 flush between steps, outside the step's events
+    torch.cuda.synchronize()
+    launches = mg.launch_count() - n0
+    prof = mg.profile_stop()
+    clk = clocks.stop() if clocks else None
+
+    dep = sum(e[0].elapsed_time(e[1]) for _, e in recs)
+    sol = sum(e[1].elapsed_time(e[2]) for _, e in recs)
+    gat = sum(e[2].elapsed_time(e[3]) for _, e in recs)
+    total_ms = dep + sol + gat
+    total_ms = reduce_max(total_ms, world, dev)
+    cycles = [st.cycles for st, _ in recs]
+    ups_rank = sum(c * updates_per_cycle(N_MESH) for c in cycles)
+    value = ups_rank * world / (total_ms * 1e-3) / 1e6
+
+    # end to end through the public API with host buffers (pinned), H2D + D2H inside the timing
+    pos_host = torch.from_numpy(pos_h).pin_memory()
+    force_host = torch.empty((npart, 3), dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    for it in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pos.copy_(pos_host, non_blocking=True)
+        mg.deposit_cic(pos, N_MESH, rho)
+        field.view(-1)[:1].copy_(nan1, non_blocking=True)
+        st = mg.solve_scalar(prm, 1.0, rho, field, TOL)
+        mg.gather_force(prm, 1.0, field, pos, 1.0, force)
+        force_host.copy_(force, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = reduce_max(sum(e2e_ms), world, dev)
+    e2e_value = st.cycles * updates_per_cycle(N_MESH) * len(e2e_ms) * world / (e2e_total * 1e-3) / 1e6
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = measured_peaks()
+    # dominant timed kernel class (by total time) and its algorithmic bandwidth
+    classes = {k: v for k, v in prof.items() if v["bytes"] > 0}
+    dom = max(classes, key=lambda k: classes[k]["ms"]) if classes else None
+    roof = None
+    if dom:
+        d = classes[dom]
+        avg_s = d["ms"] / d["launches"] * 1e-3
+        achieved = d["bytes"] / d["launches"] / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom,
+                "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+                "avg_launch_ms": round(d["ms"] / d["launches"], 4)}
+    timed_total = sum(v["ms"] for v in prof.values())
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                   "share_of_step": round(v["ms"] / max(total_ms, 1e-9), 4),
+                   "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["bytes"] else None}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == mg.MIXED else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N_MESH, "box_mpch": BOX, "fR0": FR0, "n": 1, "tol": TOL,
+                   "particles": npart, "precision": args.precision, "inner_cycles": args.inner_cycles,
+                   "nu1": prm.nu1, "nu2": prm.nu2, "coarse_sweeps": prm.coarse_sweeps,
+                   "levels": level_sizes(N_MESH),
+                   "l2": "512 MB written between timed steps; positions (201 MB) exceed L2",
+                   "parallelism": f"independent realisation per GPU x{world}"},
+        "time_to_tol_ms": round(sol / args.steps, 3), "deposit_ms": round(dep / args.steps, 3),
+        "gather_ms": round(gat / args.steps, 3), "cycles": cycles, "outer_steps": recs[-1][0].outer,
+        "final_resid": recs[-1][0].resid, "solved_Mcells_per_s": round(N_MESH ** 3 * args.steps * world / (sol * 1e-3) / 1e6, 1),
+        "roofline": roof, "kernels": kernels, "timed_kernel_ms": round(timed_total, 3),
+        "gpu_launches": int(launches),
+        "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(pos_host.numel() * 4),
+                "d2h_bytes_per_step": int(force_host.numel() * 4), "ms_per_step": round(e2e_total / len(e2e_ms), 3)},
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = run_oracle_baseline(pos_h)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--inner-cycles", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

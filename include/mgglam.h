@@ -1,0 +1,225 @@
+/*
+ * mgglam.h -- C ABI of the GB300 (sm_103a) MG-GLAM scalar-field library.
+ *
+ * The library solves, on a periodic N^3 particle mesh in GLAM code units
+ * (Sec. 3.1.1; cell size h = 1 on the finest level), the quasi-static scalar
+ * field equation of three modified-gravity models and provides the particle
+ * steps around it:
+ *   f(R) Hu-Sawicki, n = 0, 1, 2   Eq. fR_eom_codeunit2 (unknown u = (-f_R)^{1/(n+1)})
+ *   symmetron                      Eq. sym_eom_code_unit (unknown u = phi/phi_*)
+ *   coupled quintessence (CQ)      Eq. csf_eom_code (unknown phi~ = c~^2 delta phi)
+ * by FAS multigrid with red-black nonlinear Gauss-Seidel smoothing (Sec. 3.2.1,
+ * closed-form local roots of Secs. 3.2.4-3.2.5; Newton-Gauss-Seidel for CQ,
+ * Sec. 3.2.3), 8-child-mean restriction and 27/9/3/1 trilinear prolongation.
+ *
+ * Conventions shared by every entry point:
+ *  - Mesh arrays are contiguous, row-major [i][j][k] with k fastest
+ *    (index (i*N + j)*N + k); cell c spans [c, c+1) with its centre at c + 1/2.
+ *  - Pointers documented "device" must be CUDA device (or managed) memory on the
+ *    current device; "host" pointers are ordinary host memory.  The caller owns
+ *    every buffer it passes; the library never frees them.
+ *  - 'stream' is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued on it; calls return after enqueueing unless
+ *    documented otherwise (the solvers read the residual back to decide
+ *    convergence and therefore synchronise 'stream' at those points).
+ *  - The library keeps scratch memory (the multigrid level pyramid, reduction
+ *    partials) in a cache keyed by (device, N, precision), allocated on first
+ *    use and reused afterwards; mgglam_release() frees it.  Calls that share a
+ *    cache entry must be ordered on the GPU (same stream, or synchronised).
+ *  - Every entry point returns an mgglam_status; nothing aborts or throws.
+ *    Invalid arguments are rejected before any work is enqueued.
+ */
+#ifndef MGGLAM_H
+#define MGGLAM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MGGLAM_OK = 0,
+  MGGLAM_ERR_ARG = -1,           /* null pointer, bad model/parameter value */
+  MGGLAM_ERR_SHAPE = -2,         /* mesh size not supported (see each call) */
+  MGGLAM_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+  MGGLAM_ERR_NOT_CONVERGED = -4, /* max_cycles reached above tol (results still written) */
+  MGGLAM_ERR_NONFINITE = -5,     /* residual became NaN/Inf */
+  MGGLAM_ERR_TIMEOUT = -6,       /* a bounded device-side wait expired */
+  MGGLAM_ERR_OOM = -7            /* scratch allocation failed */
+} mgglam_status;
+
+typedef enum { MGGLAM_FR = 0, MGGLAM_SYMMETRON = 1, MGGLAM_CQ = 2 } mgglam_model;
+
+typedef enum {
+  MGGLAM_FP64 = 0, /* every level and sweep in FP64 */
+  MGGLAM_MIXED = 1 /* FP64 fine residual + defect correction around FP32 FAS cycles */
+} mgglam_precision;
+
+/* Model and solver parameters.  All physical values in GLAM code units;
+ * box in Mpc/h.  mgglam_default_params() fills the defaults noted here. */
+typedef struct {
+  int model;          /* mgglam_model */
+  int n;              /* f(R): Hu-Sawicki index 0, 1 or 2 (Eq. fR_HS) */
+  int keep_exp;       /* CQ: keep exp(beta phi~/c~^2) before (1+delta) (Sec. 3.2.3 drops it; default 0) */
+  int precision;      /* mgglam_precision (default MGGLAM_MIXED) */
+  double fR0_abs;     /* f(R): |f_R0| */
+  double omega_m;     /* matter density parameter today (default 0.3) */
+  double omega_l;     /* 1 - omega_m (default 0.7) */
+  double box;         /* box side L in Mpc/h; c~ = (N/L) c/H0 */
+  double a_star;      /* symmetron: symmetry-breaking scale factor a_* */
+  double xi;          /* symmetron: xi = H0/m_* (range * H0/c) */
+  double beta_star;   /* symmetron: coupling beta_* (forces only) */
+  double alpha;       /* CQ: potential slope alpha > 0 (Eq. csf_potential) */
+  double beta;        /* CQ: coupling beta < 0 (Eq. csf_coupling_function) */
+  double lambda;      /* CQ: lambda of Eq. csf_param_lambda (from the background solver) */
+  double phibar;      /* CQ: background field phibar(a) > 0 */
+  int levels;         /* multigrid levels; 0 = halve while the mesh stays even and >= 4 (default 0) */
+  int nu1, nu2;       /* pre-/post-smoothing red-black sweeps per level (default 2, 2) */
+  int coarse_sweeps;  /* red-black sweeps on the coarsest level (default 16) */
+  int max_cycles;     /* cap on multigrid cycles (default 50) */
+  int inner_cycles;   /* MIXED: FP32 V-cycles per FP64 defect-correction step (default 1) */
+  int check_every;    /* test convergence every k cycles (default 1) */
+  int reserved[4];
+} mgglam_params;
+
+/* Per-solve statistics.  resid values are the relative global residual:
+ * RMS of the fine-level local residual divided by the RMS of the model's
+ * linear source term (f(R): Om delta/a; symmetron: a^2/(2xi^2)(a_star/a)^3 ubar delta;
+ * CQ: 3 beta Om e^{beta phibar} delta / a), or by 1 when that is zero. */
+typedef struct {
+  int cycles;               /* multigrid cycles run (MIXED: inner FP32 V-cycles) */
+  int outer;                /* MIXED: FP64 defect-correction steps */
+  int converged;            /* 1 if resid <= tol */
+  int pad;
+  long long guarded;        /* reserved: positivity-guard replacements (not counted yet) */
+  double resid0;            /* before the first cycle */
+  double resid;             /* at return */
+  double seconds;           /* host wall time of the call */
+  double resid_hist[64];    /* resid before cycle 0, after each checked cycle (first 64) */
+} mgglam_stats;
+
+/* Library version string (static storage). */
+const char* mgglam_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char* mgglam_status_string(int status);
+
+/* Fill *prm with the defaults listed in mgglam_params.  MGGLAM_ERR_ARG if prm is NULL. */
+int mgglam_default_params(mgglam_params* prm);
+
+/*
+ * Cloud-in-cell density assignment (Sec. 3.1): each particle adds mass N^3/np
+ * shared between the 8 nearest cell centres with weights
+ * prod_d (1 - |x_d - (c_d + 1/2)|), periodic, so that the mean density is 1.
+ *   pos    device, [np][3] float32 positions in cell units; any real value is
+ *          wrapped periodically into [0, N).
+ *   np     number of particles (>= 1).
+ *   N      mesh side, 2 <= N <= 2048.
+ *   rho    device, N^3 float32 output (overwritten).
+ * Accumulation is in 64-bit fixed point (2^-32 of a particle's weight), so the
+ * result is bitwise reproducible and independent of particle order.
+ * Errors: MGGLAM_ERR_ARG (null pointer, np < 1), MGGLAM_ERR_SHAPE (N),
+ * MGGLAM_ERR_OOM, MGGLAM_ERR_CUDA.
+ */
+int mgglam_deposit_cic(const float* pos, long long np, int N, float* rho, void* stream);
+
+/*
+ * Solve the model's discrete scalar-field equation N_h(u; rho) = 0 (the
+ * fine-level local residual of Eq. residual_d set to zero) by multigrid cycles
+ * until the relative global residual (see mgglam_stats) is <= tol or
+ * prm->max_cycles cycles have run.
+ *   prm    host, model + solver parameters (prm->precision selects FP64 or MIXED).
+ *   a      scale factor (> 0).
+ *   rho    device, N^3 float32 density (any positive mean: it is rescaled to
+ *          mean 1 in FP64, Eq. code_units2's mean-1 convention).
+ *   N      mesh side; even, 4 <= N <= 2048.
+ *   field  device, N^3 float64, in/out: on input the initial guess, or if its
+ *          first element is NaN the background value (f(R), symmetron ubar; CQ 0);
+ *          on output the solution (f(R): u = (-f_R)^{1/(n+1)}; symmetron: u;
+ *          CQ: phi~).
+ *   tol    target relative residual (>= 0).
+ *   stats  host, may be NULL.
+ * Returns MGGLAM_OK when converged, MGGLAM_ERR_NOT_CONVERGED if max_cycles was
+ * reached first (field holds the last iterate), MGGLAM_ERR_NONFINITE if the
+ * residual became NaN/Inf, or an argument/CUDA/allocation error.  Synchronises
+ * 'stream' once per convergence check.
+ */
+int mgglam_solve_scalar(const mgglam_params* prm, double a, const float* rho, int N,
+                        double* field, double tol, mgglam_stats* stats, void* stream);
+
+/*
+ * Fifth force on particles (Sec. 3.1: three-point central differences at cell
+ * centres, CIC-interpolated to the particle with the deposit's weights):
+ *   f(R):      F = prefactor * (c~^2/2) grad f_R,  f_R = -u^{n+1}   (Eq. F5_fR_codeunit)
+ *   symmetron: F = prefactor * (-3 xi^2 Om beta_*^2 c~^2 a_*^-3) grad(u^2)  (Eq. F_5_codeunit)
+ *   CQ:        F = prefactor * (-beta) grad phi~   (the fifth-force part of Eq. csf_particle_geodesic_code2)
+ * prefactor is the caller's time factor (e.g. H0/adot).
+ *   field  device, N^3 float64 solution from mgglam_solve_scalar.
+ *   pos    device, [np][3] float32 positions (cell units, wrapped periodically).
+ *   force  device, [np][3] float32 output (overwritten).
+ * Errors: MGGLAM_ERR_ARG, MGGLAM_ERR_SHAPE (N even, 4..2048), MGGLAM_ERR_OOM, MGGLAM_ERR_CUDA.
+ */
+int mgglam_gather_force(const mgglam_params* prm, double a, const double* field, int N,
+                        const float* pos, long long np, float* force, double prefactor,
+                        void* stream);
+
+/* ---- single-step entry points (one multigrid operation on one level, FP64) ----
+ * These expose each step of the path for testing and for callers composing
+ * their own cycles.  'n' is the level's mesh side, 'h' its cell size (the finest
+ * level has h = 1 and c~ is fixed by the finest mesh side Nfine = n*h); 'rho'
+ * is the level's float64 density with mean 1 on the finest level; 'S' is the
+ * level's FAS source (may be NULL on the finest level, meaning S = 0).  All
+ * arrays are device float64 n^3 unless noted. */
+
+/* Red-black sweeps (black = (i+j+k) even first, then red; Sec. 3.2.1), in place on u. */
+int mgglam_smooth(const mgglam_params* prm, double a, int n, double h, double* u,
+                  const double* rho, const double* S, int sweeps, void* stream);
+
+/* Local residual d = N_h(u) - S (Eq. residual_d); d may be NULL.  *sumsq (host)
+ * receives sum d^2 (synchronises 'stream'); sumsq may be NULL. */
+int mgglam_residual(const mgglam_params* prm, double a, int n, double h, const double* u,
+                    const double* rho, const double* S, double* d, double* sumsq, void* stream);
+
+/* Restriction: coarse[(n/2)^3] = mean of the 8 children of each coarse cell (Sec. 3.2.1). */
+int mgglam_restrict(int n, const double* fine, double* coarse, void* stream);
+
+/* Coarse-grid correction, Eq. solution_correction: u_fine += P(uH - RuH) with
+ * the 27/9/3/1 (/64) prolongation; uH, RuH are (n/2)^3 for fine side n.  For
+ * f(R), a fine value that is not positive afterwards is set to half its value
+ * before the correction. */
+int mgglam_prolong_correct(const mgglam_params* prm, int n, const double* uH, const double* RuH,
+                           double* u_fine, void* stream);
+
+/* Free every cached scratch allocation on the current device. */
+int mgglam_release(void);
+
+/* ---- tracing (not part of the paper's method: measurement support) ---- */
+
+/* Accumulated CUDA-event timing of one class of kernel launches. */
+typedef struct {
+  char name[40];        /* kernel class, e.g. "smooth32_fine" */
+  long long launches;   /* timed launches */
+  double ms;            /* summed event-to-event time on the launching stream */
+  double bytes;         /* summed algorithmic bytes of those launches (the data
+                           the operation must read and write once) */
+} mgglam_kernel_profile;
+
+/* Start timing: every later fine-level kernel launch (and the deposit and
+ * gather kernels) is bracketed by a pair of CUDA events recorded on its
+ * stream; the coarse levels of a multigrid cycle are timed as one class.
+ * Clears earlier records. */
+int mgglam_profile_start(void);
+
+/* Stop timing, synchronise the device, and write up to max_entries per-class
+ * totals to out (host array); *n_entries (host) receives the number of classes
+ * that had launches.  out may be NULL to query the count.  MGGLAM_ERR_CUDA if
+ * the device synchronisation fails. */
+int mgglam_profile_stop(mgglam_kernel_profile* out, int max_entries, int* n_entries);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices, all streams), counted at enqueue time. */
+long long mgglam_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGGLAM_H */

@@ -1,0 +1,259 @@
+"""ctypes binding of libmgglam.so (declared in include/mgglam.h).
+
+Argument marshalling only: torch CUDA tensors are passed as raw device pointers
+together with the current CUDA stream; every step of the computation runs in
+the library's kernels.  There is no CPU fallback: if the library is missing or
+the tensors are not on a CUDA device, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field, fields
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmgglam.so")
+
+FR, SYMMETRON, CQ = 0, 1, 2
+FP64, MIXED = 0, 1
+
+STATUS = {0: "ok", -1: "invalid argument", -2: "unsupported mesh size", -3: "CUDA error",
+          -4: "not converged", -5: "non-finite residual", -6: "device wait timed out",
+          -7: "out of device memory"}
+
+
+class MgglamError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__(f"{fn} failed: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("n", ctypes.c_int), ("keep_exp", ctypes.c_int),
+                ("precision", ctypes.c_int),
+                ("fR0_abs", ctypes.c_double), ("omega_m", ctypes.c_double), ("omega_l", ctypes.c_double),
+                ("box", ctypes.c_double), ("a_star", ctypes.c_double), ("xi", ctypes.c_double),
+                ("beta_star", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("lam", ctypes.c_double), ("phibar", ctypes.c_double),
+                ("levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("coarse_sweeps", ctypes.c_int), ("max_cycles", ctypes.c_int),
+                ("inner_cycles", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
+
+
+class CStats(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("outer", ctypes.c_int), ("converged", ctypes.c_int),
+                ("pad", ctypes.c_int), ("guarded", ctypes.c_longlong), ("resid0", ctypes.c_double),
+                ("resid", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("resid_hist", ctypes.c_double * 64)]
+
+
+@dataclass
+class Params:
+    """Mirror of mgglam_params (defaults = mgglam_default_params)."""
+    model: int = FR
+    n: int = 1
+    keep_exp: bool = False
+    precision: int = MIXED
+    fR0_abs: float = 1e-5
+    omega_m: float = 0.3
+    omega_l: float = 0.7
+    box: float = 256.0
+    a_star: float = 0.5
+    xi: float = 100.0 / 299792.458
+    beta_star: float = 1.0
+    alpha: float = 0.1
+    beta: float = -0.05
+    lam: float = 1.0
+    phibar: float = 1.0
+    levels: int = 0
+    nu1: int = 2
+    nu2: int = 2
+    coarse_sweeps: int = 16
+    max_cycles: int = 50
+    inner_cycles: int = 1
+    check_every: int = 1
+
+    def c(self) -> CParams:
+        p = CParams()
+        for f in fields(self):
+            setattr(p, f.name, int(getattr(self, f.name)) if f.name == "keep_exp" else getattr(self, f.name))
+        return p
+
+
+@dataclass
+class Stats:
+    cycles: int
+    outer: int
+    converged: bool
+    resid0: float
+    resid: float
+    seconds: float
+    hist: list = field(default_factory=list)
+
+
+_lib = None
+EXPORTS = ["mgglam_version", "mgglam_status_string", "mgglam_default_params", "mgglam_deposit_cic",
+           "mgglam_solve_scalar", "mgglam_gather_force", "mgglam_smooth", "mgglam_residual",
+           "mgglam_restrict", "mgglam_prolong_correct", "mgglam_release", "mgglam_profile_start",
+           "mgglam_profile_stop", "mgglam_launch_count"]
+
+
+class CKernelProfile(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (no CUDA context is created by loading)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run __graft_entry__.build() (there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    P, i, d, ll, vp = ctypes.POINTER, ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_void_p
+    lib.mgglam_version.restype = ctypes.c_char_p
+    lib.mgglam_status_string.restype = ctypes.c_char_p
+    lib.mgglam_status_string.argtypes = [i]
+    lib.mgglam_default_params.argtypes = [P(CParams)]
+    lib.mgglam_deposit_cic.argtypes = [vp, ll, i, vp, vp]
+    lib.mgglam_solve_scalar.argtypes = [P(CParams), d, vp, i, vp, d, P(CStats), vp]
+    lib.mgglam_gather_force.argtypes = [P(CParams), d, vp, i, vp, ll, vp, d, vp]
+    lib.mgglam_smooth.argtypes = [P(CParams), d, i, d, vp, vp, vp, i, vp]
+    lib.mgglam_residual.argtypes = [P(CParams), d, i, d, vp, vp, vp, vp, P(ctypes.c_double), vp]
+    lib.mgglam_restrict.argtypes = [i, vp, vp, vp]
+    lib.mgglam_prolong_correct.argtypes = [P(CParams), i, vp, vp, vp, vp]
+    lib.mgglam_release.argtypes = []
+    lib.mgglam_profile_start.argtypes = []
+    lib.mgglam_profile_stop.argtypes = [P(CKernelProfile), i, P(ctypes.c_int)]
+    lib.mgglam_launch_count.restype = ll
+    lib.mgglam_launch_count.argtypes = []
+    for name in EXPORTS:
+        getattr(lib, name).restype = getattr(lib, name).restype or i
+    lib.mgglam_version.restype = ctypes.c_char_p
+    lib.mgglam_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(fn: str, rc: int, allow=(0,)):
+    if rc not in allow:
+        raise MgglamError(fn, rc)
+    return rc
+
+
+def _ptr(t, dtype=None):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor (there is no CPU path)")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def default_params() -> CParams:
+    p = CParams()
+    _check("mgglam_default_params", load().mgglam_default_params(ctypes.byref(p)))
+    return p
+
+
+def deposit_cic(pos, N: int, rho=None, stream=None):
+    """CIC density (mean 1) of particles pos [np,3] float32 (cell units) on an N^3 float32 mesh."""
+    import torch
+    if rho is None:
+        rho = torch.empty((N, N, N), dtype=torch.float32, device=pos.device)
+    _check("mgglam_deposit_cic", load().mgglam_deposit_cic(_ptr(pos, torch.float32), pos.shape[0], N,
+                                                          _ptr(rho, torch.float32), _stream(stream)))
+    return rho
+
+
+def solve_scalar(prm: Params, a: float, rho, field, tol: float, stream=None, allow_unconverged=False) -> Stats:
+    """Solve in place into field (N^3 float64; NaN first element = start from the background)."""
+    import torch
+    N = rho.shape[0]
+    st = CStats()
+    rc = load().mgglam_solve_scalar(ctypes.byref(prm.c()), a, _ptr(rho, torch.float32), N,
+                                    _ptr(field, torch.float64), tol, ctypes.byref(st), _stream(stream))
+    _check("mgglam_solve_scalar", rc, (0, -4) if allow_unconverged else (0,))
+    nh = min(64, (st.outer if prm.precision == MIXED else st.cycles) + 1)
+    return Stats(st.cycles, st.outer, bool(st.converged), st.resid0, st.resid, st.seconds,
+                 list(st.resid_hist[:nh]))
+
+
+def gather_force(prm: Params, a: float, field, pos, prefactor: float = 1.0, force=None, stream=None):
+    import torch
+    N = field.shape[0]
+    if force is None:
+        force = torch.empty((pos.shape[0], 3), dtype=torch.float32, device=pos.device)
+    _check("mgglam_gather_force", load().mgglam_gather_force(ctypes.byref(prm.c()), a, _ptr(field, torch.float64), N,
+                                                            _ptr(pos, torch.float32), pos.shape[0],
+                                                            _ptr(force, torch.float32), prefactor, _stream(stream)))
+    return force
+
+
+def smooth(prm: Params, a: float, u, rho, S=None, sweeps: int = 1, h: float = 1.0, stream=None):
+    import torch
+    _check("mgglam_smooth", load().mgglam_smooth(ctypes.byref(prm.c()), a, u.shape[0], h, _ptr(u, torch.float64),
+                                                _ptr(rho, torch.float64), _ptr(S, torch.float64), sweeps,
+                                                _stream(stream)))
+    return u
+
+
+def residual(prm: Params, a: float, u, rho, S=None, h: float = 1.0, stream=None):
+    import torch
+    d = torch.empty_like(u)
+    ss = ctypes.c_double()
+    _check("mgglam_residual", load().mgglam_residual(ctypes.byref(prm.c()), a, u.shape[0], h, _ptr(u, torch.float64),
+                                                    _ptr(rho, torch.float64), _ptr(S, torch.float64),
+                                                    _ptr(d, torch.float64), ctypes.byref(ss), _stream(stream)))
+    return d, ss.value
+
+
+def restrict(fine, stream=None):
+    import torch
+    n = fine.shape[0]
+    out = torch.empty((n // 2,) * 3, dtype=torch.float64, device=fine.device)
+    _check("mgglam_restrict", load().mgglam_restrict(n, _ptr(fine, torch.float64), _ptr(out, torch.float64),
+                                                    _stream(stream)))
+    return out
+
+
+def prolong_correct(prm: Params, uH, RuH, u_fine, stream=None):
+    import torch
+    _check("mgglam_prolong_correct", load().mgglam_prolong_correct(ctypes.byref(prm.c()), u_fine.shape[0],
+                                                                  _ptr(uH, torch.float64), _ptr(RuH, torch.float64),
+                                                                  _ptr(u_fine, torch.float64), _stream(stream)))
+    return u_fine
+
+
+def release():
+    _check("mgglam_release", load().mgglam_release())
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().mgglam_launch_count())
+
+
+def profile_start():
+    _check("mgglam_profile_start", load().mgglam_profile_start())
+
+
+def profile_stop() -> dict:
+    """Per-class {launches, ms, bytes} of the event-timed launches since profile_start()."""
+    arr = (CKernelProfile * 32)()
+    n = ctypes.c_int()
+    _check("mgglam_profile_stop", load().mgglam_profile_stop(arr, 32, ctypes.byref(n)))
+    return {arr[k].name.decode(): {"launches": arr[k].launches, "ms": arr[k].ms, "bytes": arr[k].bytes}
+            for k in range(min(n.value, 32))}

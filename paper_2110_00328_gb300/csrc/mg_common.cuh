@@ -1,0 +1,44 @@
+// mg_common.cuh -- shared device helpers: indexing, deterministic block
+// reductions, launch geometry.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mg_model.cuh"
+
+namespace mg {
+
+constexpr int kThreads = 256;
+constexpr int kMaxReduceBlocks = 2048;  // size of the partial-sum array
+
+__host__ __device__ __forceinline__ size_t cidx(int n, int i, int j, int k) {
+  return ((size_t)i * n + j) * n + k;
+}
+
+// Block-wide sum of one double per thread; result valid in thread 0.  Fixed
+// shuffle/tree order, so the result is deterministic for a fixed launch shape.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  v = 0.0;
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    v = lane < nw ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+// Grid for a grid-stride loop over 'work' items, capped so that partial sums fit.
+inline int grid_for(long long work, int threads = kThreads, int cap = kMaxReduceBlocks) {
+  long long g = (work + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+}  // namespace mg

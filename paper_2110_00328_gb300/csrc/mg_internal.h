@@ -1,0 +1,115 @@
+// mg_internal.h -- host-side interfaces between the C-ABI layer and the
+// kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/mgglam.h"
+#include "mg_model.cuh"
+
+namespace mg {
+
+constexpr int kMaxLevels = 16;
+
+// One multigrid level.  FP64 arrays serve the FP64 path (and the FP64 fine
+// level of the mixed path); FP32 arrays serve the mixed path's inner cycles.
+struct Level {
+  int n = 0;
+  double h = 1.0;
+  size_t n3 = 0;
+  // FP64 path
+  double* u = nullptr;    // solution (level 0: the caller's field)
+  double* rho = nullptr;  // density, mean 1 on level 0
+  double* S = nullptr;    // FAS source (level 0: none)
+  double* Ru = nullptr;   // restricted fine solution R u^{l-1}
+  // mixed path (FP32, correction form)
+  float* e = nullptr;     // correction e on this level (level 0: two buffers, ping-pong)
+  float* e_alt = nullptr;
+  float* ub = nullptr;    // base field the correction is added to
+  float* S32 = nullptr;   // source (level 0: tau = -r64)
+  float* Re = nullptr;    // restricted correction R e^{l-1}
+  float* rho32 = nullptr; // density, mean 1
+};
+
+struct Workspace {
+  int device = -1;
+  int N = 0;
+  int precision = 0;
+  int nlev = 0;
+  int levels_req = 0;
+  Level lev[kMaxLevels];
+  void* base = nullptr;
+  size_t bytes = 0;
+  double* partials = nullptr;   // kMaxReduceBlocks doubles
+  double* scalars = nullptr;    // device scalars, see Scalar
+  double* h_scalars = nullptr;  // pinned host mirror
+  int64_t* cic_acc = nullptr;   // fixed-point deposit accumulator (allocated on demand)
+  size_t cic_bytes = 0;
+};
+
+// Slots of Workspace::scalars.
+enum Scalar { SC_MEAN = 0, SC_SUMSQ = 1, SC_SRC = 2, SC_FLAG = 3, SC_COUNT = 8 };
+
+int count_levels(int N, int levels);
+
+// Build the device model constants for level-independent use (c~ from N_fine).
+int make_model(const mgglam_params* prm, double a, int Nfine, ModelDev* m);
+
+// Workspace cache (one per (device, N, precision, levels)).
+int get_workspace(int N, int precision, int levels, Workspace** ws);
+void release_workspaces();
+
+// ---- FP64 kernels (solve64.cu) ----
+int launch_smooth64(const ModelDev& m, int n, double h, double* u, const double* rho,
+                    const double* S, int sweeps, cudaStream_t st);
+int launch_residual64(const ModelDev& m, int n, double h, const double* u, const double* rho,
+                      const double* S, double* d, double* partials, double* out_sum,
+                      cudaStream_t st);
+int launch_restrict64(int nf, const double* fine, double* coarse, cudaStream_t st);
+int launch_prolong_correct64(const ModelDev& m, int nc, const double* uH, const double* RuH,
+                             double* uf, cudaStream_t st);
+int launch_coarse64(const ModelDev& m, int n, double h, double* u, const double* rho,
+                    const double* S, int sweeps, cudaStream_t st);
+int launch_residual_restrict64(const ModelDev& m, int nf, double hf, const double* u,
+                               const double* rho, const double* S, double* Ru, double* uH,
+                               double* Rd, cudaStream_t st);
+int launch_fas_source64(const ModelDev& m, int nc, double hc, const double* Ru,
+                        const double* rho, double* S, cudaStream_t st);
+int launch_density_mean(const float* rho32, size_t n3, double* partials, double* out_sum,
+                        cudaStream_t st);
+int launch_density_to64(const float* rho32, size_t n3, const double* sum, double* rho64,
+                        cudaStream_t st);
+int launch_src_sumsq(const ModelDev& m, const double* rho64, size_t n3, double* partials,
+                     double* out, cudaStream_t st);
+int launch_init_background(const ModelDev& m, double* field, size_t n3, cudaStream_t st);
+
+// ---- tracing (profile.cu) ----
+enum ProfClass {
+  PC_SMOOTH32_FINE = 0, PC_RESTRICT32_FINE, PC_PROLONG32_FINE, PC_OUTER_RESID, PC_APPLY_CORR,
+  PC_SMOOTH64_FINE, PC_RESTRICT64_FINE, PC_PROLONG64_FINE, PC_RESID64_FINE, PC_COARSE_LEVELS,
+  PC_DEPOSIT, PC_DEPOSIT_FINISH, PC_TRANSFORM, PC_GATHER, PC_COUNT
+};
+void note_launch(int n);
+void prof_begin(int cls, cudaStream_t st, double alg_bytes);
+void prof_end(cudaStream_t st);
+
+// ---- solvers ----
+int solve_fp64(const mgglam_params* prm, double a, const float* rho, int N, double* field,
+               double tol, mgglam_stats* stats, cudaStream_t st);
+int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, double* field,
+                double tol, mgglam_stats* stats, cudaStream_t st);
+
+// ---- particles (particles.cu) ----
+int deposit_cic(const float* pos, long long np, int N, float* rho, cudaStream_t st);
+int gather_force(const ModelDev& m, int kind, int n_fr, const mgglam_params* prm,
+                 const double* field, int N, const float* pos, long long np, float* force,
+                 double prefactor, cudaStream_t st);
+
+}  // namespace mg
+
+#define MG_CUDA_TRY(call)                                  \
+  do {                                                     \
+    cudaError_t _e = (call);                               \
+    if (_e != cudaSuccess) return MGGLAM_ERR_CUDA;         \
+  } while (0)

@@ -1,0 +1,86 @@
+"""The C-ABI library builds, loads and exports every symbol include/*.h declares.
+
+CPU only: no call here reaches a CUDA kernel.  Argument checks that return
+before any device work are exercised.
+"""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2110_00328_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?\w+\*?\s+\*?(mgglam_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.load()
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for required in ("mgglam_deposit_cic", "mgglam_solve_scalar", "mgglam_gather_force"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_version_and_status_strings(lib):
+    assert b"sm_103a" in lib.mgglam_version()
+    assert lib.mgglam_status_string(0) == b"ok"
+    assert lib.mgglam_status_string(-4) == b"not converged"
+
+
+def test_default_params_match_binding_defaults(lib):
+    p = binding.default_params()
+    q = binding.Params().c()
+    for name, _ in binding.CParams._fields_:
+        if name == "reserved":
+            continue
+        assert getattr(p, name) == pytest.approx(getattr(q, name)), name
+    assert lib.mgglam_default_params(None) == -1
+
+
+def test_argument_errors_are_reported_before_any_device_work(lib):
+    p = binding.Params().c()
+    st = binding.CStats()
+    nullp = ctypes.c_void_p(0)
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: the checks return first
+    assert lib.mgglam_solve_scalar(ctypes.byref(p), 1.0, nullp, 32, fake, 1e-8, ctypes.byref(st), None) == -1
+    assert lib.mgglam_solve_scalar(ctypes.byref(p), 1.0, fake, 33, fake, 1e-8, ctypes.byref(st), None) == -2
+    assert lib.mgglam_solve_scalar(ctypes.byref(p), 1.0, fake, 2, fake, 1e-8, ctypes.byref(st), None) == -2
+    assert lib.mgglam_solve_scalar(ctypes.byref(p), 1.0, fake, 32, fake, -1.0, ctypes.byref(st), None) == -1
+    bad = binding.Params(precision=7).c()
+    assert lib.mgglam_solve_scalar(ctypes.byref(bad), 1.0, fake, 32, fake, 1e-8, ctypes.byref(st), None) == -1
+    assert lib.mgglam_deposit_cic(nullp, 10, 32, fake, None) == -1
+    assert lib.mgglam_deposit_cic(fake, 0, 32, fake, None) == -1
+    assert lib.mgglam_deposit_cic(fake, 10, 4096, fake, None) == -2
+    assert lib.mgglam_gather_force(ctypes.byref(p), 1.0, fake, 31, fake, 10, fake, 1.0, None) == -2
+    assert lib.mgglam_gather_force(None, 1.0, fake, 32, fake, 10, fake, 1.0, None) == -1
+    assert lib.mgglam_smooth(ctypes.byref(p), 1.0, 7, 1.0, fake, fake, None, 1, None) == -2
+    assert lib.mgglam_restrict(5, fake, fake, None) == -2
+    assert lib.mgglam_prolong_correct(ctypes.byref(p), 8, nullp, fake, fake, None) == -1
+
+
+def test_binding_refuses_cpu_tensors(lib):
+    import torch
+    rho = torch.ones((8, 8, 8), dtype=torch.float32)
+    field = torch.full((8, 8, 8), float("nan"), dtype=torch.float64)
+    with pytest.raises(TypeError):
+        binding.solve_scalar(binding.Params(), 1.0, rho, field, 1e-8)

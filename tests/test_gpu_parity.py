@@ -1,0 +1,234 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C-ABI.
+
+Tolerances:
+* FP64 kernels (one sweep, residual, transfers): the closed-form roots and the
+  oracle's bracketed Newton root agree to rounding; 1e-12 relative to the
+  field scale covers the different operation order.
+* FP64 solve: same V-cycle sequence as the oracle -> field rel-L2 <= 1e-10.
+* Mixed solve: field rel-L2 <= 1e-6 vs the FP64 oracle and relative residual
+  <= 1e-8 (the targets stated for the mixed-precision path), the residual
+  recomputed by the oracle on the GPU's output.
+* CIC deposit: float32 output (relative 2e-7) of a 64-bit fixed-point sum whose
+  contributions are each rounded to 2^-32 of a particle weight (absolute
+  <= count x 2^-33 x mass, bounded by 1e-8 x mass here).
+* Force: float32 gather; rel-L2 <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+from paper_2110_00328_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_00328_gb300 import binding, build
+    build.build()
+    binding.load()
+    return binding
+
+
+def cuda64(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def cuda32(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+
+
+def relL2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+MODELS = {
+    "fr0": dict(model=0, n=0, fR0_abs=1e-5),
+    "fr1": dict(model=0, n=1, fR0_abs=1e-5),
+    "fr2": dict(model=0, n=2, fR0_abs=1e-5),
+    "sym": dict(model=1, a_star=0.5, xi=1e-3, beta_star=1.0),
+    "cq": dict(model=2, alpha=0.1, beta=-0.2, lam=1.0, phibar=0.5),
+}
+
+
+def both_params(orc, mg, key, box, **extra):
+    kw = dict(MODELS[key])
+    kw.update(extra)
+    okw = {k: v for k, v in kw.items() if k in orc.Params.__dataclass_fields__}
+    return orc.Params(box=box, **okw), mg.Params(box=box, **kw)
+
+
+def trial_field(orc, po, rho, key, seed):
+    """A field near the solution: background times a smooth positive perturbation (CQ: small)."""
+    N = rho.shape[0]
+    b = orc.background(po, N)
+    g = inputs.gaussian_field(N, seed=seed, sigma=0.3)
+    if key == "cq":
+        return 0.05 * g
+    return b["ubar"] * np.exp(0.3 * g)
+
+
+@pytest.mark.parametrize("key", list(MODELS))
+@pytest.mark.parametrize("N,h", [(16, 1.0), (12, 2.0)])
+def test_smooth_one_sweep_matches_oracle(orc, mg, key, N, h):
+    po, pg = both_params(orc, mg, key, box=N * h)
+    rho = inputs.lognormal_density(N, 1.0, seed=20)
+    u0 = trial_field(orc, po, rho, key, seed=21)
+    S = 1e-3 * inputs.gaussian_field(N, seed=22) if h > 1 else None
+    kind = orc.KIND_NEWTON if key == "cq" else orc.KIND_NONLINEAR
+    ref = orc.smooth(po, u0, rho, S=S, sweeps=1, kind=kind, h=h)
+    u = cuda64(u0)
+    mg.smooth(pg, 1.0, u, cuda64(rho), S=cuda64(S) if S is not None else None, sweeps=1, h=h)
+    got = u.cpu().numpy()
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("key", list(MODELS))
+def test_residual_matches_oracle(orc, mg, key):
+    N = 16
+    po, pg = both_params(orc, mg, key, box=32.0)
+    rho = inputs.lognormal_density(N, 1.0, seed=23)
+    u0 = trial_field(orc, po, rho, key, seed=24)
+    ref = orc.residual(po, u0, rho)
+    d, ss = mg.residual(pg, 1.0, cuda64(u0), cuda64(rho))
+    got = d.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+    assert ss == pytest.approx(float((ref ** 2).sum()), rel=1e-10)
+
+
+def test_transfers_match_oracle(orc, mg):
+    rng = np.random.default_rng(25)
+    f = rng.normal(size=(12, 12, 12))
+    np.testing.assert_allclose(mg.restrict(cuda64(f)).cpu().numpy(), orc.restrict(f), atol=1e-15)
+    po, pg = both_params(orc, mg, "fr1", box=12.0)
+    uh = 1.0 + rng.random((12, 12, 12))
+    uH, RuH = rng.random((6, 6, 6)), rng.random((6, 6, 6))
+    uH[1, 2, 3] -= 50.0  # exercise the positivity guard
+    ref, guarded = orc.prolong_correct(po, uH, RuH, uh)
+    assert guarded > 0
+    got = mg.prolong_correct(pg, cuda64(uH), cuda64(RuH), cuda64(uh)).cpu().numpy()
+    np.testing.assert_allclose(got, ref, atol=1e-14)
+
+
+def solve_pair(orc, mg, key, N, box, rho, tol, precision, levels=0, max_cycles=40):
+    po, pg = both_params(orc, mg, key, box=box, precision=precision, levels=levels, max_cycles=max_cycles)
+    rho32 = rho.astype(np.float32)
+    kind = orc.KIND_NEWTON if key == "cq" else orc.KIND_NONLINEAR
+    ref = orc.solve(po, rho32.astype(np.float64), tol=tol, max_cycles=max_cycles, levels=levels, kind=kind)
+    field = torch.full((N, N, N), float("nan"), dtype=torch.float64, device="cuda")
+    st = mg.solve_scalar(pg, 1.0, cuda32(rho32), field, tol, allow_unconverged=True)
+    return po, ref, field.cpu().numpy(), st, rho32
+
+
+def test_fp64_solve_config1_matches_oracle_cycle_by_cycle(orc, mg):
+    """f(R) n=1, |fR0|=1e-5, 32^3, box 64, 5 levels, tol 1e-10 (the small parity workload)."""
+    rho = inputs.lognormal_density(32, 1.0, seed=0)
+    po, ref, got, st, _ = solve_pair(orc, mg, "fr1", 32, 64.0, rho, 1e-10, precision=0, levels=5)
+    assert st.converged and st.cycles == ref.cycles
+    # the relative residual is a difference of O(1) terms: FP64 evaluation has an
+    # absolute floor near 1e-15 whatever the order of operations
+    np.testing.assert_allclose(st.hist, ref.hist, rtol=1e-7, atol=1e-13)
+    assert relL2(got, ref.u) <= 1e-10
+
+
+@pytest.mark.parametrize("key", ["fr0", "fr1", "fr2", "sym", "cq"])
+@pytest.mark.parametrize("N", [24, 32])
+def test_fp64_solve_matches_oracle(orc, mg, key, N):
+    rho = inputs.lognormal_density(N, 1.0, seed=30 + N)
+    box = {"sym": float(N), "cq": 64.0}.get(key, 2.0 * N)
+    po, ref, got, st, _ = solve_pair(orc, mg, key, N, box, rho, 1e-10, precision=0)
+    assert st.converged, st
+    assert relL2(got, ref.u) <= 1e-9
+
+
+@pytest.mark.parametrize("key", ["fr0", "fr1", "fr2", "sym", "cq"])
+def test_mixed_solve_matches_oracle(orc, mg, key):
+    N = 32
+    rho = inputs.lognormal_density(N, 1.0, seed=40)
+    box = {"sym": float(N), "cq": 64.0}.get(key, 64.0)
+    po, ref, got, st, rho32 = solve_pair(orc, mg, key, N, box, rho, 1e-10, precision=1)
+    assert st.converged, st
+    assert relL2(got, ref.u) <= 1e-6
+    # the oracle's own residual of the GPU solution
+    rho_n = rho32.astype(np.float64) / rho32.astype(np.float64).mean()
+    d = orc.residual(po, got, rho_n)
+    eps = np.sqrt((d ** 2).mean()) / orc.source_rms(po, rho_n)
+    assert eps <= 1e-8
+
+
+def test_mixed_solve_strong_screening_ragged_levels(orc, mg):
+    """|fR0| = 1e-6 on a 48^3 mesh (levels 48, 24, 12, 6)."""
+    N = 48
+    rho = inputs.lognormal_density(N, 1.5, seed=41)
+    po, ref, got, st, _ = solve_pair(orc, mg, "fr1", N, 48.0, rho, 1e-9, precision=1)
+    assert st.converged
+    assert relL2(got, ref.u) <= 1e-6
+
+
+def test_smallest_mesh_single_level(orc, mg):
+    """N = 4: one level, the coarse solver alone."""
+    rho = inputs.lognormal_density(4, 0.5, seed=42)
+    po, ref, got, st, _ = solve_pair(orc, mg, "fr1", 4, 8.0, rho, 1e-12, precision=0, max_cycles=60)
+    assert relL2(got, ref.u) <= 1e-9
+
+
+def test_deposit_matches_oracle_and_is_order_independent(orc, mg):
+    N = 32
+    pos = inputs.zeldovich_positions(N, seed=43, sigma=1.5)
+    ref = orc.deposit_cic(pos, N)
+    p = cuda32(pos)
+    got = mg.deposit_cic(p, N).cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=2e-7, atol=1e-8)
+    perm = torch.from_numpy(np.random.default_rng(44).permutation(pos.shape[0])).cuda()
+    got2 = mg.deposit_cic(p[perm].contiguous(), N).cpu().numpy()
+    assert np.array_equal(got, got2)
+    assert got.astype(np.float64).sum() == pytest.approx(N ** 3, rel=1e-6)
+
+
+def test_deposit_fewer_particles_than_cells_and_wrap(orc, mg):
+    N = 16
+    pos = np.random.default_rng(45).uniform(-0.3, N + 0.2, size=(1001, 3)).astype(np.float32)
+    ref = orc.deposit_cic(np.mod(pos, N).astype(np.float32), N)
+    got = mg.deposit_cic(cuda32(pos), N).cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=2e-7, atol=1e-8 * N ** 3 / 1001)
+
+
+@pytest.mark.parametrize("key", ["fr0", "fr1", "fr2", "sym", "cq"])
+def test_gather_matches_oracle(orc, mg, key):
+    N = 32
+    po, pg = both_params(orc, mg, key, box=64.0)
+    rho = inputs.lognormal_density(N, 1.0, seed=46)
+    u = trial_field(orc, po, rho, key, seed=47)
+    pos = inputs.zeldovich_positions(N, seed=48, sigma=1.0, npart_side=16)
+    ref = orc.gather_force(po, u, pos, prefactor=0.7)
+    got = mg.gather_force(pg, 1.0, cuda64(u), cuda32(pos), prefactor=0.7).cpu().numpy()
+    assert relL2(got.astype(np.float64), ref) <= 1e-5
+
+
+def test_full_size_mixed_solve_256(orc, mg):
+    """The 256^3 workload (f(R) n=1, |fR0|=1e-6, box 256, Zel'dovich particles,
+    CIC): the oracle recomputes the FP64 residual of the GPU solution over the
+    whole mesh, and the mixed and plain-FP64 GPU solutions agree."""
+    N = 256
+    pos = cuda32(inputs.zeldovich_positions(N, seed=1, sigma=1.5))
+    rho = mg.deposit_cic(pos, N)
+    pg = mg.Params(model=0, n=1, fR0_abs=1e-6, box=256.0, precision=1, max_cycles=40)
+    field = torch.full((N, N, N), float("nan"), dtype=torch.float64, device="cuda")
+    st = mg.solve_scalar(pg, 1.0, rho, field, 1e-8)
+    assert st.converged
+    rho_h = rho.cpu().numpy().astype(np.float64)
+    rho_n = rho_h / rho_h.mean()
+    po = orc.Params(model=0, n=1, fR0_abs=1e-6, box=256.0)
+    u = field.cpu().numpy()
+    d = orc.residual(po, u, rho_n)
+    eps = np.sqrt((d ** 2).mean()) / orc.source_rms(po, rho_n)
+    assert eps <= 1e-8
+    pg64 = mg.Params(model=0, n=1, fR0_abs=1e-6, box=256.0, precision=0, max_cycles=40)
+    f64 = torch.full((N, N, N), float("nan"), dtype=torch.float64, device="cuda")
+    st64 = mg.solve_scalar(pg64, 1.0, rho, f64, 1e-10)
+    assert st64.converged
+    assert relL2(u, f64.cpu().numpy()) <= 1e-6
