@@ -206,7 +206,7 @@ def run_ours(args) -> None:
 
     prec = mg.FP64 if args.precision == "fp64" else mg.MIXED
     prm = mg.Params(model=mg.FR, n=1, fR0_abs=FR0, box=BOX, precision=prec, max_cycles=60,
-                    inner_cycles=args.inner_cycles)
+                    inner_cycles=args.inner_cycles, sweep_chunk=args.chunk)
     pos_h = inputs.zeldovich_positions(N_MESH, seed=1 + rank, sigma=SIGMA)
     npart = pos_h.shape[0]
     pos = torch.from_numpy(pos_h).to(dev)
@@ -312,7 +312,7 @@ def run_ours(args) -> None:
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == mg.MIXED else "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N_MESH, "box_mpch": BOX, "fR0": FR0, "n": 1, "tol": TOL,
-                   "particles": npart, "precision": args.precision, "inner_cycles": args.inner_cycles,
+                   "particles": npart, "precision": args.precision, "inner_cycles": args.inner_cycles, "sweep_chunk": args.chunk,
                    "nu1": prm.nu1, "nu2": prm.nu2, "coarse_sweeps": prm.coarse_sweeps,
                    "levels": level_sizes(N_MESH),
                    "l2": "512 MB written between timed steps; positions (201 MB) exceed L2",
@@ -341,7 +341,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
-    ap.add_argument("--inner-cycles", type=int, default=1)
+    ap.add_argument("--inner-cycles", type=int, default=0, help="0 = adaptive")
+    ap.add_argument("--chunk", type=int, default=0, help="planes per CTA of the fused sweep (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

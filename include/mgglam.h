@@ -76,9 +76,14 @@ typedef struct {
   int nu1, nu2;       /* pre-/post-smoothing red-black sweeps per level (default 2, 2) */
   int coarse_sweeps;  /* red-black sweeps on the coarsest level (default 16) */
   int max_cycles;     /* cap on multigrid cycles (default 50) */
-  int inner_cycles;   /* MIXED: FP32 V-cycles per FP64 defect-correction step (default 1) */
-  int check_every;    /* test convergence every k cycles (default 1) */
-  int reserved[4];
+  int inner_cycles;   /* MIXED: FP32 V-cycles per FP64 defect-correction step; 0 (default) =
+                         adaptive: enough to reach tol at the observed contraction, capped
+                         where single precision stops gaining within one step */
+  int check_every;    /* FP64: test convergence every k cycles (default 1) */
+  int sweep_chunk;    /* MIXED: planes per CTA of the fused sweep kernel; 0 (default) = 16 and
+                         the fused kernel only on levels that yield enough CTAs; > 0 forces
+                         the fused kernel on every level whose tile divides the mesh */
+  int reserved[3];
 } mgglam_params;
 
 /* Per-solve statistics.  resid values are the relative global residual:

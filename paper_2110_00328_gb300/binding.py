@@ -38,7 +38,7 @@ class CParams(ctypes.Structure):
                 ("levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("coarse_sweeps", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("sweep_chunk", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class CStats(ctypes.Structure):
@@ -71,8 +71,9 @@ class Params:
     nu2: int = 2
     coarse_sweeps: int = 16
     max_cycles: int = 50
-    inner_cycles: int = 1
+    inner_cycles: int = 0
     check_every: int = 1
+    sweep_chunk: int = 0
 
     def c(self) -> CParams:
         p = CParams()

@@ -41,6 +41,8 @@ def _compile(src: str, extra: list[str]) -> str:
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+    if "-v" in extra:
+        print(r.stderr, file=sys.stderr)
     return obj
 
 

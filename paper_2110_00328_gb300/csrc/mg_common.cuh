@@ -9,7 +9,7 @@
 namespace mg {
 
 constexpr int kThreads = 256;
-constexpr int kMaxReduceBlocks = 2048;  // size of the partial-sum array
+constexpr int kMaxReduceBlocks = 8192;  // size of the partial-sum array
 
 __host__ __device__ __forceinline__ size_t cidx(int n, int i, int j, int k) {
   return ((size_t)i * n + j) * n + k;

@@ -41,11 +41,19 @@ struct Workspace {
   Level lev[kMaxLevels];
   void* base = nullptr;
   size_t bytes = 0;
+  double* src64 = nullptr;      // mixed path: FP64 u-independent source term on the fine level
   double* partials = nullptr;   // kMaxReduceBlocks doubles
   double* scalars = nullptr;    // device scalars, see Scalar
   double* h_scalars = nullptr;  // pinned host mirror
   int64_t* cic_acc = nullptr;   // fixed-point deposit accumulator (allocated on demand)
   size_t cic_bytes = 0;
+  // CUDA graph of the coarse part of a V-cycle (levels >= 1), captured on
+  // cap_stream for the parameter signature coarse_sig and replayed on the
+  // caller's stream; coarse_launches = kernels in the graph.
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t coarse_exec = nullptr;
+  unsigned long long coarse_sig = 0;
+  long long coarse_launches = 0;
 };
 
 // Slots of Workspace::scalars.
@@ -91,6 +99,7 @@ enum ProfClass {
   PC_DEPOSIT, PC_DEPOSIT_FINISH, PC_TRANSFORM, PC_GATHER, PC_COUNT
 };
 void note_launch(int n);
+long long launch_count();
 void prof_begin(int cls, cudaStream_t st, double alg_bytes);
 void prof_end(cudaStream_t st);
 

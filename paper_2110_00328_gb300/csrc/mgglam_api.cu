@@ -118,6 +118,7 @@ int get_workspace(int N, int precision, int levels, Workspace** out) {
   auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes); return o; };
   size_t o_partials = take(kMaxReduceBlocks * sizeof(double));
   size_t o_scalars = take(SC_COUNT * sizeof(double));
+  size_t o_src64 = precision == MGGLAM_MIXED ? take((size_t)N * N * N * sizeof(double)) : 0;
   struct Offs { size_t u, rho, S, Ru, e, e_alt, ub, S32, Re, rho32; } offs[kMaxLevels];
   for (int l = 0, n = N; l < w->nlev; ++l, n /= 2) {
     Level& L = w->lev[l];
@@ -136,7 +137,7 @@ int get_workspace(int N, int precision, int levels, Workspace** out) {
     }
     if (precision == MGGLAM_MIXED) {
       o.e = take(L.n3 * 4);
-      if (l == 0) o.e_alt = take(L.n3 * 4);
+      o.e_alt = take(L.n3 * 4);
       o.ub = take(L.n3 * 4);
       o.S32 = take(L.n3 * 4);
       if (l > 0) o.Re = take(L.n3 * 4);
@@ -158,6 +159,7 @@ int get_workspace(int N, int precision, int levels, Workspace** out) {
   char* b = (char*)w->base;
   w->partials = (double*)(b + o_partials);
   w->scalars = (double*)(b + o_scalars);
+  if (precision == MGGLAM_MIXED) w->src64 = (double*)(b + o_src64);
   const size_t NONE = ~(size_t)0;
   for (int l = 0; l < w->nlev; ++l) {
     Level& L = w->lev[l];
@@ -186,6 +188,8 @@ void release_workspaces() {
   for (int i = 0; i < g_nws; ++i) {
     Workspace* w = g_ws[i];
     if (w->device == dev) {
+      if (w->coarse_exec) cudaGraphExecDestroy(w->coarse_exec);
+      if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
       cudaFree(w->base);
       cudaFreeHost(w->h_scalars);
       if (w->cic_acc) cudaFree(w->cic_acc);
@@ -243,7 +247,7 @@ int mgglam_default_params(mgglam_params* p) {
   p->nu2 = 2;
   p->coarse_sweeps = 16;
   p->max_cycles = 50;
-  p->inner_cycles = 1;
+  p->inner_cycles = 0;
   p->check_every = 1;
   return MGGLAM_OK;
 }

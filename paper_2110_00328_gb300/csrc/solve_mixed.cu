@@ -6,7 +6,7 @@
 // Inner loop (FP32): FAS V-cycles (Sec. 3.2.1) for the correction e = U - u,
 // where u = float(u64) is held fixed as a base field and U is the total field.
 // Each level solves M(e) = S with M(e) = N(U) - N(u) evaluated in a form
-// without cancellation (f(R): Delta w = (u+e)^{n+1} - u^{n+1} = e * sum_j ...;
+// without cancellation (f(R): Delta w = (u+e)^{n+1} - u^{n+1} factored;
 // 1/(u+e) - 1/u = -e/(u(u+e)); symmetron: (u+e)^3 - u^3 = e(3u^2 + 3ue + e^2);
 // CQ: powers and exponentials via expm1/log1p).  On the finest level
 // S = -N(u64) (from the FP64 residual), on coarse levels the FAS source
@@ -17,11 +17,11 @@
 // N(U)_i = 0); single precision then only limits how much each outer step
 // reduces the FP64 residual.
 //
-// Local solves: f(R) and the symmetron use the closed-form root of the total
-// field's local polynomial (Secs. 3.2.4-3.2.5, stable forms in mg_model.cuh),
-// followed by one Newton step on the cancellation-free correction equation,
-// which restores full relative precision of e; CQ takes one Newton step
-// (Eq. relaxation_iteration).
+// Local solves: f(R) and the symmetron take the closed-form root of the total
+// field's local polynomial (Secs. 3.2.4-3.2.5) in fast single precision as a
+// starting point, then one Newton step on the cancellation-free correction
+// equation, which restores full relative precision of e; CQ takes one Newton
+// step (Eq. relaxation_iteration).
 #include <math.h>
 #include <string.h>
 
@@ -29,22 +29,9 @@
 
 #include "mg_common.cuh"
 #include "mg_internal.h"
+#include "sweep32.cuh"
 
 namespace mg {
-
-// FP32 constants of one level.
-struct LevelF {
-  float c2_h2;   // c~^2 / h^2
-  float al;      // f(R): h^2 / (6 c~^2); symmetron: g = c~^2 xi^2 / (h^2 a^2)
-  float K;       // f(R): Rbar a^2/3 * ubar
-  float msym;    // symmetron a^2/(2 xi^2)
-  float rat3;    // symmetron (a_star/a)^3
-  float ih2;     // 1/h^2
-  float fr_s;    // f(R): s = (al K)^{1/(n+2)}, the root's natural scale
-  float fr_is1;  // f(R): 1 / s^{n+1}
-  float cq_src, cq_pot, alpha, phibar, inv_c2, beta;
-  int keep_exp;
-};
 
 static LevelF make_levelf(const ModelDev& m, double h) {
   LevelF f;
@@ -57,6 +44,7 @@ static LevelF make_levelf(const ModelDev& m, double h) {
     const double sc = pow(al * m.K, 1.0 / (double)(np1 + 1));
     f.al = (float)al;
     f.K = (float)m.K;
+    f.alK = (float)(al * m.K);
     f.fr_s = (float)sc;
     f.fr_is1 = (float)pow(sc, -(double)np1);
   } else if (m.kind == KSYM) {
@@ -75,33 +63,8 @@ static LevelF make_levelf(const ModelDev& m, double h) {
   return f;
 }
 
-// Delta w = (u+e)^{n+1} - u^{n+1}, factored so that small e loses nothing.
-template <int K>
-__device__ __forceinline__ float dw(float u, float e) {
-  if constexpr (K == KFR0) return e;
-  else if constexpr (K == KFR1) return e * (2.f * u + e);
-  else return e * (3.f * u * u + 3.f * u * e + e * e);
-}
-
-// The neighbour sum of the correction field that enters M: f(R) sum of Delta w,
-// otherwise sum of e.
-template <int K>
-__device__ __forceinline__ float nb_sum_e(const float* __restrict__ e, const float* __restrict__ ub, int n, int i,
-                                          int j, int k) {
-  const int ip = wrapi(i + 1, n), im = wrapi(i - 1, n);
-  const int jp = wrapi(j + 1, n), jm = wrapi(j - 1, n);
-  const int kp = wrapi(k + 1, n), km = wrapi(k - 1, n);
-  const size_t c0 = cidx(n, ip, j, k), c1 = cidx(n, im, j, k), c2 = cidx(n, i, jp, k), c3 = cidx(n, i, jm, k),
-               c4 = cidx(n, i, j, kp), c5 = cidx(n, i, j, km);
-  if constexpr (is_fr(K)) {
-    return dw<K>(ub[c0], e[c0]) + dw<K>(ub[c1], e[c1]) + dw<K>(ub[c2], e[c2]) + dw<K>(ub[c3], e[c3]) +
-           dw<K>(ub[c4], e[c4]) + dw<K>(ub[c5], e[c5]);
-  } else {
-    return e[c0] + e[c1] + e[c2] + e[c3] + e[c4] + e[c5];
-  }
-}
-
-// M(e) at one cell, given the neighbour sum from nb_sum_e.
+// M(e) at one cell, given the neighbours' nbq sum (accurate operations: this
+// defines the residual and the coarse sources, not a relaxation).
 template <int K>
 __device__ __forceinline__ float local_M(const LevelF& f, float u, float e, float rho, float Lnb) {
   if constexpr (is_fr(K)) {
@@ -117,143 +80,40 @@ __device__ __forceinline__ float local_M(const LevelF& f, float u, float e, floa
   }
 }
 
-// Nonlinear Gauss-Seidel update of the correction at one cell.
+// nbq sum of the six neighbours of (i,j,k) read from global arrays.
 template <int K>
-__device__ __forceinline__ float local_update_e(const LevelF& f, float u, float e, float rho, float s, float Lnb) {
+__device__ __forceinline__ float nb_sum_g(const float* __restrict__ e, const float* __restrict__ ub, int n, int i,
+                                          int j, int k) {
+  const int ip = wrapi(i + 1, n), im = wrapi(i - 1, n);
+  const int jp = wrapi(j + 1, n), jm = wrapi(j - 1, n);
+  const int kp = wrapi(k + 1, n), km = wrapi(k - 1, n);
+  const size_t c0 = cidx(n, ip, j, k), c1 = cidx(n, im, j, k), c2 = cidx(n, i, jp, k), c3 = cidx(n, i, jm, k),
+               c4 = cidx(n, i, j, kp), c5 = cidx(n, i, j, km);
   if constexpr (is_fr(K)) {
-    // total-field polynomial U^{n+2} + p U + q = 0 with p = -u^{n+1} + al K/u - (Lnb/6 + al s), q = -al K
-    const float alK = f.al * f.K;
-    const float B = Lnb * (1.f / 6.f) + f.al * s;
-    const float p = -fr_w<K>(u) + alK / u - B;
-    // scaled: U = s y with y^{n+2} + (p/s^{n+1}) y - 1 = 0 keeps single precision in range
-    const float U = f.fr_s * fr_root<K>(p * f.fr_is1, -1.f);
-    float x = U - u;
-    // one Newton step on G(e) = Delta w(e) + al K e/(u(u+e)) - B
-    const float Ue = u + x;
-    const float G = dw<K>(u, x) + alK * x / (u * Ue) - B;
-    float dG = alK / (Ue * Ue);
-    if constexpr (K == KFR0) dG += 1.f;
-    else if constexpr (K == KFR1) dG += 2.f * Ue;
-    else dG += 3.f * Ue * Ue;
-    const float xn = x - G / dG;
-    return (u + xn > 0.f) ? xn : x;
-  } else if constexpr (K == KSYM) {
-    // total-field cubic U^3 + p U + q = 0, p = rho a*^3/a^3 - 1 + 12 g, q = -(p u + u^3 + 2 g Lnb - s/msym)
-    const float p = rho * f.rat3 - 1.f + 12.f * f.al;
-    const float B = 2.f * f.al * Lnb - s / f.msym;
-    const float q = -(p * u + u * u * u + B);
-    const float U = sym_root(p, q, u + e);
-    float x = U - u;
-    // Newton step on G(e) = p e + e(3u^2 + 3ue + e^2) - B
-    const float G = p * x + x * (3.f * u * u + 3.f * u * x + x * x) - B;
-    const float Ue = u + x;
-    const float dG = p + 3.f * Ue * Ue;
-    return dG != 0.f ? x - G / dG : x;
+    return dw<K>(ub[c0], e[c0]) + dw<K>(ub[c1], e[c1]) + dw<K>(ub[c2], e[c2]) + dw<K>(ub[c3], e[c3]) +
+           dw<K>(ub[c4], e[c4]) + dw<K>(ub[c5], e[c5]);
   } else {
-    // Newton-Gauss-Seidel step on M(e) - s
-    const float r = local_M<K>(f, u, e, rho, Lnb) - s;
-    const float x = f.phibar + (u + e) * f.inv_c2;
-    float dr = -6.f * f.ih2 - f.cq_pot * (1.f + f.alpha) * powf(x, -2.f - f.alpha) * f.inv_c2;
-    if (f.keep_exp) dr -= f.cq_src * rho * f.beta * f.inv_c2 * expf(f.beta * (u + e) * f.inv_c2);
-    return e - r / dr;
+    return e[c0] + e[c1] + e[c2] + e[c3] + e[c4] + e[c5];
   }
 }
+
+// The fused sweep kernel k_sweep32 lives in sweep32.cuh.
+
+// ---------------------------------------------------------------------------
+// Per-colour sweep for levels the fused kernel does not tile
+// ---------------------------------------------------------------------------
 
 template <int K>
-__global__ void __launch_bounds__(kThreads) k_smooth32(LevelF f, int n, float* __restrict__ e,
-                                                       const float* __restrict__ ub, const float* __restrict__ rho,
-                                                       const float* __restrict__ S, int parity) {
-  const int nh = n >> 1;
-  const long long total = (long long)n * n * nh;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int kk = (int)(t % nh);
-    const long long r = t / nh;
-    const int j = (int)(r % n), i = (int)(r / n);
-    const int k = 2 * kk + ((i + j + parity) & 1);
-    const size_t c = cidx(n, i, j, k);
-    const float Lnb = nb_sum_e<K>(e, ub, n, i, j, k);
-    e[c] = local_update_e<K>(f, ub[c], e[c], rho ? rho[c] : 1.f, S[c], Lnb);
-  }
-}
-
-// For each coarse cell: d = M(e) - S at the 8 children, averaged into Rd (stored
-// in SH); the children's e averaged into Re and eH; ub averaged into ubH.
-template <int K>
-__global__ void __launch_bounds__(kThreads) k_residual_restrict32(LevelF f, int nf, const float* __restrict__ e,
-                                                                  const float* __restrict__ ub,
-                                                                  const float* __restrict__ rho,
-                                                                  const float* __restrict__ S,
-                                                                  float* __restrict__ Re, float* __restrict__ eH,
-                                                                  float* __restrict__ ubH, float* __restrict__ SH) {
-  const int nc = nf >> 1;
-  const long long total = (long long)nc * nc * nc;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int K0 = (int)(t % nc);
-    const long long r = t / nc;
-    const int J = (int)(r % nc), I = (int)(r / nc);
-    float se = 0.f, su = 0.f, sd = 0.f;
-    for (int di = 0; di < 2; ++di)
-      for (int dj = 0; dj < 2; ++dj)
-        for (int dk = 0; dk < 2; ++dk) {
-          const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K0 + dk;
-          const size_t c = cidx(nf, i, j, k);
-          const float ec = e[c], uc = ub[c];
-          se += ec;
-          su += uc;
-          sd += local_M<K>(f, uc, ec, rho ? rho[c] : 1.f, nb_sum_e<K>(e, ub, nf, i, j, k)) - S[c];
-        }
-    Re[t] = 0.125f * se;
-    eH[t] = 0.125f * se;
-    ubH[t] = 0.125f * su;
-    SH[t] = 0.125f * sd;
-  }
-}
-
-// In place: S <- M^H(Re) - S (S holds R d on entry).
-template <int K>
-__global__ void __launch_bounds__(kThreads) k_fas_source32(LevelF f, int n, const float* __restrict__ Re,
-                                                           const float* __restrict__ ub,
-                                                           const float* __restrict__ rho, float* __restrict__ S) {
-  const long long total = (long long)n * n * n;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(t % n);
-    const long long r = t / n;
-    const int j = (int)(r % n), i = (int)(r / n);
-    S[t] = local_M<K>(f, ub[t], Re[t], rho ? rho[t] : 1.f, nb_sum_e<K>(Re, ub, n, i, j, k)) - S[t];
-  }
-}
-
-// e^h += P(e^H - R e^h); f(R): if u + e would not be positive, e <- (e_old - u)/2
-// (the total field halves, as in the FP64 path).
-template <bool FR>
-__global__ void __launch_bounds__(kThreads) k_prolong_correct32(int nc, const float* __restrict__ eH,
-                                                                const float* __restrict__ Re,
-                                                                const float* __restrict__ ub,
-                                                                float* __restrict__ ef) {
-  const int nf = nc << 1;
-  const long long total = (long long)nf * nf * nf;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(t % nf);
-    const long long r = t / nf;
-    const int j = (int)(r % nf), i = (int)(r / nf);
-    const int I = i >> 1, J = j >> 1, K = k >> 1;
-    const int I2 = wrapi(I + ((i & 1) ? 1 : -1), nc);
-    const int J2 = wrapi(J + ((j & 1) ? 1 : -1), nc);
-    const int K2 = wrapi(K + ((k & 1) ? 1 : -1), nc);
-#define EH(a, b, c) (eH[cidx(nc, a, b, c)] - Re[cidx(nc, a, b, c)])
-    const float corr = (27.f * EH(I, J, K) + 9.f * (EH(I2, J, K) + EH(I, J2, K) + EH(I, J, K2)) +
-                        3.f * (EH(I2, J2, K) + EH(I2, J, K2) + EH(I, J2, K2)) + EH(I2, J2, K2)) *
-                       (1.f / 64.f);
-#undef EH
-    const float old = ef[t];
-    float v = old + corr;
-    if (FR && !(ub[t] + v > 0.f)) v = 0.5f * (old - ub[t]);
-    ef[t] = v;
-  }
+__global__ void __launch_bounds__(64) k_smooth32(LevelF f, int n, float* __restrict__ e, const float* __restrict__ ub,
+                                                 const float* __restrict__ rho, const float* __restrict__ S,
+                                                 int parity) {
+  const int i = blockIdx.z, j = blockIdx.y;
+  const int kk = blockIdx.x * blockDim.x + threadIdx.x;
+  if (kk >= (n >> 1)) return;
+  const int k = 2 * kk + ((i + j + parity) & 1);
+  const size_t c = cidx(n, i, j, k);
+  const float Lnb = nb_sum_g<K>(e, ub, n, i, j, k);
+  e[c] = update_e_fast<K>(f, ub[c], e[c], rho ? rho[c] : 1.f, S[c], Lnb);
 }
 
 template <int K>
@@ -266,77 +126,195 @@ __global__ void __launch_bounds__(512) k_coarse32(LevelF f, int n, float* __rest
       for (int t = threadIdx.x; t < n3; t += blockDim.x) {
         const int k = t % n, j = (t / n) % n, i = t / (n * n);
         if (((i + j + k) & 1) != parity) continue;
-        const float Lnb = nb_sum_e<K>(e, ub, n, i, j, k);
-        e[t] = local_update_e<K>(f, ub[t], e[t], rho ? rho[t] : 1.f, S[t], Lnb);
+        const float Lnb = nb_sum_g<K>(e, ub, n, i, j, k);
+        e[t] = update_e_fast<K>(f, ub[t], e[t], rho ? rho[t] : 1.f, S[t], Lnb);
       }
       __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------------------
+// Transfers (3D grids: x over k, y over j, z over i)
+// ---------------------------------------------------------------------------
+
+// For each coarse cell: d = M(e) - S at the 8 children, averaged into Rd (stored
+// in SH); the children's e averaged into Re and eH; ub averaged into ubH.
+template <int K>
+__global__ void __launch_bounds__(128) k_residual_restrict32(LevelF f, int nf, const float* __restrict__ e,
+                                                             const float* __restrict__ ub,
+                                                             const float* __restrict__ rho,
+                                                             const float* __restrict__ S, float* __restrict__ Re,
+                                                             float* __restrict__ eH, float* __restrict__ ubH,
+                                                             float* __restrict__ SH) {
+  const int nc = nf >> 1;
+  const int I = blockIdx.z, J = blockIdx.y;
+  const int Kc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (Kc >= nc) return;
+  float se = 0.f, su = 0.f, sd = 0.f;
+#pragma unroll
+  for (int di = 0; di < 2; ++di)
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+      for (int dk = 0; dk < 2; ++dk) {
+        const int i = 2 * I + di, j = 2 * J + dj, k = 2 * Kc + dk;
+        const size_t c = cidx(nf, i, j, k);
+        const float ec = e[c], uc = ub[c];
+        se += ec;
+        su += uc;
+        sd += local_M<K>(f, uc, ec, rho ? rho[c] : 1.f, nb_sum_g<K>(e, ub, nf, i, j, k)) - S[c];
+      }
+  const size_t t = cidx(nc, I, J, Kc);
+  Re[t] = 0.125f * se;
+  eH[t] = 0.125f * se;
+  ubH[t] = 0.125f * su;
+  SH[t] = 0.125f * sd;
+}
+
+// In place: S <- M^H(Re) - S (S holds R d on entry).
+template <int K>
+__global__ void __launch_bounds__(128) k_fas_source32(LevelF f, int n, const float* __restrict__ Re,
+                                                      const float* __restrict__ ub, const float* __restrict__ rho,
+                                                      float* __restrict__ S) {
+  const int i = blockIdx.z, j = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const size_t t = cidx(n, i, j, k);
+  S[t] = local_M<K>(f, ub[t], Re[t], rho ? rho[t] : 1.f, nb_sum_g<K>(Re, ub, n, i, j, k)) - S[t];
+}
+
+// e^h += P(e^H - R e^h); f(R): if u + e would not be positive, e <- (e_old - u)/2
+// (the total field halves, as in the FP64 path).
+template <bool FR>
+__global__ void __launch_bounds__(128) k_prolong_correct32(int nc, const float* __restrict__ eH,
+                                                           const float* __restrict__ Re, const float* __restrict__ ub,
+                                                           float* __restrict__ ef) {
+  const int nf = nc << 1;
+  const int i = blockIdx.z, j = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nf) return;
+  const int I = i >> 1, J = j >> 1, Kc = k >> 1;
+  const int I2 = wrapi(I + ((i & 1) ? 1 : -1), nc);
+  const int J2 = wrapi(J + ((j & 1) ? 1 : -1), nc);
+  const int K2 = wrapi(Kc + ((k & 1) ? 1 : -1), nc);
+#define EH(a, b, c) (eH[cidx(nc, a, b, c)] - Re[cidx(nc, a, b, c)])
+  const float corr = (27.f * EH(I, J, Kc) + 9.f * (EH(I2, J, Kc) + EH(I, J2, Kc) + EH(I, J, K2)) +
+                      3.f * (EH(I2, J2, Kc) + EH(I2, J, K2) + EH(I, J2, K2)) + EH(I2, J2, K2)) *
+                     (1.f / 64.f);
+#undef EH
+  const size_t t = cidx(nf, i, j, k);
+  const float old = ef[t];
+  float v = old + corr;
+  if (FR && !(ub[t] + v > 0.f)) v = 0.5f * (old - ub[t]);
+  ef[t] = v;
+}
+
+__global__ void __launch_bounds__(128) k_restrict32(int nf, const float* __restrict__ fine, float* __restrict__ coarse) {
+  const int nc = nf >> 1;
+  const int I = blockIdx.z, J = blockIdx.y;
+  const int Kc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (Kc >= nc) return;
+  float s = 0.f;
+  for (int di = 0; di < 2; ++di)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int dk = 0; dk < 2; ++dk) s += fine[cidx(nf, 2 * I + di, 2 * J + dj, 2 * Kc + dk)];
+  coarse[cidx(nc, I, J, Kc)] = 0.125f * s;
+}
+
+// ---------------------------------------------------------------------------
 // FP64 outer-loop kernels (fine level)
 // ---------------------------------------------------------------------------
 
-// 1/x in FP64 by Newton-Raphson refinement of a single-precision reciprocal:
-// y1 = y0 (2 - x y0) squares the relative error of y0 (about 2^-24), giving
-// about 2^-47; a second step reaches double rounding level.  Used where the
-// residual needs K/u to ~1e-14 relative without a full-precision division.
-__device__ __forceinline__ double rcp_nr(double x) {
-  double y = (double)(1.0f / (float)x);
-  double t = fma(-x, y, 1.0);
-  y = fma(y, t, y);
-  t = fma(-x, y, 1.0);
+// 1/x in FP64 by one Newton-Raphson refinement y1 = y0 (2 - x y0) of a
+// single-precision reciprocal y0: the relative error of y0 (below 2^-22) is
+// squared, leaving about 2^-44 ~ 6e-14, far below what the residual needs.
+__device__ __forceinline__ double rcp_nr(double x, float xf) {
+  const double y = (double)__frcp_rn(xf);
+  const double t = fma(-x, y, 1.0);
   return fma(y, t, y);
 }
 
-// r = N(u64) on the fine level (rho normalised by its FP64 mean): writes
-// ub = float(u64), tau = float(-r), and per-block partial sums of r^2.
+// src64 = the part of N that does not depend on u, in FP64:
+// f(R): Om (rho/mean - 1)/a + Rbar a^2/3; symmetron: rho/mean (the density
+// itself, used in the u-dependent term); CQ: -3 beta Om e^{beta phibar}/a (rho/mean - 1).
 template <int K>
-__global__ void __launch_bounds__(kThreads) k_outer_residual(ModelDev m, int n, const double* __restrict__ u,
-                                                             const float* __restrict__ rho32,
-                                                             const double* __restrict__ rho_sum, float* __restrict__ ub,
-                                                             float* __restrict__ tau, double* __restrict__ partials) {
-  const long long total = (long long)n * n * n;
-  const double inv_mean = (double)total / *rho_sum;
-  double acc = 0.0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+__global__ void k_src64(ModelDev m, const float* __restrict__ rho32, long long n3, const double* __restrict__ rho_sum,
+                        double* __restrict__ src) {
+  const double inv_mean = (double)n3 / *rho_sum;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
        t += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(t % n);
-    const long long r = t / n;
-    const int j = (int)(r % n), i = (int)(r / n);
-    const int ip = wrapi(i + 1, n), im = wrapi(i - 1, n);
-    const int jp = wrapi(j + 1, n), jm = wrapi(j - 1, n);
-    const int kp = wrapi(k + 1, n), km = wrapi(k - 1, n);
-    const double uc = u[t];
-    const double Lnb = fr_or_id<K>(u[cidx(n, ip, j, k)]) + fr_or_id<K>(u[cidx(n, im, j, k)]) +
-                       fr_or_id<K>(u[cidx(n, i, jp, k)]) + fr_or_id<K>(u[cidx(n, i, jm, k)]) +
-                       fr_or_id<K>(u[cidx(n, i, j, kp)]) + fr_or_id<K>(u[cidx(n, i, j, km)]);
-    const double rhoc = (double)rho32[t] * inv_mean;
+    const double r = (double)rho32[t] * inv_mean;
+    if constexpr (is_fr(K)) src[t] = m.om_a * (r - 1.0) + m.K0;
+    else if constexpr (K == KSYM) src[t] = r;
+    else src[t] = r;
+  }
+}
+
+// r = N(u64) on the fine level, z-marching tiles (each cell's transformed value
+// formed once): writes ub = float(u64), tau = float(-r), and per-block partial
+// sums of r^2 (accumulated from the float tau).
+template <int K, int TJ, int TK>
+__global__ void __launch_bounds__(TJ* TK) k_outer_residual(ModelDev m, int n, int chunk, const double* __restrict__ u,
+                                                           const double* __restrict__ src, float* __restrict__ ub,
+                                                           float* __restrict__ tau, double* __restrict__ partials) {
+  constexpr int PJ = TJ + 2, PK = TK + 2, PS = PJ * PK;
+  __shared__ double s_w[3][PS];
+  const int tiles_k = n / TK;
+  const int k0 = (blockIdx.x % tiles_k) * TK;
+  const int j0 = (blockIdx.x / tiles_k) * TJ;
+  const int i0 = blockIdx.y * chunk;
+  const int i1 = min(i0 + chunk, n);
+  const int t = threadIdx.x;
+  const int tj = t / TK, tk = t - tj * TK;
+  const int jg = j0 + tj, kg = k0 + tk;
+  const int cc = (tj + 1) * PK + tk + 1;
+  float acc = 0.f;
+  auto load = [&](int p) {
+    const int ig = p < 0 ? p + n : (p >= n ? p - n : p);
+    const int slot = (p + 3) % 3;
+    const size_t base = (size_t)ig * n * n;
+    for (int c = t; c < PS; c += TJ * TK) {
+      const int jj = c / PK, kk = c - jj * PK;
+      const size_t g = base + (size_t)wrapi(j0 + jj - 1, n) * n + wrapi(k0 + kk - 1, n);
+      s_w[slot][c] = fr_or_id<K>(u[g]);
+    }
+  };
+  load(i0 - 1);
+  load(i0);
+  for (int i = i0; i < i1; ++i) {
+    load(i + 1);
+    __syncthreads();
+    const int sl = (i + 3) % 3, sm = (i + 2) % 3, sp = (i + 4) % 3;
+    const size_t g = ((size_t)i * n + jg) * n + kg;
+    const double uc = u[g];
+    const double L = s_w[sm][cc] + s_w[sp][cc] + s_w[sl][cc - PK] + s_w[sl][cc + PK] + s_w[sl][cc - 1] +
+                     s_w[sl][cc + 1];
+    const float uf = (float)uc;
     double v;
     if constexpr (is_fr(K)) {
-      v = -m.c2 * (Lnb - 6.0 * fr_w<K>(uc)) + m.om_a * (rhoc - 1.0) + m.K0 - m.K * rcp_nr(uc);
+      v = fma(-m.c2, L - 6.0 * s_w[sl][cc], src[g]) - m.K * rcp_nr(uc, uf);
     } else if constexpr (K == KSYM) {
-      v = m.c2 * (Lnb - 6.0 * uc) - m.msym * ((rhoc * m.rat3 - 1.0) * uc + uc * uc * uc);
+      v = m.c2 * (L - 6.0 * uc) - m.msym * ((src[g] * m.rat3 - 1.0) * uc + uc * uc * uc);
     } else {
       const double E = m.keep_exp ? exp(m.beta * uc / m.c2) : 1.0;
       const double x = m.phibar + uc / m.c2;
-      v = (Lnb - 6.0 * uc) - m.cq_src * (E * rhoc - 1.0) + m.cq_pot * (pow(x, -1.0 - m.alpha) - m.pot0);
+      v = (L - 6.0 * uc) - m.cq_src * (E * src[g] - 1.0) + m.cq_pot * (pow(x, -1.0 - m.alpha) - m.pot0);
     }
-    ub[t] = (float)uc;
-    tau[t] = (float)(-v);
-    acc += v * v;
+    const float tv = (float)(-v);
+    ub[g] = uf;
+    tau[g] = tv;
+    acc += tv * tv;
+    __syncthreads();
   }
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  const double a = block_sum((double)acc);
+  if (threadIdx.x == 0) partials[blockIdx.x + blockIdx.y * gridDim.x] = a;
 }
 
-// u64 += e; e <- 0 (ready for the next inner solve).
-__global__ void k_apply_correction(double* __restrict__ u, float* __restrict__ e, long long n3) {
+// u64 += e (the correction of one inner solve).
+__global__ void k_apply_correction(double* __restrict__ u, const float* __restrict__ e, long long n3) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
-       t += (long long)gridDim.x * blockDim.x) {
+       t += (long long)gridDim.x * blockDim.x)
     u[t] += (double)e[t];
-    e[t] = 0.f;
-  }
 }
 
 // rho32 normalised to mean 1 (FP64 mean), for the inner levels.
@@ -346,22 +324,6 @@ __global__ void k_density_norm32(const float* __restrict__ rho, long long n3, co
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
        t += (long long)gridDim.x * blockDim.x)
     out[t] = (float)((double)rho[t] * inv_mean);
-}
-
-__global__ void k_restrict32(int nf, const float* __restrict__ fine, float* __restrict__ coarse) {
-  const int nc = nf >> 1;
-  const long long total = (long long)nc * nc * nc;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int K = (int)(t % nc);
-    const long long r = t / nc;
-    const int J = (int)(r % nc), I = (int)(r / nc);
-    float s = 0.f;
-    for (int di = 0; di < 2; ++di)
-      for (int dj = 0; dj < 2; ++dj)
-        for (int dk = 0; dk < 2; ++dk) s += fine[cidx(nf, 2 * I + di, 2 * J + dj, 2 * K + dk)];
-    coarse[t] = 0.125f * s;
-  }
 }
 
 // Source scale from the FP32 input density (sum of squares of the linear source).
@@ -394,15 +356,18 @@ __global__ void k_finalize_sum32(const double* __restrict__ partials, int count,
 // Host driver
 // ---------------------------------------------------------------------------
 
-#define MG_DISPATCH32(kind, CALL)                                  \
-  switch (kind) {                                                  \
+#define MG_DISPATCH32(kind, CALL)                                        \
+  switch (kind) {                                                        \
     case KFR0: { constexpr int KK = KFR0; CALL; note_launch(1); } break; \
     case KFR1: { constexpr int KK = KFR1; CALL; note_launch(1); } break; \
     case KFR2: { constexpr int KK = KFR2; CALL; note_launch(1); } break; \
     case KSYM: { constexpr int KK = KSYM; CALL; note_launch(1); } break; \
     case KCQ: { constexpr int KK = KCQ; CALL; note_launch(1); } break;   \
-    default: return MGGLAM_ERR_ARG;                                \
+    default: return MGGLAM_ERR_ARG;                                      \
   }
+
+static dim3 grid3(int n_k, int n_j, int n_i, int bx) { return dim3((n_k + bx - 1) / bx, n_j, n_i); }
+static int bx_for(int n) { return n >= 128 ? 128 : (n < 32 ? 32 : n); }
 
 struct MixedCtx {
   ModelDev m;
@@ -410,16 +375,137 @@ struct MixedCtx {
   Workspace* ws;
   const mgglam_params* prm;
   bool need_rho;
+  int chunk;  // planes per CTA of the fused sweep
 };
+
+// Fused-sweep tile width along k for a level side n (0 = per-colour kernels).
+static int sweep_tile_k(int n) {
+  if (n >= 64 && n % 64 == 0) return 64;
+  if (n >= 32 && n % 32 == 0) return 32;
+  if (n >= 16 && n % 16 == 0) return 16;
+  return 0;
+}
+
+template <int K, int TK>
+static void launch_sweep_t(const MixedCtx& C, int l, const float* rho, cudaStream_t st) {
+  constexpr int TJ = 8;
+  Level& L = C.ws->lev[l];
+  const int chunk = C.chunk < L.n ? C.chunk : L.n;
+  dim3 grid((L.n / TK) * (L.n / TJ), (L.n + chunk - 1) / chunk);
+  k_sweep32<K, TJ, TK><<<grid, TJ * TK / 2, 0, st>>>(C.lf[l], L.n, chunk, L.e, L.e_alt, L.ub, rho, L.S32);
+}
+
+// The fused sweep is used on a level when its tile divides the mesh and it
+// yields enough CTAs to fill the GPU (a level with few CTAs would march its
+// planes serially); a caller-set chunk forces it wherever the tile divides.
+static bool use_fused(const MixedCtx& C, int n) {
+  const int tk = sweep_tile_k(n);
+  if (!tk || n % 8 != 0) return false;
+  if (C.prm->sweep_chunk > 0) return true;
+  const long long ctas = (long long)(n / tk) * (n / 8) * ((n + C.chunk - 1) / C.chunk);
+  return ctas >= 4 * 152;
+}
 
 static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
   Level& L = C.ws->lev[l];
   const float* rho = C.need_rho ? L.rho32 : nullptr;
-  const long long half = (long long)L.n * L.n * (L.n / 2);
-  const int g = grid_for(half, kThreads, 1 << 20);
-  for (int s = 0; s < sweeps; ++s)
-    for (int parity = 0; parity < 2; ++parity)
-      MG_DISPATCH32(C.m.kind, (k_smooth32<KK><<<g, kThreads, 0, st>>>(C.lf[l], L.n, L.e, L.ub, rho, L.S32, parity)));
+  const int tk = sweep_tile_k(L.n);
+  const bool fused = use_fused(C, L.n);
+  for (int s = 0; s < sweeps; ++s) {
+    if (fused && L.e_alt) {
+      switch (tk) {
+        case 64: MG_DISPATCH32(C.m.kind, (launch_sweep_t<KK, 64>(C, l, rho, st))); break;
+        case 32: MG_DISPATCH32(C.m.kind, (launch_sweep_t<KK, 32>(C, l, rho, st))); break;
+        default: MG_DISPATCH32(C.m.kind, (launch_sweep_t<KK, 16>(C, l, rho, st))); break;
+      }
+      float* tmp = L.e;
+      L.e = L.e_alt;
+      L.e_alt = tmp;
+    } else {
+      const dim3 g = grid3(L.n / 2, L.n, L.n, 64);
+      for (int parity = 0; parity < 2; ++parity)
+        MG_DISPATCH32(C.m.kind, (k_smooth32<KK><<<g, 64, 0, st>>>(C.lf[l], L.n, L.e, L.ub, rho, L.S32, parity)));
+    }
+  }
+  return MGGLAM_OK;
+}
+
+static int vcycle32(const MixedCtx& C, int l, cudaStream_t st);
+
+// Coarse part of a V-cycle seen from the finest level: the FAS source on level 1
+// and the cycle on levels >= 1, enqueued directly.
+static int coarse_part_direct(const MixedCtx& C, cudaStream_t st) {
+  Level& H = C.ws->lev[1];
+  const float* rhoH = C.need_rho ? H.rho32 : nullptr;
+  const int bh = bx_for(H.n);
+  MG_DISPATCH32(C.m.kind, (k_fas_source32<KK><<<grid3(H.n, H.n, H.n, bh), bh, 0, st>>>(C.lf[1], H.n, H.Re, H.ub,
+                                                                                      rhoH, H.S32)));
+  return vcycle32(C, 1, st);
+}
+
+// Signature of everything the coarse graph bakes in (kernel constants and the
+// cycle shape); buffers are fixed per workspace.
+static unsigned long long coarse_signature(const MixedCtx& C) {
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  };
+  mix(&C.m.kind, sizeof(int));
+  mix(C.lf, sizeof(LevelF) * C.ws->nlev);
+  const int shape[5] = {C.prm->nu1, C.prm->nu2, C.prm->coarse_sweeps, C.chunk, C.need_rho ? 1 : 0};
+  mix(shape, sizeof(shape));
+  const int forced = C.prm->sweep_chunk > 0;
+  mix(&forced, sizeof(int));
+  return h;
+}
+
+// The coarse part as one CUDA graph launch: the ~10 small kernels per level on
+// levels >= 1 are launch-rate bound when enqueued one by one.  The graph is
+// captured once per parameter signature on a private stream and replayed on
+// the caller's stream; if capture fails, or the cycle would not leave the
+// ping-pong buffers as it found them, the kernels are enqueued directly.
+static int coarse_part(const MixedCtx& C, cudaStream_t st) {
+  Workspace* ws = C.ws;
+  const unsigned long long sig = coarse_signature(C);
+  if (!(ws->coarse_exec && ws->coarse_sig == sig)) {
+    if (ws->coarse_exec) {
+      cudaGraphExecDestroy(ws->coarse_exec);
+      ws->coarse_exec = nullptr;
+    }
+    if (!ws->cap_stream && cudaStreamCreateWithFlags(&ws->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return coarse_part_direct(C, st);
+    }
+    float* e0[kMaxLevels];
+    float* ea0[kMaxLevels];
+    for (int l = 0; l < ws->nlev; ++l) { e0[l] = ws->lev[l].e; ea0[l] = ws->lev[l].e_alt; }
+    const long long n0 = launch_count();
+    cudaGraph_t g = nullptr;
+    int rc = MGGLAM_OK;
+    bool ok = cudaStreamBeginCapture(ws->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      rc = coarse_part_direct(C, ws->cap_stream);
+      ok = cudaStreamEndCapture(ws->cap_stream, &g) == cudaSuccess && rc == MGGLAM_OK && g != nullptr;
+    }
+    const long long captured = launch_count() - n0;
+    note_launch((int)-captured);  // nothing ran during capture
+    bool same = true;
+    for (int l = 0; l < ws->nlev; ++l) same = same && ws->lev[l].e == e0[l] && ws->lev[l].e_alt == ea0[l];
+    if (ok && same) ok = cudaGraphInstantiate(&ws->coarse_exec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    for (int l = 0; l < ws->nlev; ++l) { ws->lev[l].e = e0[l]; ws->lev[l].e_alt = ea0[l]; }
+    if (!ok || !same) {
+      if (ws->coarse_exec) cudaGraphExecDestroy(ws->coarse_exec);
+      ws->coarse_exec = nullptr;
+      return coarse_part_direct(C, st);
+    }
+    ws->coarse_sig = sig;
+    ws->coarse_launches = captured;
+  }
+  MG_CUDA_TRY(cudaGraphLaunch(ws->coarse_exec, st));
+  note_launch((int)ws->coarse_launches);
   return MGGLAM_OK;
 }
 
@@ -439,17 +525,23 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st) {
   if (l == 0) prof_end(st);
   Level& H = ws->lev[l + 1];
   const float* rhoH = C.need_rho ? H.rho32 : nullptr;
-  const int gc = grid_for((long long)H.n3, kThreads, 1 << 20);
+  const int bh = bx_for(H.n);
   if (l == 0) prof_begin(PC_RESTRICT32_FINE, st, 14.0 * L.n3);
-  MG_DISPATCH32(C.m.kind, (k_residual_restrict32<KK><<<gc, kThreads, 0, st>>>(C.lf[l], L.n, L.e, L.ub, rho, L.S32,
-                                                                               H.Re, H.e, H.ub, H.S32)));
-  if (l == 0) { prof_end(st); prof_begin(PC_COARSE_LEVELS, st, 0.0); }
-  MG_DISPATCH32(C.m.kind, (k_fas_source32<KK><<<gc, kThreads, 0, st>>>(C.lf[l + 1], H.n, H.Re, H.ub, rhoH, H.S32)));
-  if ((rc = vcycle32(C, l + 1, st))) return rc;
-  const int gf = grid_for((long long)L.n3, kThreads, 1 << 20);
+  MG_DISPATCH32(C.m.kind, (k_residual_restrict32<KK><<<grid3(H.n, H.n, H.n, bh), bh, 0, st>>>(
+                               C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32)));
+  if (l == 0) {
+    prof_end(st);
+    prof_begin(PC_COARSE_LEVELS, st, 0.0);
+    if ((rc = coarse_part(C, st))) return rc;
+  } else {
+    MG_DISPATCH32(C.m.kind, (k_fas_source32<KK><<<grid3(H.n, H.n, H.n, bh), bh, 0, st>>>(C.lf[l + 1], H.n, H.Re,
+                                                                                        H.ub, rhoH, H.S32)));
+    if ((rc = vcycle32(C, l + 1, st))) return rc;
+  }
   if (l == 0) { prof_end(st); prof_begin(PC_PROLONG32_FINE, st, 13.0 * L.n3); }
-  if (is_fr(C.m.kind)) k_prolong_correct32<true><<<gf, kThreads, 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
-  else k_prolong_correct32<false><<<gf, kThreads, 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
+  const int bf = bx_for(L.n);
+  if (is_fr(C.m.kind)) k_prolong_correct32<true><<<grid3(L.n, L.n, L.n, bf), bf, 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
+  else k_prolong_correct32<false><<<grid3(L.n, L.n, L.n, bf), bf, 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
   note_launch(1);
   if (l == 0) { prof_end(st); prof_begin(PC_SMOOTH32_FINE, st, 16.0 * L.n3 * C.prm->nu2); }
   rc = smooth32(C, l, C.prm->nu2, st);
@@ -457,14 +549,44 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st) {
   return rc;
 }
 
-static int outer_residual(const MixedCtx& C, double* field, const float* rho_in, cudaStream_t st) {
+// Tile of the FP64 outer-residual kernel.
+constexpr int kRTJ = 8, kRTK = 32;
+
+template <int K>
+static int launch_outer_residual_t(const MixedCtx& C, double* field, int* blocks, cudaStream_t st) {
   Workspace* ws = C.ws;
   Level& F = ws->lev[0];
-  const int g = grid_for((long long)F.n3);
-  prof_begin(PC_OUTER_RESID, st, 20.0 * F.n3);
-  MG_DISPATCH32(C.m.kind, (k_outer_residual<KK><<<g, kThreads, 0, st>>>(C.m, F.n, field, rho_in,
-                                                                          ws->scalars + SC_MEAN, F.ub, F.S32,
-                                                                          ws->partials)));
+  if (F.n % kRTK == 0 && F.n % kRTJ == 0) {
+    int chunk = F.n >= 64 ? 64 : F.n;
+    while ((long long)(F.n / kRTK) * (F.n / kRTJ) * ((F.n + chunk - 1) / chunk) > kMaxReduceBlocks) chunk *= 2;
+    dim3 grid((F.n / kRTK) * (F.n / kRTJ), (F.n + chunk - 1) / chunk);
+    *blocks = grid.x * grid.y;
+    if (*blocks > kMaxReduceBlocks) return MGGLAM_ERR_SHAPE;
+    k_outer_residual<K, kRTJ, kRTK><<<grid, kRTJ * kRTK, 0, st>>>(C.m, F.n, chunk, field, ws->src64, F.ub, F.S32,
+                                                                  ws->partials);
+  } else {
+    // small or non-tiling meshes: two rows of the widest dividing k-tile per CTA
+    const int tk = (F.n % 16 == 0) ? 16 : ((F.n % 8 == 0) ? 8 : ((F.n % 4 == 0) ? 4 : 2));
+    dim3 grid((F.n / tk) * (F.n / 2), 1);
+    *blocks = grid.x;
+    if (*blocks > kMaxReduceBlocks) return MGGLAM_ERR_SHAPE;
+    switch (tk) {
+      case 16: k_outer_residual<K, 2, 16><<<grid, 32, 0, st>>>(C.m, F.n, F.n, field, ws->src64, F.ub, F.S32, ws->partials); break;
+      case 8: k_outer_residual<K, 2, 8><<<grid, 16, 0, st>>>(C.m, F.n, F.n, field, ws->src64, F.ub, F.S32, ws->partials); break;
+      case 4: k_outer_residual<K, 2, 4><<<grid, 8, 0, st>>>(C.m, F.n, F.n, field, ws->src64, F.ub, F.S32, ws->partials); break;
+      default: k_outer_residual<K, 2, 2><<<grid, 4, 0, st>>>(C.m, F.n, F.n, field, ws->src64, F.ub, F.S32, ws->partials); break;
+    }
+  }
+  return MGGLAM_OK;
+}
+
+static int outer_residual(const MixedCtx& C, double* field, cudaStream_t st) {
+  Workspace* ws = C.ws;
+  Level& F = ws->lev[0];
+  prof_begin(PC_OUTER_RESID, st, 24.0 * F.n3);
+  int g = 0, rc = MGGLAM_OK;
+  MG_DISPATCH32(C.m.kind, (rc = launch_outer_residual_t<KK>(C, field, &g, st)));
+  if (rc) return rc;
   k_finalize_sum32<<<1, 1024, 0, st>>>(ws->partials, g, ws->scalars + SC_SUMSQ);
   note_launch(1);
   prof_end(st);
@@ -480,28 +602,32 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
   if ((rc = get_workspace(N, MGGLAM_MIXED, prm->levels, &C.ws))) return rc;
   C.prm = prm;
   C.need_rho = (C.m.kind == KSYM) || (C.m.kind == KCQ && C.m.keep_exp);
+  C.chunk = prm->sweep_chunk > 0 ? prm->sweep_chunk : 16;
   Workspace* ws = C.ws;
   for (int l = 0; l < ws->nlev; ++l) C.lf[l] = make_levelf(C.m, ws->lev[l].h);
   Level& F = ws->lev[0];
   const long long n3 = (long long)F.n3;
   const int g = grid_for(n3);
-  // FP64 density mean; FP32 normalised pyramid where the inner operator needs it
+  // FP64 density mean and source term; FP32 normalised pyramid where the inner operator needs it
   if ((rc = launch_density_mean(rho, F.n3, ws->partials, ws->scalars + SC_MEAN, st))) return rc;
+  MG_DISPATCH32(C.m.kind, (k_src64<KK><<<grid_for(n3, kThreads, 1 << 20), kThreads, 0, st>>>(
+                               C.m, rho, n3, ws->scalars + SC_MEAN, ws->src64)));
   if (C.need_rho) {
     k_density_norm32<<<grid_for(n3, kThreads, 1 << 20), kThreads, 0, st>>>(rho, n3, ws->scalars + SC_MEAN, F.rho32);
     note_launch(1);
-    for (int l = 1; l < ws->nlev; ++l)
-      k_restrict32<<<grid_for((long long)ws->lev[l].n3, kThreads, 1 << 20), kThreads, 0, st>>>(
+    for (int l = 1; l < ws->nlev; ++l) {
+      const int b = bx_for(ws->lev[l].n);
+      k_restrict32<<<grid3(ws->lev[l].n, ws->lev[l].n, ws->lev[l].n, b), b, 0, st>>>(
           ws->lev[l - 1].n, ws->lev[l - 1].rho32, ws->lev[l].rho32);
-    note_launch(ws->nlev - 1);
+      note_launch(1);
+    }
   }
   if ((rc = launch_init_background(C.m, field, F.n3, st))) return rc;
   MG_DISPATCH32(C.m.kind, (k_src_sumsq32<KK><<<g, kThreads, 0, st>>>(C.m, rho, n3, ws->scalars + SC_MEAN,
                                                                       ws->partials)));
   k_finalize_sum32<<<1, 1024, 0, st>>>(ws->partials, g, ws->scalars + SC_SRC);
   note_launch(1);
-  MG_CUDA_TRY(cudaMemsetAsync(F.e, 0, F.n3 * sizeof(float), st));
-  if ((rc = outer_residual(C, field, rho, st))) return rc;
+  if ((rc = outer_residual(C, field, st))) return rc;
   MG_CUDA_TRY(cudaMemcpyAsync(ws->h_scalars, ws->scalars, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
   MG_CUDA_TRY(cudaStreamSynchronize(st));
   MG_CUDA_TRY(cudaGetLastError());
@@ -514,24 +640,44 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
   S->resid0 = eps;
   S->resid_hist[0] = eps;
   int cyc = 0, outer = 0, nh = 1;
-  const int inner = prm->inner_cycles > 0 ? prm->inner_cycles : 1;
+  // Inner cycles per outer step: fixed (prm->inner_cycles > 0), or adaptive:
+  // enough cycles to reach tol at the contraction rho observed so far, but no
+  // more than single precision can use in one step (a correction is accurate to
+  // ~1e-6 of itself, so rho^k below 1e-6 gains nothing before the next FP64
+  // residual).
+  double rho_est = 0.1;
   int status = MGGLAM_OK;
   while (!(eps <= tol) && cyc < prm->max_cycles) {
     if (!isfinite(eps)) { status = MGGLAM_ERR_NONFINITE; break; }
-    for (int c = 0; c < inner && cyc < prm->max_cycles; ++c, ++cyc)
+    int inner = prm->inner_cycles;
+    if (inner <= 0) {
+      const double lr = log(rho_est);
+      const int need = (int)ceil(log(fmax(tol, 1e-300) / eps) / lr - 1e-9);
+      const int cap = (int)ceil(log(1e-6) / lr);
+      inner = need < 1 ? 1 : (need > cap ? cap : need);
+    }
+    const double eps_before = eps;
+    int done = 0;
+    MG_CUDA_TRY(cudaMemsetAsync(F.e, 0, F.n3 * sizeof(float), st));
+    for (int c = 0; c < inner && cyc < prm->max_cycles; ++c, ++cyc, ++done)
       if ((rc = vcycle32(C, 0, st))) return rc;
-    prof_begin(PC_APPLY_CORR, st, 24.0 * n3);
+    prof_begin(PC_APPLY_CORR, st, 20.0 * n3);
     k_apply_correction<<<grid_for(n3, kThreads, 1 << 20), kThreads, 0, st>>>(field, F.e, n3);
     note_launch(1);
     prof_end(st);
     ++outer;
-    if ((rc = outer_residual(C, field, rho, st))) return rc;
+    if ((rc = outer_residual(C, field, st))) return rc;
     MG_CUDA_TRY(cudaMemcpyAsync(ws->h_scalars + SC_SUMSQ, ws->scalars + SC_SUMSQ, sizeof(double),
                                 cudaMemcpyDeviceToHost, st));
     MG_CUDA_TRY(cudaStreamSynchronize(st));
     MG_CUDA_TRY(cudaGetLastError());
     eps = sqrt(ws->h_scalars[SC_SUMSQ] / (double)n3) / snorm;
     if (nh < 64) S->resid_hist[nh++] = eps;
+    if (done > 0 && eps > 0.0 && eps < eps_before) {
+      // per-cycle contraction of this step, when it was not limited by single precision
+      const double r = pow(eps / eps_before, 1.0 / done);
+      if (eps / eps_before > 1e-5) rho_est = fmin(0.5, fmax(0.01, r));
+    }
   }
   if (status == MGGLAM_OK && !isfinite(eps)) status = MGGLAM_ERR_NONFINITE;
   S->cycles = cyc;

@@ -1,0 +1,346 @@
+// sweep32.cuh -- the FP32 correction-form nonlinear Gauss-Seidel sweep, both
+// colours fused in one pass over the level (the hot kernel of the mixed path).
+//
+// Work decomposition: a CTA owns a TJ x TK tile of (j,k) columns and a chunk
+// of planes [i0, i1) along i (the slowest index).  It marches up the chunk
+// keeping a ring of four planes in shared memory, each with a two-cell halo in
+// j and k.  At step s it loads plane s+1 (old values), updates the first
+// colour ((i+j+k) even, the paper's first sweep) on plane s over the tile plus
+// a one-cell ring, then the second colour on plane s-1 over the tile.  The ring
+// cells' first-colour values are recomputed from old values exactly as their
+// owner computes them, so each CTA sees the true red-black ordering.  All
+// reads come from e_in and all writes go to e_out (ping-pong), so no CTA can
+// observe another's new values: the result equals one red-black sweep for
+// any CTA schedule.
+//
+// Per cell the stencil uses a precomputed neighbour quantity q (f(R): Delta w
+// = (u+e)^{n+1} - u^{n+1}; symmetron, CQ: e), refreshed whenever e changes.
+#pragma once
+#include "mg_common.cuh"
+
+namespace mg {
+
+// FP32 constants of one level (correction form).
+struct LevelF {
+  float c2_h2;   // c~^2 / h^2
+  float al;      // f(R): h^2 / (6 c~^2); symmetron: g = c~^2 xi^2 / (h^2 a^2)
+  float K;       // f(R): Rbar a^2/3 * ubar
+  float alK;     // f(R): al * K
+  float msym;    // symmetron a^2/(2 xi^2)
+  float rat3;    // symmetron (a_star/a)^3
+  float ih2;     // 1/h^2
+  float fr_s;    // f(R): s = (al K)^{1/(n+2)}, the root's natural scale
+  float fr_is1;  // f(R): 1 / s^{n+1}
+  float cq_src, cq_pot, alpha, phibar, inv_c2, beta;
+  int keep_exp;
+};
+
+// ---- fast single-precision building blocks (MUFU-based) ----
+// approximate reciprocal (about 1 ulp): the local solve's Newton steps tolerate it
+__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+// x^{1/3} for x > 0 (fast power intrinsic, a few ulp)
+__device__ __forceinline__ float fcbrt_pos(float x) { return __powf(x, 1.0f / 3.0f); }
+// sqrt(x) for x >= 0 as x / sqrt(x) with the fast reciprocal square root (x = 0 gives 0)
+__device__ __forceinline__ float fsqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
+// Delta w = (u+e)^{n+1} - u^{n+1}, factored so that small e loses nothing.
+template <int K>
+__device__ __forceinline__ float dw(float u, float e) {
+  if constexpr (K == KFR0) return e;
+  else if constexpr (K == KFR1) return e * (2.f * u + e);
+  else return e * (3.f * u * u + 3.f * u * e + e * e);
+}
+
+// Neighbour quantity of a cell in the stencil sum.
+template <int K>
+__device__ __forceinline__ float nbq(float u, float e) {
+  if constexpr (is_fr(K)) return dw<K>(u, e);
+  else return e;
+}
+
+// Positive root y of y^{m} + p y - 1 = 0 (m = n+2) by the closed forms of
+// Sec. 3.2.5 in fast single precision, as the start for the exact polish.
+template <int K>
+__device__ __forceinline__ float fr_root_scaled_fast(float p) {
+  if constexpr (K == KFR0) {
+    // y^2 + p y - 1 = 0
+    const float s = fsqrt(p * p + 4.f);
+    return p > 0.f ? fdiv(2.f, p + s) : 0.5f * (s - p);
+  } else if constexpr (K == KFR1) {
+    // y^3 + p y - 1 = 0, D = 1/4 + (p/3)^3
+    const float p3 = p * (1.f / 3.f);
+    const float D = 0.25f + p3 * p3 * p3;
+    if (D >= 0.f) {
+      const float A = fcbrt_pos(0.5f + fsqrt(D));
+      const float B = fdiv(p3, A);
+      return frcp(A * A + p3 + B * B);
+    }
+    // three real roots: the largest lies in [sqrt(3) r, 2 r), r = sqrt(-p/3);
+    // Newton from 2r converges monotonically (P convex there)
+    float y = 2.f * fsqrt(-p3);
+#pragma unroll
+    for (int it = 0; it < 3; ++it) y -= fdiv((y * y + p) * y - 1.f, 3.f * y * y + p);
+    return y;
+  } else {
+    // y^4 + p y - 1 = 0 (Eq. fR_quartic_solns with q = -1): Delta0 = -12, Delta1 = 27 p^2
+    if (p == 0.f) return 1.f;
+    const float d1 = 27.f * p * p;
+    const float a = fcbrt_pos(0.5f * (fsqrt(d1 * d1 + 6912.f) + d1));
+    const float b = fdiv(12.f, a);
+    const float S = fsqrt(fdiv(d1, 12.f * (a * a + a * b + b * b)));
+    if (p > 0.f) {
+      const float r2 = fdiv(p, 4.f * S) - S * S;
+      const float xc = fdiv(r2 - S * S, fsqrt(fmaxf(r2, 0.f)) + S);
+      const float xl = frcp(p);
+      return (xc > 0.f && xc < xl) ? xc : xl;
+    }
+    return S + fsqrt(fmaxf(fdiv(-p, 4.f * S) - S * S, 0.f));
+  }
+}
+
+// Symmetron total-field root of U^3 + p U + q = 0 with the sign rule of the
+// FP64 path, fast single precision (start for the polish).
+__device__ __forceinline__ float sym_root_fast(float p, float q, float u_old) {
+  if (q == 0.f) return p >= 0.f ? 0.f : (u_old < 0.f ? -fsqrt(-p) : fsqrt(-p));
+  const float sg = q < 0.f ? 1.f : -1.f;
+  const float hq = 0.5f * fabsf(q);
+  const float p3 = p * (1.f / 3.f);
+  const float D = hq * hq + p3 * p3 * p3;
+  float x;
+  if (D >= 0.f) {
+    const float A = fcbrt_pos(hq + fsqrt(D));
+    const float B = fdiv(p3, A);
+    x = fdiv(hq + hq, A * A + p3 + B * B);
+  } else {
+    const float aq = -2.f * hq;  // q of the positive-side problem
+    x = 2.f * fsqrt(-p3);
+#pragma unroll
+    for (int it = 0; it < 3; ++it) x -= fdiv((x * x + p) * x + aq, 3.f * x * x + p);
+  }
+  return sg * x;
+}
+
+// Nonlinear Gauss-Seidel update of the correction e at one cell.
+//  u: base field, e: current correction, rho: density (symmetron/CQ), s: source,
+//  Lnb: sum of the six neighbours' nbq.
+template <int K>
+__device__ __forceinline__ float update_e_fast(const LevelF& f, float u, float e, float rho, float s, float Lnb) {
+  if constexpr (is_fr(K)) {
+    // total-field polynomial U^{n+2} + p U - al K = 0, p = -u^{n+1} + al K/u - B
+    const float B = Lnb * (1.f / 6.f) + f.al * s;
+    const float p = -fr_w<K>(u) + f.alK * frcp(u) - B;
+    const float U = f.fr_s * fr_root_scaled_fast<K>(p * f.fr_is1);
+    float x = U - u;
+    // two Newton steps on G(x) = Delta w(x) + al K x/(u(u+x)) - B (no cancellation
+    // in x): the closed form leaves x with an absolute error ~1e-6 u; the first
+    // step squares it, the second brings x to single-precision relative accuracy
+    const float ru = frcp(u);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const float Ue = u + x;
+      const float rU = frcp(Ue);
+      const float G = dw<K>(u, x) + f.alK * x * ru * rU - B;
+      float dG = f.alK * rU * rU;
+      if constexpr (K == KFR0) dG += 1.f;
+      else if constexpr (K == KFR1) dG += 2.f * Ue;
+      else dG += 3.f * Ue * Ue;
+      const float xn = x - fdiv(G, dG);
+      x = (u + xn > 0.f) ? xn : x;
+    }
+    return x;
+  } else if constexpr (K == KSYM) {
+    const float p = rho * f.rat3 - 1.f + 12.f * f.al;
+    const float B = 2.f * f.al * Lnb - fdiv(s, f.msym);
+    const float q = -(p * u + u * u * u + B);
+    const float U = sym_root_fast(p, q, u + e);
+    float x = U - u;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const float G = p * x + x * (3.f * u * u + 3.f * u * x + x * x) - B;
+      const float Ue = u + x;
+      const float dG = p + 3.f * Ue * Ue;
+      x = dG != 0.f ? x - fdiv(G, dG) : x;
+    }
+    return x;
+  } else {
+    // Newton-Gauss-Seidel step (Eq. relaxation_iteration) on M(e) - s
+    const float x0 = f.phibar + u * f.inv_c2;
+    const float dpow = powf(x0, -1.f - f.alpha) * expm1f((-1.f - f.alpha) * log1pf(e * f.inv_c2 / x0));
+    float r = (Lnb - 6.f * e) * f.ih2 + f.cq_pot * dpow - s;
+    const float x = x0 + e * f.inv_c2;
+    float dr = -6.f * f.ih2 - f.cq_pot * (1.f + f.alpha) * powf(x, -2.f - f.alpha) * f.inv_c2;
+    if (f.keep_exp) {
+      const float Eu = expf(f.beta * u * f.inv_c2);
+      r -= f.cq_src * rho * Eu * expm1f(f.beta * e * f.inv_c2);
+      dr -= f.cq_src * rho * f.beta * f.inv_c2 * Eu * expf(f.beta * e * f.inv_c2);
+    }
+    return e - r / dr;
+  }
+}
+
+}  // namespace mg
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+// k_sweep32: one full red-black sweep of the correction equation on one level
+// ---------------------------------------------------------------------------
+//
+// Shared-memory plane layout: a (TJ+4) x (TK+4) plane (two-cell halo) stored
+// row by row, each row split into its even-k half followed by its odd-k half.
+// The cells of one colour in a row then sit at unit stride in one half and
+// their k-neighbours at unit stride in the other half, so a warp's accesses are
+// free of bank conflicts.  Each thread computes its load and update offsets
+// once; only the plane base changes as the CTA marches along i.
+template <int K, int TJ, int TK>
+__global__ void __launch_bounds__(TJ* TK / 2) k_sweep32(LevelF f, int n, int chunk, const float* __restrict__ e_in,
+                                                        float* __restrict__ e_out, const float* __restrict__ ub,
+                                                        const float* __restrict__ rho, const float* __restrict__ S) {
+  constexpr int PJ = TJ + 4, PK = TK + 4, LS = PJ * PK;  // logical plane with a two-cell halo
+  // each row stored as its even-k half then its odd-k half; for f(R) the halves
+  // are padded to a 16-bank offset so that the two halves never share a bank
+  constexpr int HP0 = PK / 2;
+  constexpr int HP = is_fr(K) ? (HP0 <= 16 ? 16 : ((HP0 - 16 + 31) / 32) * 32 + 16) : HP0;
+  constexpr int RS = 2 * HP, PS = PJ * RS;  // row stride and stored plane size
+  constexpr int NT = TJ * TK / 2;          // threads: one second-colour cell each
+  constexpr int NE = (LS + NT - 1) / NT;   // plane elements loaded per thread
+  constexpr int RW = (TK + 2) / 2;         // first-colour cells per row of the one-cell ring
+  constexpr int NA = ((TJ + 2) * RW + NT - 1) / NT;  // first-colour cells per thread
+  constexpr bool FR = is_fr(K);
+  constexpr bool RHO = (K == KSYM) || (K == KCQ);
+  __shared__ float s_q[4][PS];             // neighbour quantity, planes s-2 .. s+1
+  __shared__ float s_u[3][PS];             // base field, planes s-1 .. s+1
+  __shared__ float s_s[3][PS];             // source
+  __shared__ float s_r[RHO ? 3 : 1][RHO ? PS : 1];
+
+  const int tiles_k = n / TK;
+  const int k0 = (blockIdx.x % tiles_k) * TK;
+  const int j0 = (blockIdx.x / tiles_k) * TJ;
+  const int i0 = blockIdx.y * chunk;
+  const int i1 = min(i0 + chunk, n);
+  const int t = threadIdx.x;
+  const size_t nn = (size_t)n * n;
+
+  // ---- per-thread offsets, computed once ----
+  int l_sx[NE];      // split shared index of each loaded element (-1: none)
+  int l_g[NE];       // in-plane global offset
+  bool l_h1[NE];     // inside the one-cell halo (source/density needed)
+#pragma unroll
+  for (int m = 0; m < NE; ++m) {
+    const int c = t + m * NT;
+    l_sx[m] = -1;
+    l_g[m] = 0;
+    l_h1[m] = false;
+    if (c < LS) {
+      const int jj = c / PK, kk = c - jj * PK;
+      l_sx[m] = jj * RS + (kk >> 1) + (kk & 1) * HP;
+      l_g[m] = wrapi(j0 + jj - 2, n) * n + wrapi(k0 + kk - 2, n);
+      l_h1[m] = jj >= 1 && jj <= TJ + 2 && kk >= 1 && kk <= TK + 2;
+    }
+  }
+  // first-colour cells on the ring rows: row jj (1..TJ+2) and index q (0..RW-1);
+  // kk = 1 + 2q + d with d = parity offset, which alternates with the plane
+  int a_jj[NA], a_q[NA], a_d0[NA];
+#pragma unroll
+  for (int m = 0; m < NA; ++m) {
+    const int c = t + m * NT;
+    a_jj[m] = -1;
+    a_q[m] = 0;
+    a_d0[m] = 0;
+    if (c < (TJ + 2) * RW) {
+      const int r = c / RW;
+      a_jj[m] = r + 1;
+      a_q[m] = c - r * RW;
+      // (i + j + k) even with k = k0 - 1 + 2q + d and i even: d = (j + k0 - 1) & 1
+      a_d0[m] = ((j0 + a_jj[m] - 2 + k0 - 1) % 2 + 2) & 1;
+    }
+  }
+  // second-colour cell: row jj = t/(TK/2) + 2, index q = t % (TK/2), kk = 2 + 2q + d
+  const int b_jj = t / (TK / 2) + 2, b_q = t % (TK / 2);
+  const int b_d0 = (j0 + b_jj - 2 + k0 + 1) & 1;  // for i even: (i + j + k) odd
+
+  float pe[NE], pu[NE], ps[NE], pr[RHO ? NE : 1];
+  auto fetch = [&](int p) {
+    const int ig = p < 0 ? p + n : (p >= n ? p - n : p);
+    const size_t base = (size_t)ig * nn;
+#pragma unroll
+    for (int m = 0; m < NE; ++m) {
+      if (l_sx[m] >= 0) {
+        const size_t g = base + l_g[m];
+        pe[m] = e_in[g];
+        pu[m] = ub[g];
+        if (l_h1[m]) {
+          ps[m] = S[g];
+          if constexpr (RHO) pr[m] = rho ? rho[g] : 1.f;
+        }
+      }
+    }
+  };
+  auto sl3 = [](int p) { return (p + 6) % 3; };
+  auto commit = [&](int p) {
+    const int slot = p & 3, s3 = sl3(p);
+#pragma unroll
+    for (int m = 0; m < NE; ++m) {
+      if (l_sx[m] >= 0) {
+        s_u[s3][l_sx[m]] = pu[m];
+        s_q[slot][l_sx[m]] = nbq<K>(pu[m], pe[m]);
+        if (l_h1[m]) {
+          s_s[s3][l_sx[m]] = ps[m];
+          if constexpr (RHO) s_r[s3][l_sx[m]] = pr[m];
+        }
+      }
+    }
+  };
+  // relax the cell at row jj, tile column kk of plane p; returns the new correction
+  auto relax = [&](int p, int jj, int kk) -> float {
+    const int slot = p & 3, sm = (p - 1) & 3, sp = (p + 1) & 3, s3 = sl3(p);
+    const int own = jj * RS + (kk >> 1) + (kk & 1) * HP;
+    const int oth = jj * RS + (1 - (kk & 1)) * HP;  // other half of the row
+    const float Lnb = s_q[sm][own] + s_q[sp][own] + s_q[slot][own - RS] + s_q[slot][own + RS] +
+                      s_q[slot][oth + ((kk - 1) >> 1)] + s_q[slot][oth + ((kk + 1) >> 1)];
+    float rv = 1.f, eo = 0.f;
+    if constexpr (RHO) rv = s_r[s3][own];
+    if constexpr (!FR) eo = s_q[slot][own];
+    const float uv = s_u[s3][own];
+    const float en = update_e_fast<K>(f, uv, eo, rv, s_s[s3][own], Lnb);
+    s_q[slot][own] = nbq<K>(uv, en);
+    return en;
+  };
+
+  fetch(i0 - 2);
+  commit(i0 - 2);
+  fetch(i0 - 1);
+  commit(i0 - 1);
+  fetch(i0);
+  for (int s = i0 - 1; s <= i1; ++s) {
+    commit(s + 1);
+    if (s + 2 <= i1 + 1) fetch(s + 2);
+    __syncthreads();
+    // first colour ((i+j+k) even) on plane s over the tile plus a one-cell ring
+    {
+      const int ig = s < 0 ? s + n : (s >= n ? s - n : s);
+      const bool store = s >= i0 && s < i1;
+      const size_t pbase = (size_t)ig * nn;
+#pragma unroll
+      for (int m = 0; m < NA; ++m) {
+        if (a_jj[m] < 0) continue;
+        const int kk = 1 + 2 * a_q[m] + (a_d0[m] ^ (ig & 1));
+        const float en = relax(s, a_jj[m], kk);
+        if (store && a_jj[m] >= 2 && a_jj[m] < TJ + 2 && kk >= 2 && kk < TK + 2)
+          e_out[pbase + (size_t)(j0 + a_jj[m] - 2) * n + (k0 + kk - 2)] = en;
+      }
+    }
+    __syncthreads();
+    // second colour on plane s-1 over the tile
+    if (s - 1 >= i0) {
+      const int p = s - 1;
+      const int kk = 2 + 2 * b_q + (b_d0 ^ (p & 1));
+      const float en = relax(p, b_jj, kk);
+      e_out[(size_t)p * nn + (size_t)(j0 + b_jj - 2) * n + (k0 + kk - 2)] = en;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace mg

@@ -152,12 +152,46 @@ def test_mixed_solve_matches_oracle(orc, mg, key):
     box = {"sym": float(N), "cq": 64.0}.get(key, 64.0)
     po, ref, got, st, rho32 = solve_pair(orc, mg, key, N, box, rho, 1e-10, precision=1)
     assert st.converged, st
-    assert relL2(got, ref.u) <= 1e-6
     # the oracle's own residual of the GPU solution
     rho_n = rho32.astype(np.float64) / rho32.astype(np.float64).mean()
     d = orc.residual(po, got, rho_n)
-    eps = np.sqrt((d ** 2).mean()) / orc.source_rms(po, rho_n)
+    snorm = orc.source_rms(po, rho_n)
+    eps = np.sqrt((d ** 2).mean()) / snorm
     assert eps <= 1e-8
+    if key != "cq":
+        assert relL2(got, ref.u) <= 1e-6
+    else:
+        # CQ: the potential's mass m^2 = alpha (1+alpha) lambda^2 a^2 phibar^{-2-alpha}/c^2
+        # (~2e-7 here) is the only restoring term for the mean of phi, so the mean
+        # is fixed only to (mean residual)/m^2 and exerts no force; the fluctuations
+        # are well conditioned (smallest nonzero K_h^2 = 4 sin^2(pi/N) >> m^2)
+        assert relL2(got - got.mean(), ref.u - ref.u.mean()) <= 1e-6
+        c2 = orc.background(po, N)["c2"]
+        m2 = po.alpha * (1 + po.alpha) * po.lam ** 2 * po.phibar ** (-2 - po.alpha) / c2
+        bound = 10 * (eps + ref.eps) * snorm / m2
+        assert abs(got.mean() - ref.u.mean()) <= bound
+
+
+@pytest.mark.parametrize("key", ["fr1", "sym"])
+@pytest.mark.parametrize("N", [64, 96])
+def test_mixed_iterates_follow_oracle_vcycles(orc, mg, key, N):
+    """One inner FP32 V-cycle in correction form reproduces, up to single
+    precision, the oracle's FP64 V-cycle on the total field (same red-black
+    order, transfers and coarse solve): compare after 1, 2 and 3 cycles.  The
+    64^3 and 96^3 meshes run the fused sweep kernel on their fine levels."""
+    rho = inputs.lognormal_density(N, 1.0, seed=50 + N)
+    rho32 = rho.astype(np.float32)
+    box = float(N) if key == "sym" else 2.0 * N
+    for cycles in (1, 2, 3):
+        # sweep_chunk > 0 forces the fused sweep kernel on every tileable level
+        po, pg = both_params(orc, mg, key, box=box, precision=1, max_cycles=cycles, sweep_chunk=8)
+        ref = orc.solve(po, rho32.astype(np.float64), tol=0.0, max_cycles=cycles)
+        field = torch.full((N, N, N), float("nan"), dtype=torch.float64, device="cuda")
+        mg.solve_scalar(pg, 1.0, cuda32(rho32), field, 0.0, allow_unconverged=True)
+        got = field.cpu().numpy()
+        b = orc.background(po, N)["ubar"]
+        # compare the deviation from the background, which is what the cycles build
+        assert relL2(got - b, ref.u - b) <= 2e-5, cycles
 
 
 def test_mixed_solve_strong_screening_ragged_levels(orc, mg):
