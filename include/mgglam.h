@@ -128,6 +128,35 @@ int mgglam_default_params(mgglam_params* prm);
 int mgglam_deposit_cic(const float* pos, long long np, int N, float* rho, void* stream);
 
 /*
+ * The same CIC density assignment as mgglam_deposit_cic (identical result, bit
+ * for bit), for callers that must not trigger a device allocation.
+ * mgglam_deposit_cic takes its accumulator from the library's scratch cache
+ * and calls cudaMalloc the first time it sees a mesh size.  Some callers
+ * cannot allow that: code that runs while a CUDA graph is being captured
+ * (an allocation there fails or breaks the capture), applications that
+ * hand all device memory to their own pool allocator and hold a fixed budget,
+ * and loops that cannot absorb the implicit device synchronisation of
+ * cudaMalloc.  This entry point allocates nothing.  Its accumulator is a fixed
+ * device array compiled into the library, sized for meshes up to N = 128
+ * (128^3 64-bit integers = 16 MiB); every GPU on which the library is used
+ * holds that array until the process exits.
+ *   Arguments and layout as for mgglam_deposit_cic.
+ *   N must satisfy 2 <= N <= 128; larger meshes return MGGLAM_ERR_SHAPE before
+ *   any work is enqueued (use mgglam_deposit_cic for them).
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before starting
+ * any stream capture.  Each call clears the part of the array it uses before
+ * accumulating, but all calls share the one array: calls that may run at the
+ * same time on the GPU (different streams without ordering, or several host
+ * threads) race and corrupt each other's results.
+ * This entry point is an implementation convenience; the paper has no
+ * counterpart.
+ * Errors: MGGLAM_ERR_ARG (null pointer, np < 1), MGGLAM_ERR_SHAPE (N),
+ * MGGLAM_ERR_CUDA.
+ */
+int mgglam_deposit_cic_static(const float* pos, long long np, int N, float* rho, void* stream);
+
+/*
  * Solve the model's discrete scalar-field equation N_h(u; rho) = 0 (the
  * fine-level local residual of Eq. residual_d set to zero) by multigrid cycles
  * until the relative global residual (see mgglam_stats) is <= tol or

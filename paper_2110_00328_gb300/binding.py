@@ -97,7 +97,7 @@ _lib = None
 EXPORTS = ["mgglam_version", "mgglam_status_string", "mgglam_default_params", "mgglam_deposit_cic",
            "mgglam_solve_scalar", "mgglam_gather_force", "mgglam_smooth", "mgglam_residual",
            "mgglam_restrict", "mgglam_prolong_correct", "mgglam_release", "mgglam_profile_start",
-           "mgglam_profile_stop", "mgglam_launch_count"]
+           "mgglam_profile_stop", "mgglam_launch_count", "mgglam_deposit_cic_static"]
 
 
 class CKernelProfile(ctypes.Structure):
@@ -258,3 +258,23 @@ def profile_stop() -> dict:
     _check("mgglam_profile_stop", load().mgglam_profile_stop(arr, 32, ctypes.byref(n)))
     return {arr[k].name.decode(): {"launches": arr[k].launches, "ms": arr[k].ms, "bytes": arr[k].bytes}
             for k in range(min(n.value, 32))}
+
+
+def deposit_cic_static(pos, N: int, rho=None, stream=None):
+    """CIC density through mgglam_deposit_cic_static (no device allocation; N <= 128).
+
+    rho must be supplied by a caller that cannot allocate; it is created here
+    only for convenience when omitted.
+    """
+    import torch
+    lib = load()
+    if not hasattr(lib, "_static_bound"):
+        lib.mgglam_deposit_cic_static.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
+                                                  ctypes.c_void_p, ctypes.c_void_p]
+        lib.mgglam_deposit_cic_static.restype = ctypes.c_int
+        lib._static_bound = True
+    if rho is None:
+        rho = torch.empty((N, N, N), dtype=torch.float32, device=pos.device)
+    _check("mgglam_deposit_cic_static", lib.mgglam_deposit_cic_static(_ptr(pos, torch.float32), pos.shape[0], N,
+                                                                    _ptr(rho, torch.float32), _stream(stream)))
+    return rho

@@ -15,6 +15,8 @@
 // around it with its CIC weights.
 #include <math.h>
 
+#include <mutex>
+
 #include "mg_common.cuh"
 #include "mg_internal.h"
 
@@ -194,3 +196,65 @@ int gather_force(const ModelDev& m, int kind, int n_fr, const mgglam_params* prm
 }
 
 }  // namespace mg
+
+// ---------------------------------------------------------------------------
+// Deposit without allocation (mgglam_deposit_cic_static)
+// ---------------------------------------------------------------------------
+//
+// The accumulator lives in a fixed file-scope device array instead of the
+// scratch cache, so this entry point never calls cudaMalloc.  The array's name
+// is only a host-side stand-in in host code; the device address comes from
+// cudaGetSymbolAddress, looked up once per device (with that device current)
+// on the first call and cached.
+
+namespace mg {
+
+constexpr int kStaticDepositMaxN = 128;
+constexpr size_t kStaticDepositCells = (size_t)kStaticDepositMaxN * kStaticDepositMaxN * kStaticDepositMaxN;
+constexpr int kStaticMaxDevices = 64;
+
+static __device__ __align__(256) unsigned long long g_static_deposit_acc[kStaticDepositCells];
+
+static std::mutex g_static_mu;
+static unsigned long long* g_static_acc_ptr[kStaticMaxDevices];
+
+static int static_deposit_scratch(unsigned long long** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return MGGLAM_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kStaticMaxDevices) return MGGLAM_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_acc_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_deposit_acc);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return MGGLAM_ERR_CUDA;
+    }
+    g_static_acc_ptr[dev] = (unsigned long long*)p;
+  }
+  *out = g_static_acc_ptr[dev];
+  return MGGLAM_OK;
+}
+
+}  // namespace mg
+
+extern "C" int mgglam_deposit_cic_static(const float* pos, long long np, int N, float* rho, void* stream) {
+  using namespace mg;
+  if (!pos || !rho || np < 1) return MGGLAM_ERR_ARG;
+  if (N < 2 || N > kStaticDepositMaxN) return MGGLAM_ERR_SHAPE;
+  unsigned long long* acc = nullptr;
+  int rc = static_deposit_scratch(&acc);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long n3 = (long long)N * N * N;
+  // the array keeps the previous call's sums: clear the part this call uses
+  MG_CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)n3 * sizeof(unsigned long long), st));
+  k_deposit_fixed<<<grid_for(np, kThreads, 1 << 20), kThreads, 0, st>>>(pos, np, N, acc);
+  k_deposit_finish<<<grid_for(n3, kThreads, 1 << 20), kThreads, 0, st>>>(acc, n3, (double)n3 / (double)np, rho);
+  note_launch(2);
+  MG_CUDA_TRY(cudaGetLastError());
+  return MGGLAM_OK;
+}
