@@ -80,9 +80,9 @@ typedef struct {
                          adaptive: enough to reach tol at the observed contraction, capped
                          where single precision stops gaining within one step */
   int check_every;    /* FP64: test convergence every k cycles (default 1) */
-  int sweep_chunk;    /* MIXED: planes per CTA of the fused sweep kernel; 0 (default) = 16 and
-                         the fused kernel only on levels that yield enough CTAs; > 0 forces
-                         the fused kernel on every level whose tile divides the mesh */
+  int sweep_chunk;    /* MIXED: <= 0 (default): one smoothing kernel per colour on every
+                         level; > 0: the fused two-colour sweep kernel, with this many
+                         planes per CTA, on every level whose tile divides the mesh */
   int reserved[3];
 } mgglam_params;
 

@@ -88,18 +88,13 @@ template <int K>
 __global__ void __launch_bounds__(kThreads) k_smooth64(ModelDev m, int n, double h, double* __restrict__ u,
                                                        const double* __restrict__ rho,
                                                        const double* __restrict__ S, int parity) {
-  const int nh = n >> 1;
-  const long long total = (long long)n * n * nh;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int kk = (int)(t % nh);
-    const long long r = t / nh;
-    const int j = (int)(r % n), i = (int)(r / n);
-    const int k = 2 * kk + ((i + j + parity) & 1);
-    const size_t c = cidx(n, i, j, k);
-    const double Lnb = nb_sum64<K>(u, n, i, j, k);
-    u[c] = local_update64<K>(m, h, u[c], rho[c], S ? S[c] : 0.0, Lnb);
-  }
+  const int i = blockIdx.z, j = blockIdx.y;
+  const int kk = blockIdx.x * blockDim.x + threadIdx.x;
+  if (kk >= (n >> 1)) return;
+  const int k = 2 * kk + ((i + j + parity) & 1);
+  const size_t c = cidx(n, i, j, k);
+  const double Lnb = nb_sum64<K>(u, n, i, j, k);
+  u[c] = local_update64<K>(m, h, u[c], rho[c], S ? S[c] : 0.0, Lnb);
 }
 
 // d = N(u) - S on every cell; optional store of d; per-block partial sums of d^2.
@@ -108,16 +103,16 @@ __global__ void __launch_bounds__(kThreads) k_residual64(ModelDev m, int n, doub
                                                          const double* __restrict__ rho,
                                                          const double* __restrict__ S, double* __restrict__ d,
                                                          double* __restrict__ partials) {
-  const long long total = (long long)n * n * n;
   double acc = 0.0;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(t % n);
-    const long long r = t / n;
-    const int j = (int)(r % n), i = (int)(r / n);
-    const double v = local_N64<K>(m, h, u[t], rho[t], nb_sum64<K>(u, n, i, j, k)) - (S ? S[t] : 0.0);
-    if (d) d[t] = v;
-    acc += v * v;
+  // grid-stride over rows (i, j), threads along k
+  for (int r = blockIdx.x; r < n * n; r += gridDim.x) {
+    const int i = r / n, j = r - (r / n) * n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const size_t t = cidx(n, i, j, k);
+      const double v = local_N64<K>(m, h, u[t], rho[t], nb_sum64<K>(u, n, i, j, k)) - (S ? S[t] : 0.0);
+      if (d) d[t] = v;
+      acc += v * v;
+    }
   }
   acc = block_sum(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
@@ -134,18 +129,14 @@ __global__ void k_finalize_sum(const double* __restrict__ partials, int count, d
 // coarse = mean of the 8 children.
 __global__ void k_restrict64(int nf, const double* __restrict__ fine, double* __restrict__ coarse) {
   const int nc = nf >> 1;
-  const long long total = (long long)nc * nc * nc;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int K = (int)(t % nc);
-    const long long r = t / nc;
-    const int J = (int)(r % nc), I = (int)(r / nc);
-    double s = 0.0;
-    for (int di = 0; di < 2; ++di)
-      for (int dj = 0; dj < 2; ++dj)
-        for (int dk = 0; dk < 2; ++dk) s += fine[cidx(nf, 2 * I + di, 2 * J + dj, 2 * K + dk)];
-    coarse[t] = s * 0.125;
-  }
+  const int I = blockIdx.z, J = blockIdx.y;
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K >= nc) return;
+  double s = 0.0;
+  for (int di = 0; di < 2; ++di)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int dk = 0; dk < 2; ++dk) s += fine[cidx(nf, 2 * I + di, 2 * J + dj, 2 * K + dk)];
+  coarse[cidx(nc, I, J, K)] = s * 0.125;
 }
 
 // Fused: for each coarse cell, the local residual of its 8 children is formed
@@ -159,12 +150,10 @@ __global__ void __launch_bounds__(kThreads) k_residual_restrict64(ModelDev m, in
                                                                   double* __restrict__ Ru, double* __restrict__ uH,
                                                                   double* __restrict__ Rd) {
   const int nc = nf >> 1;
-  const long long total = (long long)nc * nc * nc;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int K0 = (int)(t % nc);
-    const long long r = t / nc;
-    const int J = (int)(r % nc), I = (int)(r / nc);
+  const int I = blockIdx.z, J = blockIdx.y;
+  const int K0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (K0 < nc) {
+    const size_t t = cidx(nc, I, J, K0);
     double su = 0.0, sd = 0.0;
     for (int di = 0; di < 2; ++di)
       for (int dj = 0; dj < 2; ++dj)
@@ -186,14 +175,11 @@ __global__ void __launch_bounds__(kThreads) k_residual_restrict64(ModelDev m, in
 template <int K>
 __global__ void __launch_bounds__(kThreads) k_fas_source64(ModelDev m, int n, double h, const double* __restrict__ Ru,
                                                            const double* __restrict__ rho, double* __restrict__ S) {
-  const long long total = (long long)n * n * n;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(t % n);
-    const long long r = t / n;
-    const int j = (int)(r % n), i = (int)(r / n);
-    S[t] = local_N64<K>(m, h, Ru[t], rho[t], nb_sum64<K>(Ru, n, i, j, k)) - S[t];
-  }
+  const int i = blockIdx.z, j = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const size_t t = cidx(n, i, j, k);
+  S[t] = local_N64<K>(m, h, Ru[t], rho[t], nb_sum64<K>(Ru, n, i, j, k)) - S[t];
 }
 
 // The prolongation weight stencil at fine cell (i,j,k) of coarse field c (side nc).
@@ -215,12 +201,10 @@ __global__ void __launch_bounds__(kThreads) k_prolong_correct64(int nc, const do
                                                                 const double* __restrict__ RuH,
                                                                 double* __restrict__ uf) {
   const int nf = nc << 1;
-  const long long total = (long long)nf * nf * nf;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(t % nf);
-    const long long r = t / nf;
-    const int j = (int)(r % nf), i = (int)(r / nf);
+  const int i = blockIdx.z, j = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nf) {
+    const size_t t = cidx(nf, i, j, k);
     const int I = i >> 1, J = j >> 1, K = k >> 1;
     const int I2 = wrapi(I + ((i & 1) ? 1 : -1), nc);
     const int J2 = wrapi(J + ((j & 1) ? 1 : -1), nc);
@@ -306,6 +290,10 @@ __global__ void k_init_background_first(double* __restrict__ field, double ubar)
 // Launchers (dispatch on the model kind)
 // ---------------------------------------------------------------------------
 
+// 3D grid for kernels indexed (x: k, y: j, z: i) with k3dThreads threads along k.
+constexpr int k3dThreads = 64;
+static dim3 grid3d(int n_k, int n_j, int n_i) { return dim3((n_k + k3dThreads - 1) / k3dThreads, n_j, n_i); }
+
 #define MG_DISPATCH(kind, KERNEL_CALL)                       \
   switch (kind) {                                            \
     case KFR0: { constexpr int KK = KFR0; KERNEL_CALL; note_launch(1); } break; \
@@ -318,11 +306,10 @@ __global__ void k_init_background_first(double* __restrict__ field, double ubar)
 
 int launch_smooth64(const ModelDev& m, int n, double h, double* u, const double* rho, const double* S,
                     int sweeps, cudaStream_t st) {
-  const long long half = (long long)n * n * (n / 2);
-  const int g = grid_for(half, kThreads, 1 << 20);
+  const dim3 g = grid3d(n / 2, n, n);
   for (int s = 0; s < sweeps; ++s)
     for (int parity = 0; parity < 2; ++parity) {
-      MG_DISPATCH(m.kind, (k_smooth64<KK><<<g, kThreads, 0, st>>>(m, n, h, u, rho, S, parity)));
+      MG_DISPATCH(m.kind, (k_smooth64<KK><<<g, k3dThreads, 0, st>>>(m, n, h, u, rho, S, parity)));
     }
   MG_CUDA_TRY(cudaGetLastError());
   return MGGLAM_OK;
@@ -331,8 +318,9 @@ int launch_smooth64(const ModelDev& m, int n, double h, double* u, const double*
 int launch_residual64(const ModelDev& m, int n, double h, const double* u, const double* rho,
                       const double* S, double* d, double* partials, double* out_sum, cudaStream_t st) {
   const long long n3 = (long long)n * n * n;
-  const int g = grid_for(n3);
-  MG_DISPATCH(m.kind, (k_residual64<KK><<<g, kThreads, 0, st>>>(m, n, h, u, rho, S, d, partials)));
+  const int g = n * n < 2048 ? n * n : 2048;
+  const int bt = n >= 256 ? 256 : (n <= 32 ? 32 : ((n + 31) / 32) * 32);
+  MG_DISPATCH(m.kind, (k_residual64<KK><<<g, bt, 0, st>>>(m, n, h, u, rho, S, d, partials)));
   k_finalize_sum<<<1, 1024, 0, st>>>(partials, g, out_sum);
   note_launch(1);
   MG_CUDA_TRY(cudaGetLastError());
@@ -341,7 +329,7 @@ int launch_residual64(const ModelDev& m, int n, double h, const double* u, const
 
 int launch_restrict64(int nf, const double* fine, double* coarse, cudaStream_t st) {
   const long long nc3 = (long long)(nf / 2) * (nf / 2) * (nf / 2);
-  k_restrict64<<<grid_for(nc3, kThreads, 1 << 20), kThreads, 0, st>>>(nf, fine, coarse);
+  k_restrict64<<<grid3d(nf / 2, nf / 2, nf / 2), k3dThreads, 0, st>>>(nf, fine, coarse);
   note_launch(1);
   MG_CUDA_TRY(cudaGetLastError());
   return MGGLAM_OK;
@@ -350,9 +338,9 @@ int launch_restrict64(int nf, const double* fine, double* coarse, cudaStream_t s
 int launch_prolong_correct64(const ModelDev& m, int nc, const double* uH, const double* RuH, double* uf,
                              cudaStream_t st) {
   const long long nf3 = 8LL * nc * nc * nc;
-  const int g = grid_for(nf3, kThreads, 1 << 20);
-  if (is_fr(m.kind)) k_prolong_correct64<true><<<g, kThreads, 0, st>>>(nc, uH, RuH, uf);
-  else k_prolong_correct64<false><<<g, kThreads, 0, st>>>(nc, uH, RuH, uf);
+  const dim3 g = grid3d(2 * nc, 2 * nc, 2 * nc);
+  if (is_fr(m.kind)) k_prolong_correct64<true><<<g, k3dThreads, 0, st>>>(nc, uH, RuH, uf);
+  else k_prolong_correct64<false><<<g, k3dThreads, 0, st>>>(nc, uH, RuH, uf);
   note_launch(1);
   MG_CUDA_TRY(cudaGetLastError());
   return MGGLAM_OK;
@@ -369,8 +357,8 @@ int launch_coarse64(const ModelDev& m, int n, double h, double* u, const double*
 int launch_residual_restrict64(const ModelDev& m, int nf, double hf, const double* u, const double* rho,
                                const double* S, double* Ru, double* uH, double* Rd, cudaStream_t st) {
   const long long nc3 = (long long)(nf / 2) * (nf / 2) * (nf / 2);
-  const int g = grid_for(nc3, kThreads, 1 << 20);
-  MG_DISPATCH(m.kind, (k_residual_restrict64<KK><<<g, kThreads, 0, st>>>(m, nf, hf, u, rho, S, Ru, uH, Rd)));
+  const dim3 g = grid3d(nf / 2, nf / 2, nf / 2);
+  MG_DISPATCH(m.kind, (k_residual_restrict64<KK><<<g, k3dThreads, 0, st>>>(m, nf, hf, u, rho, S, Ru, uH, Rd)));
   MG_CUDA_TRY(cudaGetLastError());
   return MGGLAM_OK;
 }
@@ -379,7 +367,7 @@ int launch_fas_source64(const ModelDev& m, int nc, double hc, const double* Ru, 
                         cudaStream_t st) {
   const long long n3 = (long long)nc * nc * nc;
   const int g = grid_for(n3, kThreads, 1 << 20);
-  MG_DISPATCH(m.kind, (k_fas_source64<KK><<<g, kThreads, 0, st>>>(m, nc, hc, Ru, rho, S)));
+  MG_DISPATCH(m.kind, (k_fas_source64<KK><<<grid3d(nc, nc, nc), k3dThreads, 0, st>>>(m, nc, hc, Ru, rho, S)));
   MG_CUDA_TRY(cudaGetLastError());
   return MGGLAM_OK;
 }

@@ -395,15 +395,16 @@ static void launch_sweep_t(const MixedCtx& C, int l, const float* rho, cudaStrea
   k_sweep32<K, TJ, TK><<<grid, TJ * TK / 2, 0, st>>>(C.lf[l], L.n, chunk, L.e, L.e_alt, L.ub, rho, L.S32);
 }
 
-// The fused sweep is used on a level when its tile divides the mesh and it
-// yields enough CTAs to fill the GPU (a level with few CTAs would march its
-// planes serially); a caller-set chunk forces it wherever the tile divides.
+// The fused sweep runs only when the caller asks for it (sweep_chunk > 0) on a
+// level its tile divides.  Both kernels are bound by instruction issue on
+// GB300 (the local root costs ~120 instructions per cell); measured at 256^3,
+// one kernel per colour is ~8% faster than the fused pass, whose ring
+// recomputation and per-plane barriers cost more than the DRAM traffic they
+// save.
 static bool use_fused(const MixedCtx& C, int n) {
   const int tk = sweep_tile_k(n);
   if (!tk || n % 8 != 0) return false;
-  if (C.prm->sweep_chunk > 0) return true;
-  const long long ctas = (long long)(n / tk) * (n / 8) * ((n + C.chunk - 1) / C.chunk);
-  return ctas >= 4 * 152;
+  return C.prm->sweep_chunk > 0;
 }
 
 static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
@@ -602,7 +603,7 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
   if ((rc = get_workspace(N, MGGLAM_MIXED, prm->levels, &C.ws))) return rc;
   C.prm = prm;
   C.need_rho = (C.m.kind == KSYM) || (C.m.kind == KCQ && C.m.keep_exp);
-  C.chunk = prm->sweep_chunk > 0 ? prm->sweep_chunk : 16;
+  C.chunk = prm->sweep_chunk > 0 ? prm->sweep_chunk : 16;  // < 0: per-colour kernels only
   Workspace* ws = C.ws;
   for (int l = 0; l < ws->nlev; ++l) C.lf[l] = make_levelf(C.m, ws->lev[l].h);
   Level& F = ws->lev[0];

@@ -39,10 +39,17 @@ struct LevelF {
 // approximate reciprocal (about 1 ulp): the local solve's Newton steps tolerate it
 __device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
-// x^{1/3} for x > 0 (fast power intrinsic, a few ulp)
+// x^{1/3} for x > 0 (fast power intrinsic, ~1e-6 relative)
 __device__ __forceinline__ float fcbrt_pos(float x) { return __powf(x, 1.0f / 3.0f); }
 // sqrt(x) for x >= 0 as x / sqrt(x) with the fast reciprocal square root (x = 0 gives 0)
 __device__ __forceinline__ float fsqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
+// Newton polishing steps after the closed-form start of the local solve.  The
+// start inherits the single-precision cancellation in the polynomial's
+// coefficient p (-u^{n+1} + al K/u - B): in strongly screened cells its
+// relative error reaches ~1e-4, which two steps (error squared twice) remove;
+// with one step the mixed solve stalls near a 1e-10 relative residual.
+constexpr int kPolishSteps = 2;
 
 // Delta w = (u+e)^{n+1} - u^{n+1}, factored so that small e loses nothing.
 template <int K>
@@ -132,12 +139,11 @@ __device__ __forceinline__ float update_e_fast(const LevelF& f, float u, float e
     const float p = -fr_w<K>(u) + f.alK * frcp(u) - B;
     const float U = f.fr_s * fr_root_scaled_fast<K>(p * f.fr_is1);
     float x = U - u;
-    // two Newton steps on G(x) = Delta w(x) + al K x/(u(u+x)) - B (no cancellation
-    // in x): the closed form leaves x with an absolute error ~1e-6 u; the first
-    // step squares it, the second brings x to single-precision relative accuracy
+    // Newton steps on G(x) = Delta w(x) + al K x/(u(u+x)) - B (no cancellation
+    // in x) bring x to single-precision relative accuracy
     const float ru = frcp(u);
 #pragma unroll
-    for (int it = 0; it < 2; ++it) {
+    for (int it = 0; it < kPolishSteps; ++it) {
       const float Ue = u + x;
       const float rU = frcp(Ue);
       const float G = dw<K>(u, x) + f.alK * x * ru * rU - B;
@@ -156,7 +162,7 @@ __device__ __forceinline__ float update_e_fast(const LevelF& f, float u, float e
     const float U = sym_root_fast(p, q, u + e);
     float x = U - u;
 #pragma unroll
-    for (int it = 0; it < 2; ++it) {
+    for (int it = 0; it < kPolishSteps; ++it) {
       const float G = p * x + x * (3.f * u * u + 3.f * u * x + x * x) - B;
       const float Ue = u + x;
       const float dG = p + 3.f * Ue * Ue;
