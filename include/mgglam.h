@@ -196,6 +196,34 @@ int mgglam_gather_force(const mgglam_params* prm, double a, const double* field,
                         const float* pos, long long np, float* force, double prefactor,
                         void* stream);
 
+/*
+ * Adjoint of the solve: gradients of a scalar loss l(u*) with respect to the
+ * density and (f(R)) ln|f_R0|, given g = dl/du* at the solution u* of
+ * mgglam_solve_scalar (f(R) any n, or the symmetron).  With J = dN/du at u*
+ * (N the discrete operator of Eq. fR_eom_codeunit2 / Eq. sym_eom_code_unit),
+ * the adjoint field lambda solves J^T lambda = g, written as the symmetric
+ * screened-Poisson problem -c~^2 Delta_h lambda + m lambda = sigma g
+ * (f(R): m = K/((n+1)u^{n+2}), sigma = 1/((n+1)u^n); symmetron:
+ * m = a^2/(2xi^2)(rho a*^3/a^3 - 1 + 3u^2), sigma = -1), and is found by
+ * multigrid (FP64 residual, FP32 correction V-cycles with the forward solve's
+ * transfers; the coarse-level coefficients are rebuilt from u* on each call, no
+ * forward iterate is stored).  Then
+ *   grad_rho[i] = dl/d delta_i = -(dN_i/d delta_i) lambda_i   (delta = rho/mean - 1)
+ *   *grad_logfR0 = dl/d ln|f_R0| = sum_i lambda_i K/((n+1) u_i)   (f(R); 0 otherwise)
+ *   prm, a, rho, N   as passed to mgglam_solve_scalar (rho device float32)
+ *   field            device, N^3 float64, the converged u*
+ *   grad_field       device, N^3 float64, g = dl/du*
+ *   grad_rho         device, N^3 float64 output
+ *   grad_logfR0      host, may be NULL
+ *   tol              relative residual of the adjoint equation
+ * Returns as mgglam_solve_scalar; MGGLAM_ERR_ARG for the CQ model (not supported).
+ * The paper differentiates nothing; this serves gradient-based inference
+ * through the solver (the paper's emulator motivation, Sec. 6).
+ */
+int mgglam_solve_adjoint(const mgglam_params* prm, double a, const double* field, const float* rho, int N,
+                         const double* grad_field, double* grad_rho, double* grad_logfR0, double tol,
+                         mgglam_stats* stats, void* stream);
+
 /* ---- single-step entry points (one multigrid operation on one level, FP64) ----
  * These expose each step of the path for testing and for callers composing
  * their own cycles.  'n' is the level's mesh side, 'h' its cell size (the finest

@@ -233,3 +233,67 @@ def local_root(model: int, n: int, p: float, q: float, u_old: float = 1.0) -> fl
 
 def num_threads() -> int:
     return lib().or_num_threads()
+
+
+# ---------------------------------------------------------------------------
+# Adjoint (plain definition: the Jacobian assembled from the operator's
+# derivatives, J^T lambda = g solved by sparse LU)
+# ---------------------------------------------------------------------------
+
+def _neighbour_index(N):
+    idx = np.arange(N ** 3).reshape(N, N, N)
+    return [np.roll(idx, s, ax).ravel() for ax in range(3) for s in (1, -1)]
+
+
+def jacobian(p: Params, u, rho_n):
+    """J = dN/du of the fine-level operator at u (scipy CSR), rho_n the mean-1 density.
+
+    f(R) (Eq. fR_eom_codeunit2, w = u^{n+1}): dN_i/du_j = -c^2 (n+1) u_j^n for a
+    face neighbour j, dN_i/du_i = 6 c^2 (n+1) u_i^n + K/u_i^2.
+    symmetron (Eq. sym_eom_code_unit): dN_i/du_j = c^2, dN_i/du_i = -6 c^2 -
+    msym (rho a*^3/a^3 - 1 + 3 u_i^2).
+    """
+    import scipy.sparse as sp
+    u = _f64(u)
+    N = u.shape[0]
+    b = background(p, N)
+    n3 = N ** 3
+    rows = np.arange(n3)
+    nbrs = _neighbour_index(N)
+    uf = u.ravel()
+    if p.model == FR:
+        dwdu = (p.n + 1) * uf ** p.n
+        diag = 6 * b["c2"] * dwdu + b["K"] / uf ** 2
+        offv = [-b["c2"] * dwdu[nb] for nb in nbrs]   # column j = neighbour, value uses u_j
+    elif p.model == SYMMETRON:
+        r3 = (p.a_star / p.a) ** 3
+        diag = -6 * b["c2"] - b["msym"] * (_f64(rho_n).ravel() * r3 - 1 + 3 * uf ** 2)
+        offv = [np.full(n3, b["c2"]) for _ in nbrs]
+    else:
+        raise ValueError("adjoint: f(R) and symmetron only")
+    r = [rows] + [rows] * 6
+    c = [rows] + nbrs
+    v = [diag] + offv
+    return sp.csr_matrix((np.concatenate(v), (np.concatenate(r), np.concatenate(c))), shape=(n3, n3))
+
+
+def adjoint(p: Params, u, rho_n, g):
+    """lambda = J^{-T} g; returns (lambda, dl/d delta, dl/d ln|fR0|).
+
+    dl/d delta_i = -(dN_i/d delta_i) lambda_i: f(R) dN/d delta = Om/a; symmetron
+    dN/d delta = -msym (a*/a)^3 u.  dl/d ln|fR0| = -lambda . dN/d ln|fR0| with
+    dN_i/d ln|fR0| = -K/((n+1) u_i) (ubar scales as |fR0|^{1/(n+1)}).
+    """
+    import scipy.sparse.linalg as spla
+    u = _f64(u)
+    N = u.shape[0]
+    b = background(p, N)
+    J = jacobian(p, u, rho_n)
+    lam = spla.spsolve(J.T.tocsc(), _f64(g).ravel()).reshape(u.shape)
+    if p.model == FR:
+        gd = -(p.omega_m / p.a) * lam
+        gt = float(np.sum(lam * b["K"] / ((p.n + 1) * u)))
+    else:
+        gd = b["msym"] * (p.a_star / p.a) ** 3 * u * lam
+        gt = 0.0
+    return lam, gd, gt

@@ -97,7 +97,8 @@ _lib = None
 EXPORTS = ["mgglam_version", "mgglam_status_string", "mgglam_default_params", "mgglam_deposit_cic",
            "mgglam_solve_scalar", "mgglam_gather_force", "mgglam_smooth", "mgglam_residual",
            "mgglam_restrict", "mgglam_prolong_correct", "mgglam_release", "mgglam_profile_start",
-           "mgglam_profile_stop", "mgglam_launch_count", "mgglam_deposit_cic_static"]
+           "mgglam_profile_stop", "mgglam_launch_count", "mgglam_deposit_cic_static",
+           "mgglam_solve_adjoint"]
 
 
 class CKernelProfile(ctypes.Structure):
@@ -278,3 +279,28 @@ def deposit_cic_static(pos, N: int, rho=None, stream=None):
     _check("mgglam_deposit_cic_static", lib.mgglam_deposit_cic_static(_ptr(pos, torch.float32), pos.shape[0], N,
                                                                     _ptr(rho, torch.float32), _stream(stream)))
     return rho
+
+
+def solve_adjoint(prm: Params, a: float, field, rho, grad_field, tol: float = 1e-10, stream=None,
+                  allow_unconverged=False):
+    """Adjoint solve: returns (grad_rho [N^3 float64], dl/d ln|fR0|, Stats)."""
+    import torch
+    lib = load()
+    if not hasattr(lib, "_adjoint_bound"):
+        vp = ctypes.c_void_p
+        lib.mgglam_solve_adjoint.argtypes = [ctypes.POINTER(CParams), ctypes.c_double, vp, vp, ctypes.c_int, vp, vp,
+                                             ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                             ctypes.POINTER(CStats), vp]
+        lib.mgglam_solve_adjoint.restype = ctypes.c_int
+        lib._adjoint_bound = True
+    N = field.shape[0]
+    grad_rho = torch.empty_like(field)
+    gth = ctypes.c_double()
+    st = CStats()
+    rc = lib.mgglam_solve_adjoint(ctypes.byref(prm.c()), a, _ptr(field, torch.float64), _ptr(rho, torch.float32), N,
+                                  _ptr(grad_field, torch.float64), _ptr(grad_rho, torch.float64), ctypes.byref(gth),
+                                  tol, ctypes.byref(st), _stream(stream))
+    _check("mgglam_solve_adjoint", rc, (0, -4) if allow_unconverged else (0,))
+    nh = min(64, st.outer + 1)
+    return grad_rho, gth.value, Stats(st.cycles, st.outer, bool(st.converged), st.resid0, st.resid, st.seconds,
+                                      list(st.resid_hist[:nh]))

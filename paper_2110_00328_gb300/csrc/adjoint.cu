@@ -1,0 +1,440 @@
+// adjoint.cu -- gradients of a loss through the scalar-field solve.
+//
+// The solve defines u*(delta, theta) by N(u*; delta, theta) = 0 (the discrete
+// equations of Eq. fR_eom_codeunit2 / Eq. sym_eom_code_unit, theta =
+// ln|f_R0|).  For a loss l(u*) with g = dl/du*, the adjoint field lambda solves
+// J^T lambda = g with J = dN/du at u*, and
+//   dl/d delta = -(dN/d delta)^T lambda,   dl/d theta = -lambda . dN/d theta.
+// With Delta_h the 7-point Laplacian (symmetric) the transposed problem takes
+// one screened-Poisson form for both models,
+//   -kappa Delta_h lambda + m lambda = sigma g,
+//   f(R):      J = -c^2 Delta_h diag((n+1)u^n) + diag(K/u^2), so
+//              kappa = c~^2, m = K/((n+1)u^{n+2}), sigma = 1/((n+1)u^n);
+//   symmetron: J = c^2 Delta_h - diag(msym (rho a*^3/a^3 - 1 + 3u^2)), so
+//              kappa = c~^2, m = msym (rho a*^3/a^3 - 1 + 3u^2), sigma = -1;
+// m > 0 in both (the f(R) field is positive; in the symmetron's broken phase
+// rho a*^3/a^3 - 1 + 3u^2 = 2u^2 at the local minimum), so the operator is
+// symmetric positive definite and red-black Gauss-Seidel multigrid converges.
+//
+// Solver: FP64 outer residual r = sigma g - A lambda on the fine level, FP32
+// correction-scheme V-cycles for A e = r (the same cycle shape, restriction
+// and prolongation as the forward solve), lambda += e.  The coarse-level mass
+// is the 8-child mean of the fine mass, rebuilt from u* on every call (no state
+// of the forward V-cycles is kept).
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+#include <mutex>
+
+#include "mg_common.cuh"
+#include "mg_internal.h"
+
+namespace mg {
+
+// ---- per-cell coefficients from the converged field ----
+// m64, m32 = mass; rhs = sigma * g (FP64); also the density-gradient factor
+// gam (dl/d delta_i = gam_i lambda_i) and the theta factor tq (dl/d theta =
+// sum lambda_i tq_i).
+template <int K>
+__global__ void k_adj_setup(ModelDev m, int n, const double* __restrict__ u, const float* __restrict__ rho32,
+                            const double* __restrict__ rho_sum, const double* __restrict__ g,
+                            double* __restrict__ m64, float* __restrict__ m32, double* __restrict__ rhs,
+                            double* __restrict__ gam, double* __restrict__ tq) {
+  const int i = blockIdx.z, j = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const size_t t = cidx(n, i, j, k);
+  const double uc = u[t];
+  double mass, sigma, gm, tqv;
+  if constexpr (is_fr(K)) {
+    constexpr int np1 = K + 1;
+    double un = 1.0;  // u^n
+    for (int q = 0; q < K; ++q) un *= uc;
+    mass = m.K / ((double)np1 * un * uc * uc);
+    sigma = 1.0 / ((double)np1 * un);
+    gm = -m.om_a;                   // dN/d delta = Om/a
+    tqv = m.K / ((double)np1 * uc);  // -dN/d theta = K/((n+1)u)
+  } else {
+    const double r = (double)rho32[t] * ((double)n * n * n / *rho_sum);
+    mass = m.msym * (r * m.rat3 - 1.0 + 3.0 * uc * uc);
+    sigma = -1.0;
+    gm = m.msym * m.rat3 * uc;      // dN/d delta = -msym (a*/a)^3 u
+    tqv = 0.0;
+  }
+  m64[t] = mass;
+  m32[t] = (float)mass;
+  rhs[t] = sigma * g[t];
+  gam[t] = gm;
+  tq[t] = tqv;
+}
+
+// r = rhs - (-kappa Delta_h lambda + m lambda) on the fine level (FP64);
+// writes b = float(r) and per-block partial sums of r^2 and rhs^2.
+__global__ void k_adj_residual64(int n, double kappa, const double* __restrict__ lam, const double* __restrict__ m64,
+                                 const double* __restrict__ rhs, float* __restrict__ b,
+                                 double* __restrict__ partials, double* __restrict__ partials2) {
+  double acc = 0.0, acc2 = 0.0;
+  for (int r = blockIdx.x; r < n * n; r += gridDim.x) {
+    const int i = r / n, j = r - (r / n) * n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const size_t t = cidx(n, i, j, k);
+      const double L = lam[cidx(n, wrapi(i + 1, n), j, k)] + lam[cidx(n, wrapi(i - 1, n), j, k)] +
+                       lam[cidx(n, i, wrapi(j + 1, n), k)] + lam[cidx(n, i, wrapi(j - 1, n), k)] +
+                       lam[cidx(n, i, j, wrapi(k + 1, n))] + lam[cidx(n, i, j, wrapi(k - 1, n))];
+      const double lc = lam[t];
+      const double v = rhs[t] - (-kappa * (L - 6.0 * lc) + m64[t] * lc);
+      b[t] = (float)v;
+      acc += v * v;
+      acc2 += rhs[t] * rhs[t];
+    }
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  acc2 = block_sum(acc2);
+  if (threadIdx.x == 0) partials2[blockIdx.x] = acc2;
+}
+
+__global__ void k_adj_finalize(const double* __restrict__ p, const double* __restrict__ p2, int count,
+                               double* __restrict__ out) {
+  double a = 0.0, a2 = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    a += p[i];
+    a2 += p2[i];
+  }
+  a = block_sum(a);
+  if (threadIdx.x == 0) out[0] = a;
+  a2 = block_sum(a2);
+  if (threadIdx.x == 0) out[1] = a2;
+}
+
+// Red-black Gauss-Seidel on one colour: x_i = (b_i + kh sum_nb x) / (6 kh + m_i), kh = kappa/h^2.
+__global__ void __launch_bounds__(64) k_adj_smooth32(int n, float kh, float* __restrict__ x, const float* __restrict__ b,
+                                                     const float* __restrict__ m32, int parity) {
+  const int i = blockIdx.z, j = blockIdx.y;
+  const int kk = blockIdx.x * blockDim.x + threadIdx.x;
+  if (kk >= (n >> 1)) return;
+  const int k = 2 * kk + ((i + j + parity) & 1);
+  const size_t c = cidx(n, i, j, k);
+  const float L = x[cidx(n, wrapi(i + 1, n), j, k)] + x[cidx(n, wrapi(i - 1, n), j, k)] +
+                  x[cidx(n, i, wrapi(j + 1, n), k)] + x[cidx(n, i, wrapi(j - 1, n), k)] +
+                  x[cidx(n, i, j, wrapi(k + 1, n))] + x[cidx(n, i, j, wrapi(k - 1, n))];
+  x[c] = (b[c] + kh * L) / (6.f * kh + m32[c]);
+}
+
+__global__ void __launch_bounds__(512) k_adj_coarse32(int n, float kh, float* __restrict__ x,
+                                                      const float* __restrict__ b, const float* __restrict__ m32,
+                                                      int sweeps) {
+  const int n3 = n * n * n;
+  for (int s = 0; s < sweeps; ++s)
+    for (int parity = 0; parity < 2; ++parity) {
+      for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+        const int k = t % n, j = (t / n) % n, i = t / (n * n);
+        if (((i + j + k) & 1) != parity) continue;
+        const float L = x[cidx(n, wrapi(i + 1, n), j, k)] + x[cidx(n, wrapi(i - 1, n), j, k)] +
+                        x[cidx(n, i, wrapi(j + 1, n), k)] + x[cidx(n, i, wrapi(j - 1, n), k)] +
+                        x[cidx(n, i, j, wrapi(k + 1, n))] + x[cidx(n, i, j, wrapi(k - 1, n))];
+        x[t] = (b[t] + kh * L) / (6.f * kh + m32[t]);
+      }
+      __syncthreads();
+    }
+}
+
+// Coarse right-hand side: b^H = R (b - A x) over the 8 children; x^H = 0.
+__global__ void __launch_bounds__(64) k_adj_restrict_resid32(int nf, float kh, const float* __restrict__ x,
+                                                             const float* __restrict__ b,
+                                                             const float* __restrict__ m32, float* __restrict__ bH,
+                                                             float* __restrict__ xH) {
+  const int nc = nf >> 1;
+  const int I = blockIdx.z, J = blockIdx.y;
+  const int Kc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (Kc >= nc) return;
+  float s = 0.f;
+  for (int di = 0; di < 2; ++di)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int dk = 0; dk < 2; ++dk) {
+        const int i = 2 * I + di, j = 2 * J + dj, k = 2 * Kc + dk;
+        const size_t c = cidx(nf, i, j, k);
+        const float L = x[cidx(nf, wrapi(i + 1, nf), j, k)] + x[cidx(nf, wrapi(i - 1, nf), j, k)] +
+                        x[cidx(nf, i, wrapi(j + 1, nf), k)] + x[cidx(nf, i, wrapi(j - 1, nf), k)] +
+                        x[cidx(nf, i, j, wrapi(k + 1, nf))] + x[cidx(nf, i, j, wrapi(k - 1, nf))];
+        s += b[c] - (-kh * (L - 6.f * x[c]) + m32[c] * x[c]);
+      }
+  const size_t t = cidx(nc, I, J, Kc);
+  bH[t] = 0.125f * s;
+  xH[t] = 0.f;
+}
+
+// x^h += P x^H (27/9/3/1 weights).
+__global__ void __launch_bounds__(64) k_adj_prolong32(int nc, const float* __restrict__ xH, float* __restrict__ xf) {
+  const int nf = nc << 1;
+  const int i = blockIdx.z, j = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nf) return;
+  const int I = i >> 1, J = j >> 1, Kc = k >> 1;
+  const int I2 = wrapi(I + ((i & 1) ? 1 : -1), nc);
+  const int J2 = wrapi(J + ((j & 1) ? 1 : -1), nc);
+  const int K2 = wrapi(Kc + ((k & 1) ? 1 : -1), nc);
+#define XH(a, b, c) xH[cidx(nc, a, b, c)]
+  const float corr = (27.f * XH(I, J, Kc) + 9.f * (XH(I2, J, Kc) + XH(I, J2, Kc) + XH(I, J, K2)) +
+                      3.f * (XH(I2, J2, Kc) + XH(I2, J, K2) + XH(I, J2, K2)) + XH(I2, J2, K2)) *
+                     (1.f / 64.f);
+#undef XH
+  xf[cidx(nf, i, j, k)] += corr;
+}
+
+__global__ void __launch_bounds__(64) k_adj_restrict_m32(int nf, const float* __restrict__ fine,
+                                                         float* __restrict__ coarse) {
+  const int nc = nf >> 1;
+  const int I = blockIdx.z, J = blockIdx.y;
+  const int Kc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (Kc >= nc) return;
+  float s = 0.f;
+  for (int di = 0; di < 2; ++di)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int dk = 0; dk < 2; ++dk) s += fine[cidx(nf, 2 * I + di, 2 * J + dj, 2 * Kc + dk)];
+  coarse[cidx(nc, I, J, Kc)] = 0.125f * s;
+}
+
+// lambda += e; grad_rho = gam * lambda (after the last step); partial sums of lambda * tq.
+__global__ void k_adj_apply(long long n3, double* __restrict__ lam, const float* __restrict__ e) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
+       t += (long long)gridDim.x * blockDim.x)
+    lam[t] += (double)e[t];
+}
+
+__global__ void k_adj_outputs(long long n3, const double* __restrict__ lam, const double* __restrict__ gam,
+                              const double* __restrict__ tq, double* __restrict__ grad_rho,
+                              double* __restrict__ partials) {
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
+       t += (long long)gridDim.x * blockDim.x) {
+    grad_rho[t] = gam[t] * lam[t];
+    acc += lam[t] * tq[t];
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Scratch: one allocation per (device, N): FP64 lambda, m, rhs, gam, tq on the
+// fine level; FP32 x, b, m on every level; partial sums.
+// ---------------------------------------------------------------------------
+
+struct AdjWork {
+  int device = -1, N = 0, nlev = 0;
+  void* base = nullptr;
+  double *lam = nullptr, *m64 = nullptr, *rhs = nullptr, *gam = nullptr, *tq = nullptr;
+  double *partials = nullptr, *partials2 = nullptr, *scal = nullptr, *h_scal = nullptr;
+  int n[kMaxLevels];
+  float *x[kMaxLevels], *b[kMaxLevels], *m32[kMaxLevels];
+};
+
+static std::mutex g_adj_mu;
+static AdjWork* g_adj[32];
+static int g_nadj = 0;
+
+static int adj_work(int N, int levels, AdjWork** out) {
+  int dev = 0;
+  MG_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_adj_mu);
+  const int nlev = count_levels(N, levels);
+  for (int i = 0; i < g_nadj; ++i)
+    if (g_adj[i]->device == dev && g_adj[i]->N == N && g_adj[i]->nlev == nlev) {
+      *out = g_adj[i];
+      return MGGLAM_OK;
+    }
+  if (g_nadj >= 32) return MGGLAM_ERR_OOM;
+  AdjWork* w = new AdjWork();
+  w->device = dev;
+  w->N = N;
+  w->nlev = nlev;
+  const size_t n3 = (size_t)N * N * N;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
+  const size_t o_lam = take(n3 * 8), o_m = take(n3 * 8), o_rhs = take(n3 * 8), o_gam = take(n3 * 8),
+               o_tq = take(n3 * 8), o_p = take(kMaxReduceBlocks * 8), o_p2 = take(kMaxReduceBlocks * 8),
+               o_s = take(64);
+  size_t ox[kMaxLevels], ob[kMaxLevels], om[kMaxLevels];
+  for (int l = 0, nn = N; l < nlev; ++l, nn /= 2) {
+    const size_t c = (size_t)nn * nn * nn;
+    w->n[l] = nn;
+    ox[l] = take(c * 4);
+    ob[l] = take(c * 4);
+    om[l] = take(c * 4);
+  }
+  if (cudaMalloc(&w->base, off) != cudaSuccess) {
+    cudaGetLastError();
+    delete w;
+    return MGGLAM_ERR_OOM;
+  }
+  if (cudaMallocHost((void**)&w->h_scal, 64) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(w->base);
+    delete w;
+    return MGGLAM_ERR_OOM;
+  }
+  char* b = (char*)w->base;
+  w->lam = (double*)(b + o_lam);
+  w->m64 = (double*)(b + o_m);
+  w->rhs = (double*)(b + o_rhs);
+  w->gam = (double*)(b + o_gam);
+  w->tq = (double*)(b + o_tq);
+  w->partials = (double*)(b + o_p);
+  w->partials2 = (double*)(b + o_p2);
+  w->scal = (double*)(b + o_s);
+  for (int l = 0; l < nlev; ++l) {
+    w->x[l] = (float*)(b + ox[l]);
+    w->b[l] = (float*)(b + ob[l]);
+    w->m32[l] = (float*)(b + om[l]);
+  }
+  g_adj[g_nadj++] = w;
+  *out = w;
+  return MGGLAM_OK;
+}
+
+void release_adjoint_work() {
+  std::lock_guard<std::mutex> lk(g_adj_mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int keep = 0;
+  for (int i = 0; i < g_nadj; ++i) {
+    if (g_adj[i]->device == dev) {
+      cudaFree(g_adj[i]->base);
+      cudaFreeHost(g_adj[i]->h_scal);
+      delete g_adj[i];
+    } else {
+      g_adj[keep++] = g_adj[i];
+    }
+  }
+  g_nadj = keep;
+}
+
+static dim3 grid_k(int n_k, int n_j, int n_i) { return dim3((n_k + 63) / 64, n_j, n_i); }
+
+static void adj_vcycle(AdjWork* w, int l, double kappa, const mgglam_params* prm, cudaStream_t st) {
+  const int n = w->n[l];
+  const float kh = (float)(kappa / ((double)(1 << l) * (double)(1 << l)));
+  if (l == w->nlev - 1) {
+    if ((long long)n * n * n <= 4096) {
+      k_adj_coarse32<<<1, 512, 0, st>>>(n, kh, w->x[l], w->b[l], w->m32[l], prm->coarse_sweeps);
+      note_launch(1);
+    } else {
+      for (int s = 0; s < prm->coarse_sweeps; ++s)
+        for (int par = 0; par < 2; ++par) {
+          k_adj_smooth32<<<grid_k(n / 2, n, n), 64, 0, st>>>(n, kh, w->x[l], w->b[l], w->m32[l], par);
+          note_launch(1);
+        }
+    }
+    return;
+  }
+  for (int s = 0; s < prm->nu1; ++s)
+    for (int par = 0; par < 2; ++par) {
+      k_adj_smooth32<<<grid_k(n / 2, n, n), 64, 0, st>>>(n, kh, w->x[l], w->b[l], w->m32[l], par);
+      note_launch(1);
+    }
+  const int nc = w->n[l + 1];
+  k_adj_restrict_resid32<<<grid_k(nc, nc, nc), 64, 0, st>>>(n, kh, w->x[l], w->b[l], w->m32[l], w->b[l + 1],
+                                                             w->x[l + 1]);
+  note_launch(1);
+  adj_vcycle(w, l + 1, kappa, prm, st);
+  k_adj_prolong32<<<grid_k(n, n, n), 64, 0, st>>>(nc, w->x[l + 1], w->x[l]);
+  note_launch(1);
+  for (int s = 0; s < prm->nu2; ++s)
+    for (int par = 0; par < 2; ++par) {
+      k_adj_smooth32<<<grid_k(n / 2, n, n), 64, 0, st>>>(n, kh, w->x[l], w->b[l], w->m32[l], par);
+      note_launch(1);
+    }
+}
+
+int solve_adjoint(const mgglam_params* prm, double a, const double* field, const float* rho, int N,
+                  const double* grad_field, double* grad_rho, double* grad_theta, double tol, mgglam_stats* stats,
+                  cudaStream_t st) {
+  auto t0 = std::chrono::steady_clock::now();
+  ModelDev m;
+  int rc = make_model(prm, a, N, &m);
+  if (rc) return rc;
+  if (!(is_fr(m.kind) || m.kind == KSYM)) return MGGLAM_ERR_ARG;
+  AdjWork* w = nullptr;
+  if ((rc = adj_work(N, prm->levels, &w))) return rc;
+  Workspace* ws = nullptr;  // for the density mean scratch
+  if ((rc = get_workspace(4, MGGLAM_FP64, 1, &ws))) return rc;
+  const long long n3 = (long long)N * N * N;
+  if ((rc = launch_density_mean(rho, (size_t)n3, ws->partials, ws->scalars + SC_MEAN, st))) return rc;
+  const dim3 gf = grid_k(N, N, N);
+  switch (m.kind) {
+    case KFR0: k_adj_setup<KFR0><<<gf, 64, 0, st>>>(m, N, field, rho, ws->scalars + SC_MEAN, grad_field, w->m64, w->m32[0], w->rhs, w->gam, w->tq); break;
+    case KFR1: k_adj_setup<KFR1><<<gf, 64, 0, st>>>(m, N, field, rho, ws->scalars + SC_MEAN, grad_field, w->m64, w->m32[0], w->rhs, w->gam, w->tq); break;
+    case KFR2: k_adj_setup<KFR2><<<gf, 64, 0, st>>>(m, N, field, rho, ws->scalars + SC_MEAN, grad_field, w->m64, w->m32[0], w->rhs, w->gam, w->tq); break;
+    default: k_adj_setup<KSYM><<<gf, 64, 0, st>>>(m, N, field, rho, ws->scalars + SC_MEAN, grad_field, w->m64, w->m32[0], w->rhs, w->gam, w->tq); break;
+  }
+  note_launch(1);
+  for (int l = 1; l < w->nlev; ++l) {
+    k_adj_restrict_m32<<<grid_k(w->n[l], w->n[l], w->n[l]), 64, 0, st>>>(w->n[l - 1], w->m32[l - 1], w->m32[l]);
+    note_launch(1);
+  }
+  MG_CUDA_TRY(cudaMemsetAsync(w->lam, 0, (size_t)n3 * 8, st));
+  const double kappa = m.c2;
+  const int gr = N * N < 2048 ? N * N : 2048;
+  const int bt = N >= 256 ? 256 : (N <= 32 ? 32 : ((N + 31) / 32) * 32);
+  auto residual = [&]() -> int {
+    k_adj_residual64<<<gr, bt, 0, st>>>(N, kappa, w->lam, w->m64, w->rhs, w->b[0], w->partials, w->partials2);
+    k_adj_finalize<<<1, 1024, 0, st>>>(w->partials, w->partials2, gr, w->scal);
+    note_launch(2);
+    MG_CUDA_TRY(cudaMemcpyAsync(w->h_scal, w->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MG_CUDA_TRY(cudaStreamSynchronize(st));
+    MG_CUDA_TRY(cudaGetLastError());
+    return MGGLAM_OK;
+  };
+  if ((rc = residual())) return rc;
+  const double bnorm = sqrt(w->h_scal[1] / (double)n3);
+  const double snorm = bnorm > 0.0 ? bnorm : 1.0;
+  double eps = sqrt(w->h_scal[0] / (double)n3) / snorm;
+  mgglam_stats local;
+  mgglam_stats* S = stats ? stats : &local;
+  memset(S, 0, sizeof(*S));
+  S->resid0 = eps;
+  S->resid_hist[0] = eps;
+  int cyc = 0, outer = 0, nh = 1;
+  const int inner = prm->inner_cycles > 0 ? prm->inner_cycles : 3;
+  int status = MGGLAM_OK;
+  while (!(eps <= tol) && cyc < prm->max_cycles) {
+    if (!isfinite(eps)) { status = MGGLAM_ERR_NONFINITE; break; }
+    MG_CUDA_TRY(cudaMemsetAsync(w->x[0], 0, (size_t)n3 * 4, st));
+    for (int c = 0; c < inner && cyc < prm->max_cycles; ++c, ++cyc) adj_vcycle(w, 0, kappa, prm, st);
+    k_adj_apply<<<grid_for(n3, kThreads, 1 << 20), kThreads, 0, st>>>(n3, w->lam, w->x[0]);
+    note_launch(1);
+    ++outer;
+    if ((rc = residual())) return rc;
+    eps = sqrt(w->h_scal[0] / (double)n3) / snorm;
+    if (nh < 64) S->resid_hist[nh++] = eps;
+  }
+  const int go = grid_for(n3);
+  k_adj_outputs<<<go, kThreads, 0, st>>>(n3, w->lam, w->gam, w->tq, grad_rho, w->partials);
+  k_adj_finalize<<<1, 1024, 0, st>>>(w->partials, w->partials, go, w->scal);
+  note_launch(2);
+  MG_CUDA_TRY(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+  MG_CUDA_TRY(cudaStreamSynchronize(st));
+  MG_CUDA_TRY(cudaGetLastError());
+  if (grad_theta) *grad_theta = w->h_scal[0];
+  if (status == MGGLAM_OK && !isfinite(eps)) status = MGGLAM_ERR_NONFINITE;
+  S->cycles = cyc;
+  S->outer = outer;
+  S->resid = eps;
+  S->converged = eps <= tol;
+  S->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (status == MGGLAM_OK && !S->converged) status = MGGLAM_ERR_NOT_CONVERGED;
+  return status;
+}
+
+}  // namespace mg
+
+extern "C" int mgglam_solve_adjoint(const mgglam_params* prm, double a, const double* field, const float* rho,
+                                    int N, const double* grad_field, double* grad_rho, double* grad_logfR0,
+                                    double tol, mgglam_stats* stats, void* stream) {
+  if (!prm || !field || !rho || !grad_field || !grad_rho || !(tol >= 0.0)) return MGGLAM_ERR_ARG;
+  if (N < 4 || N > 2048 || N % 2) return MGGLAM_ERR_SHAPE;
+  if (prm->model != MGGLAM_FR && prm->model != MGGLAM_SYMMETRON) return MGGLAM_ERR_ARG;
+  return mg::solve_adjoint(prm, a, field, rho, N, grad_field, grad_rho, grad_logfR0, tol, stats,
+                           (cudaStream_t)stream);
+}

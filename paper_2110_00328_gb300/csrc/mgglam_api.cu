@@ -336,6 +336,7 @@ int mgglam_prolong_correct(const mgglam_params* prm, int n, const double* uH, co
 int mgglam_release(void) {
   cudaError_t e = cudaDeviceSynchronize();
   release_workspaces();
+  release_adjoint_work();
   return e == cudaSuccess ? MGGLAM_OK : MGGLAM_ERR_CUDA;
 }
 
