@@ -187,6 +187,135 @@ def run_reference(args) -> None:
 
 
 # ---------------------------------------------------------------------------
+# Extra measurements: adjoint at 512^3, batch of 48 uneven solves
+# ---------------------------------------------------------------------------
+
+def batch_workload(seed: int = 4, count: int = 48):
+    """48 solves: N from {64, 96, 128, 192} (L = N Mpc/h), f(R) n=1 with |fR0|
+    log-uniform in [1e-7, 1e-4] or symmetron (a* = 0.5, beta* = 1, range log-uniform
+    in [0.5, 3] Mpc/h), 50/50; lognormal densities with sigma_g ~ U[0.8, 2.0], seed 100 + i."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        N = int(rng.choice([64, 96, 128, 192]))
+        sg = float(rng.uniform(0.8, 2.0))
+        if rng.random() < 0.5:
+            kw = dict(model=0, n=1, fR0_abs=float(10 ** rng.uniform(-7, -4)), box=float(N))
+        else:
+            rng_mpch = float(10 ** rng.uniform(np.log10(0.5), np.log10(3.0)))
+            kw = dict(model=1, a_star=0.5, beta_star=1.0, xi=rng_mpch * 100.0 / 299792.458, box=float(N))
+        out.append((N, sg, 100 + i, kw))
+    return out
+
+
+def run_batch_extra(mg, torch, dev, tol=TOL) -> dict:
+    from paper_2110_00328_gb300 import inputs
+    work = batch_workload()
+    prms = [mg.Params(**kw, max_cycles=60) for (_, _, _, kw) in work]
+    rhos = [torch.from_numpy(inputs.lognormal_density(N, sg, seed).astype(np.float32)).to(dev)
+            for (N, sg, seed, _) in work]
+    fields = [torch.empty((N,) * 3, dtype=torch.float64, device=dev) for (N, _, _, _) in work]
+    cells = sum(N ** 3 for (N, _, _, _) in work)
+
+    def reset():
+        for f in fields:
+            f.fill_(float("nan"))
+        torch.cuda.synchronize()
+
+    def timed(fn, reps):
+        best = []
+        for _ in range(reps):
+            reset()
+            t0 = time.perf_counter()
+            out = fn()
+            torch.cuda.synchronize()
+            best.append((time.perf_counter() - t0) * 1e3)
+        return min(best), out
+
+    reset()
+    mg.solve_batch(prms, [1.0] * len(work), rhos, fields, tol)  # allocation, autotune, graph capture
+    t_batch, stats = timed(lambda: mg.solve_batch(prms, [1.0] * len(work), rhos, fields, tol), 2)
+
+    def seq(precision):
+        out = []
+        for p, r, f in zip(prms, rhos, fields):
+            q = mg.Params(**{**p.__dict__, "precision": precision})
+            out.append(mg.solve_scalar(q, 1.0, r, f, tol, allow_unconverged=True))
+        return out
+
+    seq(mg.MIXED)  # workspaces for every mesh size
+    t_seq_mixed, st_mixed = timed(lambda: seq(mg.MIXED), 1)
+    t_seq_fp64, st_fp64 = timed(lambda: seq(mg.FP64), 1)
+    return {"workload": "48 solves, N in {64,96,128,192}, f(R) n=1 |fR0| log-U[1e-7,1e-4] / symmetron range "
+                        "log-U[0.5,3] Mpc/h, lognormal sigma_g U[0.8,2], seeds 4 and 100+i, tol 1e-8",
+            "cells": int(cells), "batched_ms": round(t_batch, 2),
+            "sequential_mixed_ms": round(t_seq_mixed, 2), "sequential_fp64_ms": round(t_seq_fp64, 2),
+            "speedup_vs_sequential_mixed": round(t_seq_mixed / t_batch, 2),
+            "speedup_vs_sequential_fp64": round(t_seq_fp64 / t_batch, 2),
+            "all_converged": bool(all(s.converged for s in stats)),
+            "max_resid": float(max(s.resid for s in stats)),
+            "max_cycles": int(max(s.cycles for s in stats)),
+            "fp64_all_converged": bool(all(s.converged for s in st_fp64))}
+
+
+def run_adjoint_extra(mg, torch, dev) -> dict:
+    """Gradient of sum_b log P_F(k_b) (fifth-force power, 32 log bins) w.r.t. the
+    density and ln|fR0| at 512^3 (f(R) n=1, |fR0| = 1e-5, box 512 Mpc/h, lognormal
+    sigma_g = 1.5, seed 3), timed, and checked against central differences (step 1e-3)."""
+    import math
+    from paper_2110_00328_gb300 import autograd as ag
+    from paper_2110_00328_gb300 import inputs
+    N = 512
+    prm = mg.Params(model=0, n=1, fR0_abs=1e-5, box=512.0, precision=mg.MIXED, max_cycles=80)
+    rho0 = torch.from_numpy(inputs.lognormal_density(N, 1.5, seed=3).astype(np.float32)).to(dev)
+    t0v = math.log(1e-5)
+    tol = 1e-10
+
+    def fwd_bwd():
+        rho = rho0.clone().requires_grad_(True)
+        th = torch.tensor(t0v, dtype=torch.float64, requires_grad=True)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        u = ag.solve(rho, th, prm, 1.0, tol)
+        loss = ag.fifth_force_power_loss(u, prm)
+        torch.cuda.synchronize()
+        b = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize()
+        c = time.perf_counter()
+        return rho.grad.double(), float(th.grad), (b - a) * 1e3, (c - b) * 1e3
+
+    fwd_bwd()
+    g_rho, g_th, f_ms, b_ms = fwd_bwd()
+
+    def L(r, t):
+        with torch.no_grad():
+            return float(ag.fifth_force_power_loss(ag.solve(r, torch.tensor(t, dtype=torch.float64), prm, 1.0, tol),
+                                                   prm))
+
+    h = 1e-3
+    fdt = (L(rho0, t0v + h) - L(rho0, t0v - h)) / (2 * h)
+    v = torch.from_numpy(np.random.default_rng(5).normal(size=(N, N, N))).to(dev) * rho0.double()
+    rp, rm = (rho0.double() + h * v).float(), (rho0.double() - h * v).float()
+    v_eff = (rp.double() - rm.double()) / (2 * h)
+    fdd = (L(rp, t0v) - L(rm, t0v)) / (2 * h)
+    adj = float((g_rho * v_eff).sum())
+    # the plain FP64 forward solve on the same input, for comparison
+    p64 = mg.Params(**{**prm.__dict__, "precision": mg.FP64})
+    f64 = torch.full((N,) * 3, float("nan"), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    mg.solve_scalar(p64, 1.0, rho0, f64, tol, allow_unconverged=True)
+    torch.cuda.synchronize()
+    fp64_ms = (time.perf_counter() - a) * 1e3
+    return {"workload": "fR n=1 |fR0|=1e-5 512^3 box 512 lognormal sigma_g 1.5 seed 3; loss sum_b log P_F(k_b), "
+                        "32 log bins; tol 1e-10",
+            "forward_ms": round(f_ms, 2), "backward_ms": round(b_ms, 2), "plain_fp64_forward_ms": round(fp64_ms, 2),
+            "grad_logfR0": g_th, "fd_logfR0": fdt, "rel_err_logfR0": abs(g_th - fdt) / abs(fdt),
+            "grad_dir": adj, "fd_dir": fdd, "rel_err_density_dir": abs(adj - fdd) / abs(fdd)}
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -326,6 +455,9 @@ def run_ours(args) -> None:
                 "d2h_bytes_per_step": int(force_host.numel() * 4), "ms_per_step": round(e2e_total / len(e2e_ms), 3)},
         "clocks": clk,
     }
+    if not args.no_extras:
+        line["batch"] = run_batch_extra(mg, torch, dev)
+        line["adjoint"] = run_adjoint_extra(mg, torch, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = run_oracle_baseline(pos_h)
     print(json.dumps(line), flush=True)
@@ -346,6 +478,7 @@ def main():
     ap.add_argument("--nu1", type=int, default=2, help="pre-smoothing sweeps")
     ap.add_argument("--nu2", type=int, default=1, help="post-smoothing sweeps (2+1 gives the shortest time to 1e-8 here)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batch and adjoint measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -224,6 +224,32 @@ int mgglam_solve_adjoint(const mgglam_params* prm, double a, const double* field
                          const double* grad_field, double* grad_rho, double* grad_logfR0, double tol,
                          mgglam_stats* stats, void* stream);
 
+/*
+ * Many independent solves at once (an emulator's parameter grid, several
+ * realisations): each solve s has its own parameters prm[s] (model, f(R) n,
+ * |f_R0|, symmetron parameters, box), scale factor a[s], density rho[s] and mesh
+ * N[s]; every solve is the mixed-precision solve of mgglam_solve_scalar
+ * (prm[s].precision is ignored), carried to tol.  The solves advance in lock
+ * step: each multigrid phase is one kernel launch over the blocks of all solves
+ * that take part in it, one V-cycle of the batch is replayed as a CUDA graph,
+ * and converged solves drop out (their blocks exit at once).
+ *   count   number of solves (>= 1)
+ *   prm     host array [count]; nu1, nu2, coarse_sweeps must agree across solves;
+ *           inner_cycles and max_cycles are taken from prm[0]
+ *   a       host array [count]
+ *   rho     host array [count] of device float32 N[s]^3 pointers
+ *   N       host array [count]; each a multiple of 32, 32..2048
+ *   field   host array [count] of device float64 N[s]^3 pointers (in/out as for
+ *           mgglam_solve_scalar)
+ *   stats   host array [count] or NULL (seconds = the whole batch's time)
+ * Scratch for a batch is cached by its list of mesh sizes and levels.  Returns
+ * MGGLAM_OK when every solve converged, else MGGLAM_ERR_NOT_CONVERGED /
+ * MGGLAM_ERR_NONFINITE (per-solve outcome in stats), or an argument error.
+ * Not in the paper (it runs independent realisations with MPI, Sec. 3.1).
+ */
+int mgglam_solve_batch(int count, const mgglam_params* prm, const double* a, const float* const* rho, const int* N,
+                       double* const* field, double tol, mgglam_stats* stats, void* stream);
+
 /* ---- single-step entry points (one multigrid operation on one level, FP64) ----
  * These expose each step of the path for testing and for callers composing
  * their own cycles.  'n' is the level's mesh side, 'h' its cell size (the finest

@@ -98,7 +98,7 @@ EXPORTS = ["mgglam_version", "mgglam_status_string", "mgglam_default_params", "m
            "mgglam_solve_scalar", "mgglam_gather_force", "mgglam_smooth", "mgglam_residual",
            "mgglam_restrict", "mgglam_prolong_correct", "mgglam_release", "mgglam_profile_start",
            "mgglam_profile_stop", "mgglam_launch_count", "mgglam_deposit_cic_static",
-           "mgglam_solve_adjoint"]
+           "mgglam_solve_adjoint", "mgglam_solve_batch"]
 
 
 class CKernelProfile(ctypes.Structure):
@@ -304,3 +304,29 @@ def solve_adjoint(prm: Params, a: float, field, rho, grad_field, tol: float = 1e
     nh = min(64, st.outer + 1)
     return grad_rho, gth.value, Stats(st.cycles, st.outer, bool(st.converged), st.resid0, st.resid, st.seconds,
                                       list(st.resid_hist[:nh]))
+
+
+def solve_batch(prms, a_list, rhos, fields, tol: float, stream=None, allow_unconverged=False):
+    """Batched solve: prms, a_list, rhos (float32 N^3 CUDA), fields (float64 N^3 CUDA) per solve.
+
+    Returns a list of Stats (one per solve)."""
+    import torch
+    lib = load()
+    if not hasattr(lib, "_batch_bound"):
+        vp = ctypes.c_void_p
+        lib.mgglam_solve_batch.argtypes = [ctypes.c_int, ctypes.POINTER(CParams), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp),
+                                           ctypes.c_double, ctypes.POINTER(CStats), vp]
+        lib.mgglam_solve_batch.restype = ctypes.c_int
+        lib._batch_bound = True
+    n = len(prms)
+    cp = (CParams * n)(*[p.c() for p in prms])
+    ca = (ctypes.c_double * n)(*a_list)
+    cr = (ctypes.c_void_p * n)(*[_ptr(r, torch.float32).value for r in rhos])
+    cn = (ctypes.c_int * n)(*[r.shape[0] for r in rhos])
+    cf = (ctypes.c_void_p * n)(*[_ptr(f, torch.float64).value for f in fields])
+    st = (CStats * n)()
+    rc = lib.mgglam_solve_batch(n, cp, ca, cr, cn, cf, tol, st, _stream(stream))
+    _check("mgglam_solve_batch", rc, (0, -4) if allow_unconverged else (0,))
+    return [Stats(s.cycles, s.outer, bool(s.converged), s.resid0, s.resid, s.seconds,
+                  list(s.resid_hist[:min(64, s.outer + 1)])) for s in st]

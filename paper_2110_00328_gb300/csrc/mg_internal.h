@@ -109,8 +109,9 @@ int solve_fp64(const mgglam_params* prm, double a, const float* rho, int N, doub
 int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, double* field,
                 double tol, mgglam_stats* stats, cudaStream_t st);
 
-// ---- adjoint (adjoint.cu) ----
+// ---- adjoint (adjoint.cu), batch (batch.cu) ----
 void release_adjoint_work();
+void release_batches();
 
 // ---- particles (particles.cu) ----
 int deposit_cic(const float* pos, long long np, int N, float* rho, cudaStream_t st);

@@ -337,6 +337,7 @@ int mgglam_release(void) {
   cudaError_t e = cudaDeviceSynchronize();
   release_workspaces();
   release_adjoint_work();
+  release_batches();
   return e == cudaSuccess ? MGGLAM_OK : MGGLAM_ERR_CUDA;
 }
 
