@@ -455,8 +455,12 @@ def run_ours(args) -> None:
                 "d2h_bytes_per_step": int(force_host.numel() * 4), "ms_per_step": round(e2e_total / len(e2e_ms), 3)},
         "clocks": clk,
     }
-    if not args.no_extras:
+    extras = {"all": ("batch", "adjoint"), "none": ()}.get(args.extras, (args.extras,))
+    if args.no_extras:
+        extras = ()
+    if "batch" in extras:
         line["batch"] = run_batch_extra(mg, torch, dev)
+    if "adjoint" in extras:
         line["adjoint"] = run_adjoint_extra(mg, torch, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = run_oracle_baseline(pos_h)
@@ -478,7 +482,9 @@ def main():
     ap.add_argument("--nu1", type=int, default=2, help="pre-smoothing sweeps")
     ap.add_argument("--nu2", type=int, default=1, help="post-smoothing sweeps (2+1 gives the shortest time to 1e-8 here)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batch and adjoint measurements")
+    ap.add_argument("--extras", choices=["all", "none", "batch", "adjoint"], default="all",
+                    help="extra measurements after the main step: the 48-solve batch, the 512^3 adjoint")
+    ap.add_argument("--no-extras", action="store_true", help="same as --extras none")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

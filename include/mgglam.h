@@ -83,7 +83,14 @@ typedef struct {
   int sweep_chunk;    /* MIXED: <= 0 (default): one smoothing kernel per colour on every
                          level; > 0: the fused two-colour sweep kernel, with this many
                          planes per CTA, on every level whose tile divides the mesh */
-  int reserved[3];
+  int sweep_slab;     /* MIXED, per-colour kernels on levels of side >= 256: planes per slab
+                         of the L2-blocked sweep (first colour on a slab, then the second
+                         colour one plane behind it, while the slab is still in L2; the
+                         result equals the unblocked sweep bit for bit).  <= 0 (default):
+                         one pass per colour (measured faster at 256^3: the kernel is bound
+                         by instruction issue, and the extra launches cost more than the
+                         DRAM traffic they save) */
+  int reserved[2];
 } mgglam_params;
 
 /* Per-solve statistics.  resid values are the relative global residual:

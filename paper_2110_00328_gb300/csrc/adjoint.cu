@@ -402,7 +402,7 @@ int solve_adjoint(const mgglam_params* prm, double a, const double* field, const
     if (!isfinite(eps)) { status = MGGLAM_ERR_NONFINITE; break; }
     MG_CUDA_TRY(cudaMemsetAsync(w->x[0], 0, (size_t)n3 * 4, st));
     for (int c = 0; c < inner && cyc < prm->max_cycles; ++c, ++cyc) adj_vcycle(w, 0, kappa, prm, st);
-    k_adj_apply<<<grid_for(n3, kThreads, 1 << 20), kThreads, 0, st>>>(n3, w->lam, w->x[0]);
+    k_adj_apply<<<stream_grid(n3), kThreads, 0, st>>>(n3, w->lam, w->x[0]);
     note_launch(1);
     ++outer;
     if ((rc = residual())) return rc;

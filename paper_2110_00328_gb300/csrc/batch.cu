@@ -616,17 +616,17 @@ int solve_batch(int count, const mgglam_params* prm, const double* a, const floa
     const Batch::S& v = B->sv[s];
     const long long n3 = (long long)v.N * v.N * v.N;
     if ((rc = launch_density_mean(rho[s], (size_t)n3, B->partials, B->rmean + s, st))) return rc;
-    MG_BDISPATCH(models[s].kind, (k_src64<KK><<<grid_for(n3, kThreads, 1 << 20), kThreads, 0, st>>>(
+    MG_BDISPATCH(models[s].kind, (k_src64<KK><<<stream_grid(n3), kThreads, 0, st>>>(
                                      models[s], rho[s], n3, B->rmean + s, v.src64)));
-    k_density_norm32<<<grid_for(n3, kThreads, 1 << 20), kThreads, 0, st>>>(rho[s], n3, B->rmean + s, v.rho32[0]);
+    k_density_norm32<<<stream_grid(n3), kThreads, 0, st>>>(rho[s], n3, B->rmean + s, v.rho32[0]);
     for (int l = 1; l < v.nlev; ++l) {
       const int nc = v.N >> l;
       k_restrict32<<<dim3((nc + 63) / 64, nc, nc), 64, 0, st>>>(v.N >> (l - 1), v.rho32[l - 1], v.rho32[l]);
     }
     if ((rc = launch_init_background(models[s], field[s], (size_t)n3, st))) return rc;
-    MG_BDISPATCH(models[s].kind, (k_src_sumsq32<KK><<<grid_for(n3), kThreads, 0, st>>>(
+    MG_BDISPATCH(models[s].kind, (k_src_sumsq32<KK><<<stream_grid(n3), kThreads, 0, st>>>(
                                      models[s], rho[s], n3, B->rmean + s, B->partials)));
-    k_finalize_sum32<<<1, 1024, 0, st>>>(B->partials, grid_for(n3), B->ssum + s);
+    k_finalize_sum32<<<1, 1024, 0, st>>>(B->partials, stream_grid(n3), B->ssum + s);
     MG_CUDA_TRY(cudaMemsetAsync(v.e[0], 0, (size_t)n3 * 4, st));
     note_launch(5 + v.nlev);
   }

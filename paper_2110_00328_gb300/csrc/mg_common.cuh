@@ -10,6 +10,10 @@ namespace mg {
 
 constexpr int kThreads = 256;
 constexpr int kMaxReduceBlocks = 8192;  // size of the partial-sum array
+// Grid cap of the grid-stride elementwise kernels: about two waves of
+// 256-thread blocks on 152 SMs, so that per-thread setup (a division, a
+// scalar read) is paid once per ~30 cells, not once per cell.
+constexpr int kStreamBlocks = 2432;
 
 __host__ __device__ __forceinline__ size_t cidx(int n, int i, int j, int k) {
   return ((size_t)i * n + j) * n + k;
@@ -40,5 +44,23 @@ inline int grid_for(long long work, int threads = kThreads, int cap = kMaxReduce
   if (g > cap) g = cap;
   return (int)g;
 }
+
+// Grid for a grid-stride elementwise kernel.
+inline int stream_grid(long long work) { return grid_for(work, kThreads, kStreamBlocks); }
+
+// Error-free accumulation of single-precision values (Knuth's two-sum): after
+// any number of steps hi + lo equals the exact sum up to the rounding of lo,
+// i.e. to ~2^-46 relative, without double-precision arithmetic.
+struct FloatFloat {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 
 }  // namespace mg

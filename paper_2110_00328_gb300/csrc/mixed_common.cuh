@@ -45,7 +45,7 @@ static inline LevelF make_levelf(const ModelDev& m, double h) {
 template <int K>
 __device__ __forceinline__ float local_M(const LevelF& f, float u, float e, float rho, float Lnb) {
   if constexpr (is_fr(K)) {
-    return -f.c2_h2 * (Lnb - 6.f * dw<K>(u, e)) + f.K * e / (u * (u + e));
+    return -f.c2_h2 * (Lnb - 6.f * dw<K>(u, e)) + f.K * e * frcp(u * (u + e));
   } else if constexpr (K == KSYM) {
     return f.c2_h2 * (Lnb - 6.f * e) - f.msym * ((rho * f.rat3 - 1.f) * e + e * (3.f * u * u + 3.f * u * e + e * e));
   } else {
@@ -74,6 +74,170 @@ __device__ __forceinline__ float nb_sum_g(const float* __restrict__ e, const flo
   }
 }
 
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+
+// ---------------------------------------------------------------------------
+// Restriction of the defect, four fine cells per lane (fine side nf % 4 == 0)
+// ---------------------------------------------------------------------------
+//
+// A lane owns the coarse cells (I, J, 2tq) and (I, J, 2tq+1), whose children
+// are the fine quads k0 = 4tq .. k0+3 of the four fine rows (2I+a, 2J+b),
+// a, b in {0, 1}.  It reads those rows and the eight rows around them that
+// the Laplacian of their cells touches (2I-1, 2I+2 in i; 2J-1, 2J+2 in j) as
+// 16-byte quads, forms d = M(e) - S at the sixteen children and writes the
+// 8-child means of e, u and d (Eq. restriction) as float2 pairs.  The two
+// k-neighbours outside the quad come from the adjacent lanes by shuffles.  All
+// 32 lanes of a warp take part (same I, J); lanes past the row end work on a
+// clamped quad and store nothing.
+template <int K>
+__device__ __forceinline__ void restrict_quad(const LevelF& f, int nf, const float* __restrict__ e,
+                                              const float* __restrict__ ub, const float* __restrict__ rho,
+                                              const float* __restrict__ S, float* __restrict__ Re,
+                                              float* __restrict__ eH, float* __restrict__ ubH,
+                                              float* __restrict__ SH, int I, int J, int tq, int lane) {
+  constexpr bool FR = is_fr(K);
+  constexpr bool RHO = (K == KSYM) || (K == KCQ);
+  const int nc = nf >> 1, nq = nf >> 2;
+  const bool act = tq < nq;
+  const int k0 = 4 * (act ? tq : nq - 1);
+  const int i0 = 2 * I, j0 = 2 * J;
+  const int iA = i0 == 0 ? nf - 1 : i0 - 1, iB = i0 + 2 == nf ? 0 : i0 + 2;
+  const int jA = j0 == 0 ? nf - 1 : j0 - 1, jB = j0 + 2 == nf ? 0 : j0 + 2;
+  auto row = [&](int i, int j) { return ((long long)i * nf + j) * nf + k0; };
+  auto q4 = [&](long long c) {
+    const float4 E = ld4(e + c);
+    if constexpr (FR) {
+      const float4 U = ld4(ub + c);
+      return make_float4(dw<K>(U.x, E.x), dw<K>(U.y, E.y), dw<K>(U.z, E.z), dw<K>(U.w, E.w));
+    } else {
+      return E;
+    }
+  };
+  auto q1 = [&](long long c) { return nbq<K>(FR ? ub[c] : 0.f, e[c]); };
+  // own rows (a, b) and their quads
+  long long co[2][2];
+  float4 E[2][2], U[2][2], Q[2][2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      co[a][b] = row(i0 + a, j0 + b);
+      E[a][b] = ld4(e + co[a][b]);
+      U[a][b] = ld4(ub + co[a][b]);
+      Q[a][b] = FR ? make_float4(dw<K>(U[a][b].x, E[a][b].x), dw<K>(U[a][b].y, E[a][b].y),
+                                 dw<K>(U[a][b].z, E[a][b].z), dw<K>(U[a][b].w, E[a][b].w))
+                   : E[a][b];
+    }
+  // halo rows: qi[0][b] = row (2I-1, 2J+b), qi[1][b] = row (2I+2, 2J+b); qj[a][0], qj[a][1] likewise in j
+  float4 qi[2][2], qj[2][2];
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    qi[0][b] = q4(row(iA, j0 + b));
+    qi[1][b] = q4(row(iB, j0 + b));
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    qj[a][0] = q4(row(i0 + a, jA));
+    qj[a][1] = q4(row(i0 + a, jB));
+  }
+  float se0 = 0.f, se1 = 0.f, su0 = 0.f, su1 = 0.f, sd0 = 0.f, sd1 = 0.f;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const float4 q = Q[a][b];
+      float qm = __shfl_up_sync(0xffffffffu, q.w, 1);
+      float qp = __shfl_down_sync(0xffffffffu, q.x, 1);
+      if (lane == 0) qm = q1(co[a][b] + (k0 == 0 ? nf - 1 : -1));
+      if (lane == 31 || tq + 1 >= nq) qp = q1(co[a][b] + (k0 + 4 == nf ? 4 - nf : 4));
+      const float4 ni = a == 0 ? qi[0][b] : Q[0][b];   // i - 1
+      const float4 pi = a == 0 ? Q[1][b] : qi[1][b];   // i + 1
+      const float4 nj = b == 0 ? qj[a][0] : Q[a][0];   // j - 1
+      const float4 pj = b == 0 ? Q[a][1] : qj[a][1];   // j + 1
+      const float4 Sv = ld4(S + co[a][b]);
+      float4 R = make_float4(1.f, 1.f, 1.f, 1.f);
+      if constexpr (RHO) {
+        if (rho) R = ld4(rho + co[a][b]);
+      }
+      const float4 Ev = E[a][b], Uv = U[a][b];
+      const float dx = local_M<K>(f, Uv.x, Ev.x, R.x, (qm + q.y) + (ni.x + pi.x) + (nj.x + pj.x)) - Sv.x;
+      const float dy = local_M<K>(f, Uv.y, Ev.y, R.y, (q.x + q.z) + (ni.y + pi.y) + (nj.y + pj.y)) - Sv.y;
+      const float dz = local_M<K>(f, Uv.z, Ev.z, R.z, (q.y + q.w) + (ni.z + pi.z) + (nj.z + pj.z)) - Sv.z;
+      const float dv = local_M<K>(f, Uv.w, Ev.w, R.w, (q.z + qp) + (ni.w + pi.w) + (nj.w + pj.w)) - Sv.w;
+      se0 += Ev.x + Ev.y;
+      se1 += Ev.z + Ev.w;
+      su0 += Uv.x + Uv.y;
+      su1 += Uv.z + Uv.w;
+      sd0 += dx + dy;
+      sd1 += dz + dv;
+    }
+  if (act) {
+    const long long t = ((long long)I * nc + J) * nc + (k0 >> 1);
+    const float2 me = make_float2(0.125f * se0, 0.125f * se1);
+    *reinterpret_cast<float2*>(Re + t) = me;
+    *reinterpret_cast<float2*>(eH + t) = me;
+    *reinterpret_cast<float2*>(ubH + t) = make_float2(0.125f * su0, 0.125f * su1);
+    *reinterpret_cast<float2*>(SH + t) = make_float2(0.125f * sd0, 0.125f * sd1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Prolongation-correction, four fine cells per lane (fine side % 4 == 0)
+// ---------------------------------------------------------------------------
+//
+// e_h += P(e_H - R e_h) with the 27/9/3/1 (/64) weights of Eq. prolongation,
+// which factor into (3/4, 1/4) per axis: the lane first combines the four
+// coarse rows (I, J) 9, (I2, J) 3, (I, J2) 3, (I2, J2) 1 at its two coarse k
+// (2tq, 2tq+1), takes the combinations at 2tq-1 and 2tq+2 from the adjacent
+// lanes, and weights (3, 1) along k.  f(R): where u + e would not be positive
+// the total field is halved instead (e <- (e_old - u)/2).
+template <bool FR>
+__device__ __forceinline__ void prolong_quad(int nc, const float* __restrict__ eH, const float* __restrict__ Re,
+                                             const float* __restrict__ ub, float* __restrict__ ef, int i, int j,
+                                             int tq, int lane) {
+  const int nf = nc << 1, nq = nf >> 2;
+  const bool act = tq < nq;
+  const int t = act ? tq : nq - 1;
+  const int k0 = 4 * t, K0 = 2 * t;
+  const int I = i >> 1, J = j >> 1;
+  int I2 = I + ((i & 1) ? 1 : -1), J2 = J + ((j & 1) ? 1 : -1);
+  I2 = I2 < 0 ? nc - 1 : (I2 >= nc ? 0 : I2);
+  J2 = J2 < 0 ? nc - 1 : (J2 >= nc ? 0 : J2);
+  const long long rA = ((long long)I * nc + J) * nc, rB = ((long long)I2 * nc + J) * nc,
+                  rC = ((long long)I * nc + J2) * nc, rD = ((long long)I2 * nc + J2) * nc;
+  auto d2 = [&](long long r) {
+    const float2 a = ld2(eH + r + K0), b = ld2(Re + r + K0);
+    return make_float2(a.x - b.x, a.y - b.y);
+  };
+  auto d1 = [&](long long r, int Kc) { return eH[r + Kc] - Re[r + Kc]; };
+  const float2 A = d2(rA), B = d2(rB), C = d2(rC), D = d2(rD);
+  const float Rx = 9.f * A.x + 3.f * (B.x + C.x) + D.x;
+  const float Ry = 9.f * A.y + 3.f * (B.y + C.y) + D.y;
+  float Rm = __shfl_up_sync(0xffffffffu, Ry, 1);    // coarse k = K0 - 1
+  float Rp = __shfl_down_sync(0xffffffffu, Rx, 1);  // coarse k = K0 + 2
+  if (lane == 0) {
+    const int Km = K0 == 0 ? nc - 1 : K0 - 1;
+    Rm = 9.f * d1(rA, Km) + 3.f * (d1(rB, Km) + d1(rC, Km)) + d1(rD, Km);
+  }
+  if (lane == 31 || tq + 1 >= nq) {
+    const int Kp = K0 + 2 == nc ? 0 : K0 + 2;
+    Rp = 9.f * d1(rA, Kp) + 3.f * (d1(rB, Kp) + d1(rC, Kp)) + d1(rD, Kp);
+  }
+  constexpr float w = 1.f / 64.f;
+  const long long c = ((long long)i * nf + j) * nf + k0;
+  const float4 old = ld4(ef + c);
+  float4 v = make_float4(old.x + (3.f * Rx + Rm) * w, old.y + (3.f * Rx + Ry) * w, old.z + (3.f * Ry + Rx) * w,
+                         old.w + (3.f * Ry + Rp) * w);
+  if constexpr (FR) {
+    const float4 u = ld4(ub + c);
+    if (!(u.x + v.x > 0.f)) v.x = 0.5f * (old.x - u.x);
+    if (!(u.y + v.y > 0.f)) v.y = 0.5f * (old.y - u.y);
+    if (!(u.z + v.z > 0.f)) v.z = 0.5f * (old.z - u.z);
+    if (!(u.w + v.w > 0.f)) v.w = 0.5f * (old.w - u.w);
+  }
+  if (act) *reinterpret_cast<float4*>(ef + c) = v;
+}
+
 // 1/x in FP64 by one Newton-Raphson refinement y1 = y0 (2 - x y0) of a
 // single-precision reciprocal y0: the relative error of y0 (below 2^-22) is
 // squared, leaving about 2^-44 ~ 6e-14, far below what the residual needs.
@@ -90,13 +254,12 @@ template <int K>
 __global__ void k_src64(ModelDev m, const float* __restrict__ rho32, long long n3, const double* __restrict__ rho_sum,
                         double* __restrict__ src) {
   const double inv_mean = (double)n3 / *rho_sum;
+  // f(R): Om/a (rho/mean - 1) + K0 = c1 rho + c0, one FMA per cell
+  const double c1 = is_fr(K) ? m.om_a * inv_mean : inv_mean;
+  const double c0 = is_fr(K) ? m.K0 - m.om_a : 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
-       t += (long long)gridDim.x * blockDim.x) {
-    const double r = (double)rho32[t] * inv_mean;
-    if constexpr (is_fr(K)) src[t] = m.om_a * (r - 1.0) + m.K0;
-    else if constexpr (K == KSYM) src[t] = r;
-    else src[t] = r;
-  }
+       t += (long long)gridDim.x * blockDim.x)
+    src[t] = fma(c1, (double)rho32[t], c0);
 }
 
 // r = N(u64) on the fine level, z-marching tiles (each cell's transformed value
@@ -174,10 +337,10 @@ __global__ void __launch_bounds__(TJ* TK) k_outer_residual(ModelDev m, int n, in
 // rho32 normalised to mean 1 (FP64 mean), for the inner levels.
 static __global__ void k_density_norm32(const float* __restrict__ rho, long long n3, const double* __restrict__ sum,
                                  float* __restrict__ out) {
-  const double inv_mean = (double)n3 / *sum;
+  const float im = (float)((double)n3 / *sum);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
        t += (long long)gridDim.x * blockDim.x)
-    out[t] = (float)((double)rho[t] * inv_mean);
+    out[t] = rho[t] * im;
 }
 
 static __global__ void __launch_bounds__(128) k_restrict32(int nf, const float* __restrict__ fine, float* __restrict__ coarse) {
@@ -196,19 +359,24 @@ static __global__ void __launch_bounds__(128) k_restrict32(int nf, const float* 
 template <int K>
 static __global__ void k_src_sumsq32(ModelDev m, const float* __restrict__ rho32, long long n3,
                               const double* __restrict__ rho_sum, double* __restrict__ partials) {
+  // a normalisation scale: single precision per cell is ample.  delta =
+  // rho/mean - 1 is formed with an FMA against the two-float 1/mean, so it
+  // keeps its relative precision where rho is close to the mean.
   const double inv_mean = (double)n3 / *rho_sum;
-  double acc = 0.0;
+  const float im_hi = (float)inv_mean, im_lo = (float)(inv_mean - (double)im_hi);
+  float acc = 0.f;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
        t += (long long)gridDim.x * blockDim.x) {
-    const double delta = (double)rho32[t] * inv_mean - 1.0;
-    double s;
-    if constexpr (is_fr(K)) s = m.om_a * delta;
-    else if constexpr (K == KSYM) s = m.msym * m.rat3 * delta * m.ubar;
-    else s = m.cq_src * delta;
-    acc += s * s;
+    const float r = rho32[t];
+    const float delta = fmaf(r, im_hi, -1.f) + r * im_lo;
+    acc = fmaf(delta, delta, acc);
   }
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  double f;
+  if constexpr (is_fr(K)) f = m.om_a;
+  else if constexpr (K == KSYM) f = m.msym * m.rat3 * m.ubar;
+  else f = m.cq_src;
+  const double a = block_sum((double)acc * (f * f));
+  if (threadIdx.x == 0) partials[blockIdx.x] = a;
 }
 
 static __global__ void k_finalize_sum32(const double* __restrict__ partials, int count, double* __restrict__ out) {

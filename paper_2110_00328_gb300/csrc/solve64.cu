@@ -241,21 +241,21 @@ __global__ void __launch_bounds__(512) k_coarse64(ModelDev m, int n, double h, d
 }
 
 __global__ void k_sum_f32(const float* __restrict__ x, long long n3, double* __restrict__ partials) {
-  double acc = 0.0;
+  FloatFloat acc;  // FP32 arithmetic (GB300's FP64 rate is 1/64 of FP32), exact to ~1e-14
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
        t += (long long)gridDim.x * blockDim.x)
-    acc += (double)x[t];
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    acc.add(x[t]);
+  const double a = block_sum(acc.value());
+  if (threadIdx.x == 0) partials[blockIdx.x] = a;
 }
 
 // rho64 = rho32 / mean, mean = sum / n3 read from device memory.
 __global__ void k_density_to64(const float* __restrict__ rho32, long long n3, const double* __restrict__ sum,
                                double* __restrict__ rho64) {
-  const double mean = *sum / (double)n3;
+  const double inv_mean = (double)n3 / *sum;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
        t += (long long)gridDim.x * blockDim.x)
-    rho64[t] = (double)rho32[t] / mean;
+    rho64[t] = (double)rho32[t] * inv_mean;
 }
 
 // Sum of squares of the model's linear source term (relative-residual scale).
@@ -373,7 +373,7 @@ int launch_fas_source64(const ModelDev& m, int nc, double hc, const double* Ru, 
 }
 
 int launch_density_mean(const float* rho32, size_t n3, double* partials, double* out_sum, cudaStream_t st) {
-  const int g = grid_for((long long)n3);
+  const int g = stream_grid((long long)n3);
   k_sum_f32<<<g, kThreads, 0, st>>>(rho32, (long long)n3, partials);
   k_finalize_sum<<<1, 1024, 0, st>>>(partials, g, out_sum);
   note_launch(2);
@@ -382,7 +382,7 @@ int launch_density_mean(const float* rho32, size_t n3, double* partials, double*
 }
 
 int launch_density_to64(const float* rho32, size_t n3, const double* sum, double* rho64, cudaStream_t st) {
-  k_density_to64<<<grid_for((long long)n3, kThreads, 1 << 20), kThreads, 0, st>>>(rho32, (long long)n3, sum, rho64);
+  k_density_to64<<<stream_grid((long long)n3), kThreads, 0, st>>>(rho32, (long long)n3, sum, rho64);
   note_launch(1);
   MG_CUDA_TRY(cudaGetLastError());
   return MGGLAM_OK;
@@ -399,7 +399,7 @@ int launch_src_sumsq(const ModelDev& m, const double* rho64, size_t n3, double* 
 }
 
 int launch_init_background(const ModelDev& m, double* field, size_t n3, cudaStream_t st) {
-  k_init_background<<<grid_for((long long)n3, kThreads, 1 << 20), kThreads, 0, st>>>(field, (long long)n3, m.ubar);
+  k_init_background<<<stream_grid((long long)n3), kThreads, 0, st>>>(field, (long long)n3, m.ubar);
   k_init_background_first<<<1, 1, 0, st>>>(field, m.ubar);
   note_launch(2);
   MG_CUDA_TRY(cudaGetLastError());

@@ -56,6 +56,19 @@ __global__ void __launch_bounds__(64) k_smooth32(LevelF f, int n, float* __restr
   e[c] = update_e_fast<K>(f, ub[c], e[c], rho ? rho[c] : 1.f, S[c], Lnb);
 }
 
+// Quad version (levels with n % 4 == 0) on the planes i0 .. i0+np-1 (mod n):
+// block (32, 4) = four rows (i, j), grid (ceil(n/128), n, ceil(np/4)).
+template <int K>
+__global__ void __launch_bounds__(128) k_smooth32q(LevelF f, int n, float* __restrict__ e,
+                                                   const float* __restrict__ ub, const float* __restrict__ rho,
+                                                   const float* __restrict__ S, int parity, int i0, int np) {
+  const int z = blockIdx.z * 4 + threadIdx.y;
+  if (z >= np) return;  // whole warps: z is uniform in a warp
+  int i = i0 + z;
+  if (i >= n) i -= n;
+  smooth_quad<K>(f, n, e, ub, rho, S, i, blockIdx.y, blockIdx.x * 32 + threadIdx.x, threadIdx.x, parity);
+}
+
 template <int K>
 __global__ void __launch_bounds__(512) k_coarse32(LevelF f, int n, float* __restrict__ e, const float* __restrict__ ub,
                                                   const float* __restrict__ rho, const float* __restrict__ S,
@@ -109,6 +122,30 @@ __global__ void __launch_bounds__(128) k_residual_restrict32(LevelF f, int nf, c
   eH[t] = 0.125f * se;
   ubH[t] = 0.125f * su;
   SH[t] = 0.125f * sd;
+}
+
+// Quad versions (fine side % 4 == 0): block (32, 4), lanes along k.
+// Restriction: grid (ceil(nf/128), nc [J], ceil(nc/4) [I]).
+template <int K>
+__global__ void __launch_bounds__(128) k_residual_restrict32q(LevelF f, int nf, const float* __restrict__ e,
+                                                              const float* __restrict__ ub,
+                                                              const float* __restrict__ rho,
+                                                              const float* __restrict__ S, float* __restrict__ Re,
+                                                              float* __restrict__ eH, float* __restrict__ ubH,
+                                                              float* __restrict__ SH) {
+  const int I = blockIdx.z * 4 + threadIdx.y;
+  if (I >= (nf >> 1)) return;  // whole warps
+  restrict_quad<K>(f, nf, e, ub, rho, S, Re, eH, ubH, SH, I, blockIdx.y, blockIdx.x * 32 + threadIdx.x,
+                   threadIdx.x);
+}
+
+// Prolongation: grid (ceil(nf/128), nf [j], nf/4 [i]).
+template <bool FR>
+__global__ void __launch_bounds__(128) k_prolong_correct32q(int nc, const float* __restrict__ eH,
+                                                            const float* __restrict__ Re,
+                                                            const float* __restrict__ ub, float* __restrict__ ef) {
+  prolong_quad<FR>(nc, eH, Re, ub, ef, blockIdx.z * 4 + threadIdx.y, blockIdx.y, blockIdx.x * 32 + threadIdx.x,
+                   threadIdx.x);
 }
 
 // In place: S <- M^H(Re) - S (S holds R d on entry).
@@ -219,6 +256,15 @@ static bool use_fused(const MixedCtx& C, int n) {
   return C.prm->sweep_chunk > 0;
 }
 
+// Planes per L2 slab of the per-colour sweep on a level of side n (0 = one
+// pass per colour), on request only, on levels whose e, u and S (12 bytes a
+// cell) do not fit in L2 (n >= 256).
+static int slab_planes(const MixedCtx& C, int n) {
+  const int P = C.prm->sweep_slab;
+  if (P <= 0 || n < 256) return 0;
+  return P >= n ? 0 : (P < 2 ? 2 : P);
+}
+
 static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
   Level& L = C.ws->lev[l];
   const float* rho = C.need_rho ? L.rho32 : nullptr;
@@ -234,6 +280,30 @@ static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
       float* tmp = L.e;
       L.e = L.e_alt;
       L.e_alt = tmp;
+    } else if (L.n % 4 == 0 && L.n >= 16) {
+      const int P = slab_planes(C, L.n);
+      auto colour = [&](int parity, int i0, int np) -> int {
+        if (np <= 0) return MGGLAM_OK;
+        const dim3 g((L.n / 4 + 31) / 32, L.n, (np + 3) / 4);
+        MG_DISPATCH32(C.m.kind, (k_smooth32q<KK><<<g, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, rho, L.S32,
+                                                                            parity, i0, np)));
+        return MGGLAM_OK;
+      };
+      if (P <= 0) {
+        colour(0, 0, L.n);
+        colour(1, 0, L.n);
+      } else {
+        // first colour on planes [a, a+P), then the second colour on the planes
+        // whose first-colour neighbours are all final, one plane behind; planes
+        // n-1 and 0 (which see each other periodically) last
+        for (int a = 0; a < L.n; a += P) {
+          const int b = a + P < L.n ? a + P : L.n;
+          colour(0, a, b - a);
+          const int r0 = a == 0 ? 1 : a - 1;
+          colour(1, r0, (b - 1) - r0);
+        }
+        colour(1, L.n - 1, 2);
+      }
     } else {
       const dim3 g = grid3(L.n / 2, L.n, L.n, 64);
       for (int parity = 0; parity < 2; ++parity)
@@ -266,7 +336,8 @@ static unsigned long long coarse_signature(const MixedCtx& C) {
   };
   mix(&C.m.kind, sizeof(int));
   mix(C.lf, sizeof(LevelF) * C.ws->nlev);
-  const int shape[5] = {C.prm->nu1, C.prm->nu2, C.prm->coarse_sweeps, C.chunk, C.need_rho ? 1 : 0};
+  const int shape[6] = {C.prm->nu1, C.prm->nu2, C.prm->coarse_sweeps, C.chunk, C.need_rho ? 1 : 0,
+                        C.prm->sweep_slab};
   mix(shape, sizeof(shape));
   const int forced = C.prm->sweep_chunk > 0;
   mix(&forced, sizeof(int));
@@ -340,8 +411,14 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st) {
   const float* rhoH = C.need_rho ? H.rho32 : nullptr;
   const int bh = bx_for(H.n);
   if (l == 0) prof_begin(PC_RESTRICT32_FINE, st, 14.0 * L.n3);
-  MG_DISPATCH32(C.m.kind, (k_residual_restrict32<KK><<<grid3(H.n, H.n, H.n, bh), bh, 0, st>>>(
-                               C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32)));
+  if (L.n % 4 == 0 && L.n >= 8) {
+    const dim3 g((L.n / 4 + 31) / 32, H.n, (H.n + 3) / 4);
+    MG_DISPATCH32(C.m.kind, (k_residual_restrict32q<KK><<<g, dim3(32, 4), 0, st>>>(
+                                 C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32)));
+  } else {
+    MG_DISPATCH32(C.m.kind, (k_residual_restrict32<KK><<<grid3(H.n, H.n, H.n, bh), bh, 0, st>>>(
+                                 C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32)));
+  }
   if (l == 0) {
     prof_end(st);
     prof_begin(PC_COARSE_LEVELS, st, 0.0);
@@ -353,8 +430,15 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st) {
   }
   if (l == 0) { prof_end(st); prof_begin(PC_PROLONG32_FINE, st, 13.0 * L.n3); }
   const int bf = bx_for(L.n);
-  if (is_fr(C.m.kind)) k_prolong_correct32<true><<<grid3(L.n, L.n, L.n, bf), bf, 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
-  else k_prolong_correct32<false><<<grid3(L.n, L.n, L.n, bf), bf, 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
+  if (L.n % 4 == 0 && L.n >= 8) {
+    const dim3 g((L.n / 4 + 31) / 32, L.n, L.n / 4);
+    if (is_fr(C.m.kind)) k_prolong_correct32q<true><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
+    else k_prolong_correct32q<false><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
+  } else if (is_fr(C.m.kind)) {
+    k_prolong_correct32<true><<<grid3(L.n, L.n, L.n, bf), bf, 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
+  } else {
+    k_prolong_correct32<false><<<grid3(L.n, L.n, L.n, bf), bf, 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
+  }
   note_launch(1);
   if (l == 0) { prof_end(st); prof_begin(PC_SMOOTH32_FINE, st, 16.0 * L.n3 * C.prm->nu2); }
   rc = smooth32(C, l, C.prm->nu2, st);
@@ -420,13 +504,13 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
   for (int l = 0; l < ws->nlev; ++l) C.lf[l] = make_levelf(C.m, ws->lev[l].h);
   Level& F = ws->lev[0];
   const long long n3 = (long long)F.n3;
-  const int g = grid_for(n3);
+  const int g = stream_grid(n3);
   // FP64 density mean and source term; FP32 normalised pyramid where the inner operator needs it
   if ((rc = launch_density_mean(rho, F.n3, ws->partials, ws->scalars + SC_MEAN, st))) return rc;
-  MG_DISPATCH32(C.m.kind, (k_src64<KK><<<grid_for(n3, kThreads, 1 << 20), kThreads, 0, st>>>(
+  MG_DISPATCH32(C.m.kind, (k_src64<KK><<<stream_grid(n3), kThreads, 0, st>>>(
                                C.m, rho, n3, ws->scalars + SC_MEAN, ws->src64)));
   if (C.need_rho) {
-    k_density_norm32<<<grid_for(n3, kThreads, 1 << 20), kThreads, 0, st>>>(rho, n3, ws->scalars + SC_MEAN, F.rho32);
+    k_density_norm32<<<stream_grid(n3), kThreads, 0, st>>>(rho, n3, ws->scalars + SC_MEAN, F.rho32);
     note_launch(1);
     for (int l = 1; l < ws->nlev; ++l) {
       const int b = bx_for(ws->lev[l].n);
@@ -475,7 +559,7 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
     for (int c = 0; c < inner && cyc < prm->max_cycles; ++c, ++cyc, ++done)
       if ((rc = vcycle32(C, 0, st))) return rc;
     prof_begin(PC_APPLY_CORR, st, 20.0 * n3);
-    k_apply_correction<<<grid_for(n3, kThreads, 1 << 20), kThreads, 0, st>>>(field, F.e, n3);
+    k_apply_correction<<<stream_grid(n3), kThreads, 0, st>>>(field, F.e, n3);
     note_launch(1);
     prof_end(st);
     ++outer;

@@ -35,14 +35,34 @@ struct LevelF {
   int keep_exp;
 };
 
-// ---- fast single-precision building blocks (MUFU-based) ----
-// approximate reciprocal (about 1 ulp): the local solve's Newton steps tolerate it
-__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
-// x^{1/3} for x > 0 (fast power intrinsic, ~1e-6 relative)
-__device__ __forceinline__ float fcbrt_pos(float x) { return __powf(x, 1.0f / 3.0f); }
-// sqrt(x) for x >= 0 as x / sqrt(x) with the fast reciprocal square root (x = 0 gives 0)
-__device__ __forceinline__ float fsqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+// ---- fast single-precision building blocks ----
+// The PTX approximate instructions with subnormals flushed (.ftz): one special-
+// function-unit operation each, no subnormal rescaling around it.  Every value
+// they see in the local solve is a normal float (fields, corrections and their
+// squares stay far above 1e-38), and the exact Newton polish that follows each
+// closed-form start removes their few-ulp errors.
+// reciprocal, relative error below 2^-23
+__device__ __forceinline__ float frcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float fdiv(float a, float b) { return a * frcp(b); }
+// x^{1/3} for x > 0 as 2^(log2(x)/3): absolute error of the base-2 log below
+// 2^-22, so the result carries ~1e-7 relative error
+__device__ __forceinline__ float fcbrt_pos(float x) {
+  float l, y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+  l *= (1.0f / 3.0f);
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(l));
+  return y;
+}
+// sqrt(max(x, 0))
+__device__ __forceinline__ float fsqrt(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(fmaxf(x, 0.f)));
+  return y;
+}
 
 // Newton polishing steps after the closed-form start of the local solve.  The
 // start inherits the single-precision cancellation in the polynomial's
@@ -182,6 +202,93 @@ __device__ __forceinline__ float update_e_fast(const LevelF& f, float u, float e
       dr -= f.cq_src * rho * f.beta * f.inv_c2 * Eu * expf(f.beta * e * f.inv_c2);
     }
     return e - r / dr;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One colour of a red-black sweep, four consecutive cells per thread
+// ---------------------------------------------------------------------------
+//
+// A warp covers 32 quads (128 cells) of one row (i, j) of a level whose side n
+// is a multiple of 4; each lane owns the quad k0 = 4 tq .. k0+3, of which two
+// cells have the colour being updated: k0+o and k0+o+2 with o = (i+j+parity)&1.
+// The lane reads its quad of e (and u, S, rho) and the same quad of the four
+// rows (i, j+-1) and (i+-1, j) as 16-byte loads; the k-neighbours come from the
+// lane's own quad except one, which the adjacent lane hands over by a shuffle
+// (lanes at a warp or row end load it).  Cells of the other colour are only
+// read, so the update is the red-black Gauss-Seidel colour step for any
+// schedule.  All 32 lanes of the warp must call this together (the shuffles);
+// lanes past the row end (tq >= n/4) work on a clamped quad and store nothing.
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+template <int K>
+__device__ __forceinline__ void smooth_quad(const LevelF& f, int n, float* __restrict__ e,
+                                            const float* __restrict__ ub, const float* __restrict__ rho,
+                                            const float* __restrict__ S, int i, int j, int tq, int lane,
+                                            int parity) {
+  constexpr bool FR = is_fr(K);
+  constexpr bool RHO = (K == KSYM) || (K == KCQ);
+  const int nq = n >> 2;
+  const bool act = tq < nq;
+  const int k0 = 4 * (act ? tq : nq - 1);
+  const long long nn = (long long)n * n;
+  const long long c0 = (long long)i * nn + (long long)j * n + k0;
+  const long long djp = (j + 1 < n) ? (long long)n : -(long long)(n - 1) * n;
+  const long long djm = (j > 0) ? -(long long)n : (long long)(n - 1) * n;
+  const long long dip = (i + 1 < n) ? nn : -(long long)(n - 1) * nn;
+  const long long dim = (i > 0) ? -nn : (long long)(n - 1) * nn;
+  float* e0 = e + c0;
+  const float* u0 = ub + c0;
+  const float4 E = ld4(e0), U = ld4(u0), Sv = ld4(S + c0);
+  const float4 Ejp = ld4(e0 + djp), Ejm = ld4(e0 + djm), Eip = ld4(e0 + dip), Eim = ld4(e0 + dim);
+  float4 Ujp = make_float4(0.f, 0.f, 0.f, 0.f), Ujm = Ujp, Uip = Ujp, Uim = Ujp;
+  if constexpr (FR) {
+    Ujp = ld4(u0 + djp);
+    Ujm = ld4(u0 + djm);
+    Uip = ld4(u0 + dip);
+    Uim = ld4(u0 + dim);
+  }
+  float4 R = make_float4(1.f, 1.f, 1.f, 1.f);
+  if constexpr (RHO) {
+    if (rho) R = ld4(rho + c0);  // CQ without the exponential coupling passes no density
+  }
+  if (((i + j + parity) & 1) == 0) {
+    // cells k0 (x) and k0+2 (z); k-neighbours k0-1 (previous lane's w), y, w
+    const float qy = nbq<K>(U.y, E.y), qw = nbq<K>(U.w, E.w);
+    float qm = __shfl_up_sync(0xffffffffu, qw, 1);
+    if (lane == 0) {
+      const long long cm = c0 + (k0 == 0 ? n - 1 : -1);
+      qm = nbq<K>(FR ? ub[cm] : 0.f, e[cm]);
+    }
+    const float LA = (qm + qy) + (nbq<K>(Ujp.x, Ejp.x) + nbq<K>(Ujm.x, Ejm.x)) +
+                     (nbq<K>(Uip.x, Eip.x) + nbq<K>(Uim.x, Eim.x));
+    const float LB = (qy + qw) + (nbq<K>(Ujp.z, Ejp.z) + nbq<K>(Ujm.z, Ejm.z)) +
+                     (nbq<K>(Uip.z, Eip.z) + nbq<K>(Uim.z, Eim.z));
+    const float eA = update_e_fast<K>(f, U.x, E.x, R.x, Sv.x, LA);
+    const float eB = update_e_fast<K>(f, U.z, E.z, R.z, Sv.z, LB);
+    if (act) {
+      e0[0] = eA;
+      e0[2] = eB;
+    }
+  } else {
+    // cells k0+1 (y) and k0+3 (w); k-neighbours x, z, k0+4 (next lane's x)
+    const float qx = nbq<K>(U.x, E.x), qz = nbq<K>(U.z, E.z);
+    float qp = __shfl_down_sync(0xffffffffu, qx, 1);
+    if (lane == 31 || tq + 1 >= nq) {
+      const long long cp = c0 + (k0 + 4 == n ? 4 - n : 4);
+      qp = nbq<K>(FR ? ub[cp] : 0.f, e[cp]);
+    }
+    const float LA = (qx + qz) + (nbq<K>(Ujp.y, Ejp.y) + nbq<K>(Ujm.y, Ejm.y)) +
+                     (nbq<K>(Uip.y, Eip.y) + nbq<K>(Uim.y, Eim.y));
+    const float LB = (qz + qp) + (nbq<K>(Ujp.w, Ejp.w) + nbq<K>(Ujm.w, Ejm.w)) +
+                     (nbq<K>(Uip.w, Eip.w) + nbq<K>(Uim.w, Eim.w));
+    const float eA = update_e_fast<K>(f, U.y, E.y, R.y, Sv.y, LA);
+    const float eB = update_e_fast<K>(f, U.w, E.w, R.w, Sv.w, LB);
+    if (act) {
+      e0[1] = eA;
+      e0[3] = eB;
+    }
   }
 }
 
