@@ -22,53 +22,119 @@
 
 namespace mg {
 
-// Periodic cell index and weight pair along one axis for coordinate x.
-__device__ __forceinline__ void cic_axis(float x, int N, int& i0, int& i1, double& w0, double& w1) {
-  // wrap into [0, N)
+// Position wrapped into [0, N).
+__device__ __forceinline__ float wrap_pos(float x, int N) {
+  if (x >= 0.f && x < (float)N) return x;
   float xf = fmodf(x, (float)N);
   if (xf < 0.f) xf += (float)N;
   if (xf >= (float)N) xf = 0.f;
-  const double xs = (double)xf - 0.5;
-  const double fl = floor(xs);
-  const double f = xs - fl;
-  int i = (int)fl;  // -1 .. N-1
-  i0 = i < 0 ? i + N : i;
-  i1 = i + 1 >= N ? i + 1 - N : i + 1;
-  w0 = 1.0 - f;
+  return xf;
+}
+
+// round(x * 2^31) for 0 <= x < 2^32 by integer operations on the float's bits
+// (exact for x >= 2^-8, whose bits all lie at or above 2^-31).
+__device__ __forceinline__ unsigned long long fix31(float x) {
+  const unsigned b = __float_as_uint(x);
+  const int ex = (int)(b >> 23);
+  if (ex == 0) return 0ull;  // zero (or subnormal: far below 2^-31)
+  const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+  const int sh = ex - 127 - 23 + 31;  // x * 2^31 = m * 2^sh
+  if (sh >= 0) return m << sh;
+  if (sh < -25) return 0ull;
+  return (m + (1ull << (-sh - 1))) >> (-sh);
+}
+
+// CIC along one axis in fixed point: cells c0 = floor(x - 1/2), c1 = c0 + 1
+// (periodic) and weights W0 = 1 - f, W1 = f in units of 2^-31, f = the
+// fractional part of x - 1/2 -- the same numbers the FP64 definition gives,
+// without double-precision arithmetic (GB300's FP64 rate is 1/64 of FP32).
+__device__ __forceinline__ void cic_axis_fixed(float x, int N, int& c0, int& c1, unsigned long long& W0,
+                                               unsigned long long& W1) {
+  const long long xs = (long long)fix31(wrap_pos(x, N)) - (1ll << 30);
+  const int c = (int)(xs >> 31);  // -1 .. N-1 (arithmetic shift = floor)
+  const unsigned long long F = (unsigned long long)(xs & 0x7FFFFFFFll);
+  c0 = c < 0 ? c + N : c;
+  c1 = c + 1 >= N ? c + 1 - N : c + 1;
+  W1 = F;
+  W0 = (1ull << 31) - F;
+}
+
+// round(P W / 2^61) for P <= 2^62, W <= 2^31: a product of three axis weights
+// (units 2^-93) rounded to the accumulator's unit 2^-32, exactly.
+__device__ __forceinline__ unsigned long long wmul(unsigned long long P, unsigned long long W) {
+  const unsigned long long lo = P * W, hi = __umul64hi(P, W);
+  return ((hi << 3) | (lo >> 61)) + ((lo >> 60) & 1ull);
+}
+
+// Single-precision CIC along one axis (for the gather, whose output is FP32).
+__device__ __forceinline__ void cic_axis_f(float x, int N, int& c0, int& c1, float& w0, float& w1) {
+  const float xs = wrap_pos(x, N) - 0.5f;
+  const float fl = floorf(xs);
+  const float f = xs - fl;
+  const int c = (int)fl;
+  c0 = c < 0 ? c + N : c;
+  c1 = c + 1 >= N ? c + 1 - N : c + 1;
+  w0 = 1.f - f;
   w1 = f;
 }
 
+// One particle per lane, warps over consecutive particles.  A lane's four
+// cells in its upper k plane are the next lane's lower-plane cells whenever
+// the two particles share (i0, j0) and sit in adjacent k cells (neighbours in
+// a lattice-ordered particle array do): the next lane then adds them to its
+// own and this lane skips those atomics.  Integer sums are exact, so the mesh
+// does not depend on which lane issues an update.
 __global__ void __launch_bounds__(kThreads) k_deposit_fixed(const float* __restrict__ pos, long long np, int N,
                                                             unsigned long long* __restrict__ acc) {
-  const double scale = 4294967296.0;  // 2^32
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < np;
-       q += (long long)gridDim.x * blockDim.x) {
-    int i0, i1, j0, j1, k0, k1;
-    double wx0, wx1, wy0, wy1, wz0, wz1;
-    cic_axis(pos[3 * q + 0], N, i0, i1, wx0, wx1);
-    cic_axis(pos[3 * q + 1], N, j0, j1, wy0, wy1);
-    cic_axis(pos[3 * q + 2], N, k0, k1, wz0, wz1);
-    const int ii[2] = {i0, i1}, jj[2] = {j0, j1}, kk[2] = {k0, k1};
-    const double wx[2] = {wx0, wx1}, wy[2] = {wy0, wy1}, wz[2] = {wz0, wz1};
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < np; base += stride) {
+    const long long q = base + lane;
+    const bool ok = q < np;
+    int i0 = 0, i1 = 0, j0 = 0, j1 = 0, k0 = -1, k1 = -2;
+    unsigned long long X0 = 0, X1 = 0, Y0 = 0, Y1 = 0, Z0 = 0, Z1 = 0;
+    if (ok) {
+      cic_axis_fixed(pos[3 * q + 0], N, i0, i1, X0, X1);
+      cic_axis_fixed(pos[3 * q + 1], N, j0, j1, Y0, Y1);
+      cic_axis_fixed(pos[3 * q + 2], N, k0, k1, Z0, Z1);
+    }
+    const unsigned long long P[4] = {X0 * Y0, X0 * Y1, X1 * Y0, X1 * Y1};  // (a, b) = 00, 01, 10, 11
+    unsigned long long lo[4], up[4];                                          // k0 and k1 planes
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+    for (int s = 0; s < 4; ++s) {
+      lo[s] = wmul(P[s], Z0);
+      up[s] = wmul(P[s], Z1);
+    }
+    const int pi = __shfl_up_sync(0xffffffffu, i0, 1), pj = __shfl_up_sync(0xffffffffu, j0, 1);
+    const int pk = __shfl_up_sync(0xffffffffu, k1, 1);
+    const bool take = lane > 0 && ok && pi == i0 && pj == j0 && pk == k0;
 #pragma unroll
-      for (int b = 0; b < 2; ++b)
+    for (int s = 0; s < 4; ++s) {
+      const unsigned long long w = __shfl_up_sync(0xffffffffu, up[s], 1);
+      if (take) lo[s] += w;
+    }
+    const bool given = __shfl_down_sync(0xffffffffu, (int)take, 1) != 0 && lane < 31;
+    if (ok) {
+      const long long ri[2] = {(long long)i0 * N, (long long)i1 * N};
+      const int jj[2] = {j0, j1};
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const double w = wx[a] * wy[b] * wz[c];
-          const unsigned long long v = (unsigned long long)llrint(w * scale);
-          if (v) atomicAdd(&acc[cidx(N, ii[a], jj[b], kk[c])], v);
-        }
+      for (int s = 0; s < 4; ++s) {
+        const long long row = (ri[s >> 1] + jj[s & 1]) * N;
+        if (lo[s]) atomicAdd(&acc[row + k0], lo[s]);
+        if (!given && up[s]) atomicAdd(&acc[row + k1], up[s]);
+      }
+    }
   }
 }
 
 __global__ void k_deposit_finish(const unsigned long long* __restrict__ acc, long long n3, double mass,
                                  float* __restrict__ rho) {
-  const double s = mass / 4294967296.0;
+  // single-precision scaling of the correctly rounded float of the sum (the
+  // output is FP32): within one ulp of the exact product
+  const float s = (float)(mass / 4294967296.0);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
        t += (long long)gridDim.x * blockDim.x)
-    rho[t] = (float)((double)acc[t] * s);
+    rho[t] = __ull2float_rn(acc[t]) * s;
 }
 
 // Scratch for the fixed-point accumulator, cached per (device, N).
@@ -101,7 +167,7 @@ int deposit_cic(const float* pos, long long np, int N, float* rho, cudaStream_t 
   k_deposit_fixed<<<grid_for(np, kThreads, 1 << 20), kThreads, 0, st>>>(pos, np, N, acc);
   prof_end(st);
   prof_begin(PC_DEPOSIT_FINISH, st, 12.0 * n3);
-  k_deposit_finish<<<grid_for(n3, kThreads, 1 << 20), kThreads, 0, st>>>(acc, n3, (double)n3 / (double)np, rho);
+  k_deposit_finish<<<stream_grid(n3), kThreads, 0, st>>>(acc, n3, (double)n3 / (double)np, rho);
   prof_end(st);
   note_launch(2);
   MG_CUDA_TRY(cudaGetLastError());
@@ -129,33 +195,57 @@ __global__ void k_transform(const double* __restrict__ u, long long n3, double u
   }
 }
 
+// Each particle reads the 32 distinct cells its three central differences at
+// the 8 CIC cells touch: the 2x2x2 core and a one-cell extension on each side
+// along each axis.
 __global__ void __launch_bounds__(kThreads) k_gather(const float* __restrict__ T, int N, const float* __restrict__ pos,
                                                      long long np, float scale, float* __restrict__ force) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < np;
        q += (long long)gridDim.x * blockDim.x) {
     int i0, i1, j0, j1, k0, k1;
-    double wx0, wx1, wy0, wy1, wz0, wz1;
-    cic_axis(pos[3 * q + 0], N, i0, i1, wx0, wx1);
-    cic_axis(pos[3 * q + 1], N, j0, j1, wy0, wy1);
-    cic_axis(pos[3 * q + 2], N, k0, k1, wz0, wz1);
-    const int ii[2] = {i0, i1}, jj[2] = {j0, j1}, kk[2] = {k0, k1};
-    const float wx[2] = {(float)wx0, (float)wx1}, wy[2] = {(float)wy0, (float)wy1}, wz[2] = {(float)wz0, (float)wz1};
-    float fx = 0.f, fy = 0.f, fz = 0.f;
+    float wx[2], wy[2], wz[2];
+    cic_axis_f(pos[3 * q + 0], N, i0, i1, wx[0], wx[1]);
+    cic_axis_f(pos[3 * q + 1], N, j0, j1, wy[0], wy[1]);
+    cic_axis_f(pos[3 * q + 2], N, k0, k1, wz[0], wz[1]);
+    const long long NN = (long long)N * N;
+    // offsets: x[0..3] = i0-1, i0, i1, i1+1 (times N^2), likewise y (times N) and z
+    const long long ox[4] = {(long long)(i0 == 0 ? N - 1 : i0 - 1) * NN, (long long)i0 * NN, (long long)i1 * NN,
+                             (long long)(i1 + 1 == N ? 0 : i1 + 1) * NN};
+    const long long oy[4] = {(long long)(j0 == 0 ? N - 1 : j0 - 1) * N, (long long)j0 * N, (long long)j1 * N,
+                             (long long)(j1 + 1 == N ? 0 : j1 + 1) * N};
+    const int oz[4] = {k0 == 0 ? N - 1 : k0 - 1, k0, k1, k1 + 1 == N ? 0 : k1 + 1};
+    float C[2][2][2];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
       for (int b = 0; b < 2; ++b)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const int i = ii[a], j = jj[b], k = kk[c];
-          const int ip = i + 1 == N ? 0 : i + 1, im = i == 0 ? N - 1 : i - 1;
-          const int jp = j + 1 == N ? 0 : j + 1, jm = j == 0 ? N - 1 : j - 1;
-          const int kp = k + 1 == N ? 0 : k + 1, km = k == 0 ? N - 1 : k - 1;
-          const float w = wx[a] * wy[b] * wz[c];
-          fx += w * (T[cidx(N, ip, j, k)] - T[cidx(N, im, j, k)]);
-          fy += w * (T[cidx(N, i, jp, k)] - T[cidx(N, i, jm, k)]);
-          fz += w * (T[cidx(N, i, j, kp)] - T[cidx(N, i, j, km)]);
-        }
+        for (int c = 0; c < 2; ++c) C[a][b][c] = T[ox[a + 1] + oy[b + 1] + oz[c + 1]];
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const float xm = T[ox[0] + oy[b + 1] + oz[c + 1]], xp = T[ox[3] + oy[b + 1] + oz[c + 1]];
+        const float w = wy[b] * wz[c];
+        fx += w * (wx[0] * (C[1][b][c] - xm) + wx[1] * (xp - C[0][b][c]));
+      }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const float ym = T[ox[a + 1] + oy[0] + oz[c + 1]], yp = T[ox[a + 1] + oy[3] + oz[c + 1]];
+        const float w = wx[a] * wz[c];
+        fy += w * (wy[0] * (C[a][1][c] - ym) + wy[1] * (yp - C[a][0][c]));
+      }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const float zm = T[ox[a + 1] + oy[b + 1] + oz[0]], zp = T[ox[a + 1] + oy[b + 1] + oz[3]];
+        const float w = wx[a] * wy[b];
+        fz += w * (wz[0] * (C[a][b][1] - zm) + wz[1] * (zp - C[a][b][0]));
+      }
     force[3 * q + 0] = 0.5f * scale * fx;
     force[3 * q + 1] = 0.5f * scale * fy;
     force[3 * q + 2] = 0.5f * scale * fz;
@@ -170,7 +260,7 @@ int gather_force(const ModelDev& m, int kind, int n_fr, const mgglam_params* prm
   if (rc) return rc;
   float* T = ws->lev[0].ub;  // scratch mesh of N^3 floats
   const long long n3 = (long long)N * N * N;
-  const int g = grid_for(n3, kThreads, 1 << 20);
+  const int g = stream_grid(n3);
   double scale;
   prof_begin(PC_TRANSFORM, st, 12.0 * n3);
   switch (kind) {
@@ -253,7 +343,7 @@ extern "C" int mgglam_deposit_cic_static(const float* pos, long long np, int N, 
   // the array keeps the previous call's sums: clear the part this call uses
   MG_CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)n3 * sizeof(unsigned long long), st));
   k_deposit_fixed<<<grid_for(np, kThreads, 1 << 20), kThreads, 0, st>>>(pos, np, N, acc);
-  k_deposit_finish<<<grid_for(n3, kThreads, 1 << 20), kThreads, 0, st>>>(acc, n3, (double)n3 / (double)np, rho);
+  k_deposit_finish<<<stream_grid(n3), kThreads, 0, st>>>(acc, n3, (double)n3 / (double)np, rho);
   note_launch(2);
   MG_CUDA_TRY(cudaGetLastError());
   return MGGLAM_OK;
