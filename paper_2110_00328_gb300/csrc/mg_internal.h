@@ -57,7 +57,8 @@ struct Workspace {
 };
 
 // Slots of Workspace::scalars.
-enum Scalar { SC_MEAN = 0, SC_SUMSQ = 1, SC_SRC = 2, SC_FLAG = 3, SC_COUNT = 8 };
+// SC_FFC: start of the float-float residual constants (48 bytes, mixed path).
+enum Scalar { SC_MEAN = 0, SC_SUMSQ = 1, SC_SRC = 2, SC_FLAG = 3, SC_FFC = 8, SC_COUNT = 16 };
 
 int count_levels(int N, int levels);
 

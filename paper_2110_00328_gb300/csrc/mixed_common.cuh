@@ -5,6 +5,7 @@
 #include <math.h>
 #include <string.h>
 
+#include "ff.cuh"
 #include "mg_common.cuh"
 #include "sweep32.cuh"
 
@@ -321,6 +322,153 @@ __device__ __forceinline__ double outer_residual_tile(const ModelDev& m, int n, 
     __syncthreads();
   }
   return block_sum((double)acc);
+}
+
+// ---------------------------------------------------------------------------
+// The same residual in float-float arithmetic (f(R) and symmetron)
+// ---------------------------------------------------------------------------
+
+// Constants of the float-float residual, written once per solve on the device
+// (the source slope depends on the density mean computed there).
+struct FFC {
+  ff c2;      // c~^2
+  ff K;       // f(R): K0 ubar
+  ff c1, c0;  // source term c1 rho + c0: f(R) Om/(a mean), K0 - Om/a; symmetron 1/mean, 0
+  ff msym, rat3;
+};
+
+__device__ __forceinline__ ff ff_split_dev(double d) {
+  const float hi = (float)d;
+  return ff{hi, (float)(d - (double)hi)};
+}
+
+static __global__ void k_ff_consts(ModelDev m, long long n3, const double* __restrict__ rho_sum,
+                                   FFC* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double inv_mean = (double)n3 / *rho_sum;
+  FFC c;
+  c.c2 = ff_split_dev(m.c2);
+  c.K = ff_split_dev(m.K);
+  const bool fr = m.kind <= KFR2;
+  c.c1 = ff_split_dev(fr ? m.om_a * inv_mean : inv_mean);
+  c.c0 = ff_split_dev(fr ? m.K0 - m.om_a : 0.0);
+  c.msym = ff_split_dev(m.msym);
+  c.rat3 = ff_split_dev(m.rat3);
+  *out = c;
+}
+
+// f(R): w = u^{n+1}; symmetron: w = u
+template <int K>
+__device__ __forceinline__ ff ff_w(ff u) {
+  if constexpr (K == KFR1) return ff_sqr(u);
+  else if constexpr (K == KFR2) return ff_mul(ff_sqr(u), u);
+  else return u;
+}
+
+// r = N(u64) at every cell of one tile, as outer_residual_tile, with the
+// arithmetic in float-float (~2^-48 relative per operation; the terms of N are
+// at most ~10^3 times the residual's scale, so the result keeps ~1e-12 of it).
+// The source is formed from the FP32 density on the fly.
+// The CTA marches up its chunk of planes with a three-plane ring of w and u in
+// shared memory; the doubles of plane i+2 are loaded into registers while
+// plane i is computed, so the global-load latency overlaps the arithmetic.
+template <int K, int TJ, int TK>
+__device__ __forceinline__ double outer_residual_tile_ff(const FFC& C, int n, int chunk, const double* __restrict__ u,
+                                                         const float* __restrict__ rho, float* __restrict__ ub,
+                                                         float* __restrict__ tau, int tile, int cb) {
+  static_assert(K != KCQ, "CQ keeps the FP64 residual");
+  constexpr int PJ = TJ + 2, PK = TK + 2, PS = PJ * PK, NT = TJ * TK, NE = (PS + NT - 1) / NT;
+  __shared__ float s_wh[3][PS], s_wl[3][PS], s_uh[3][PS], s_ul[3][PS];
+  const int tiles_k = n / TK;
+  const int k0 = (tile % tiles_k) * TK;
+  const int j0 = (tile / tiles_k) * TJ;
+  const int i0 = cb * chunk;
+  const int i1 = min(i0 + chunk, n);
+  const int t = threadIdx.x;
+  const int tj = t / TK, tk = t - tj * TK;
+  const int jg = j0 + tj, kg = k0 + tk;
+  const int cc = (tj + 1) * PK + tk + 1;
+  const size_t nn = (size_t)n * n;
+  // in-plane offsets of this thread's ring elements (fixed for the whole march)
+  size_t off[NE];
+#pragma unroll
+  for (int m = 0; m < NE; ++m) {
+    const int c = t + m * NT;
+    const int jj = c / PK, kk = c - jj * PK;
+    off[m] = c < PS ? (size_t)wrapi(j0 + jj - 1, n) * n + wrapi(k0 + kk - 1, n) : 0;
+  }
+  double pre[NE];
+  auto fetch = [&](int p) {
+    const int ig = p < 0 ? p + n : (p >= n ? p - n : p);
+    const double* base = u + (size_t)ig * nn;
+#pragma unroll
+    for (int m = 0; m < NE; ++m) pre[m] = (t + m * NT < PS) ? base[off[m]] : 0.0;
+  };
+  auto commit = [&](int p) {
+    const int slot = (p + 3) % 3;
+#pragma unroll
+    for (int m = 0; m < NE; ++m) {
+      const int c = t + m * NT;
+      if (c < PS) {
+        const ff uu = ff_from_double(pre[m]);
+        const ff w = ff_w<K>(uu);
+        s_wh[slot][c] = w.hi;
+        s_wl[slot][c] = w.lo;
+        s_uh[slot][c] = uu.hi;
+        s_ul[slot][c] = uu.lo;
+      }
+    }
+  };
+  auto W = [&](int slot, int c) { return ff{s_wh[slot][c], s_wl[slot][c]}; };
+  float acc = 0.f;
+  fetch(i0 - 1);
+  commit(i0 - 1);
+  fetch(i0);
+  commit(i0);
+  fetch(i0 + 1);
+  for (int i = i0; i < i1; ++i) {
+    commit(i + 1);
+    __syncthreads();
+    if (i + 2 <= i1) fetch(i + 2);
+    const int sl = (i + 3) % 3, sm = (i + 2) % 3, sp = (i + 4) % 3;
+    const size_t g = (size_t)i * nn + (size_t)jg * n + kg;
+    const float r = rho[g];
+    const ff uc = ff{s_uh[sl][cc], s_ul[sl][cc]};
+    const ff wc = W(sl, cc);
+    ff L = ff_add(W(sm, cc), W(sp, cc));
+    L = ff_add(L, ff_add(W(sl, cc - PK), W(sl, cc + PK)));
+    L = ff_add(L, ff_add(W(sl, cc - 1), W(sl, cc + 1)));
+    L = ff_sub(L, ff_mul_f(wc, 6.f));  // sum of the six neighbours - 6 w
+    ff v;
+    if constexpr (is_fr(K)) {
+      // c1 rho + c0 - c2 (L - 6w) - K/u
+      v = ff_add(ff_mul_f(C.c1, r), C.c0);
+      v = ff_sub(v, ff_mul(C.c2, L));
+      v = ff_sub(v, ff_mul(C.K, ff_rcp(uc)));
+    } else {
+      // c2 (L - 6u) - msym ((rho/mean rat3 - 1) u + u^3)
+      const ff a = ff_sub(ff_mul(ff_mul_f(C.c1, r), C.rat3), ff{1.f, 0.f});
+      const ff b = ff_add(ff_mul(a, uc), ff_mul(ff_sqr(uc), uc));
+      v = ff_sub(ff_mul(C.c2, L), ff_mul(C.msym, b));
+    }
+    const float tv = -ff_to_float(v);
+    ub[g] = ff_to_float(uc);
+    tau[g] = tv;
+    acc += tv * tv;
+    __syncthreads();
+  }
+  return block_sum((double)acc);
+}
+
+template <int K, int TJ, int TK>
+__global__ void __launch_bounds__(TJ* TK) k_outer_residual_ff(const FFC* __restrict__ C, int n, int chunk,
+                                                              const double* __restrict__ u,
+                                                              const float* __restrict__ rho,
+                                                              float* __restrict__ ub, float* __restrict__ tau,
+                                                              double* __restrict__ partials) {
+  const FFC c = *C;
+  const double a = outer_residual_tile_ff<K, TJ, TK>(c, n, chunk, u, rho, ub, tau, blockIdx.x, blockIdx.y);
+  if (threadIdx.x == 0) partials[blockIdx.x + blockIdx.y * gridDim.x] = a;
 }
 
 template <int K, int TJ, int TK>

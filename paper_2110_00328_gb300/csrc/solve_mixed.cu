@@ -224,8 +224,12 @@ struct MixedCtx {
   Workspace* ws;
   const mgglam_params* prm;
   bool need_rho;
-  int chunk;  // planes per CTA of the fused sweep
+  int chunk;          // planes per CTA of the fused sweep
+  const float* rho;   // the caller's density (the float-float residual forms its source from it)
+  bool ff_resid;      // fine residual in float-float (f(R), symmetron) rather than FP64 (CQ)
 };
+
+static FFC* ffc_of(Workspace* ws) { return reinterpret_cast<FFC*>(ws->scalars + SC_FFC); }
 
 // Fused-sweep tile width along k for a level side n (0 = per-colour kernels).
 static int sweep_tile_k(int n) {
@@ -450,9 +454,40 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st) {
 constexpr int kRTJ = 8, kRTK = 32;
 
 template <int K>
+static int launch_outer_residual_ff(const MixedCtx& C, double* field, int* blocks, cudaStream_t st) {
+  Workspace* ws = C.ws;
+  Level& F = ws->lev[0];
+  const FFC* ffc = ffc_of(ws);
+  if (F.n % kRTK == 0 && F.n % kRTJ == 0) {
+    int chunk = F.n >= 64 ? 64 : F.n;
+    while ((long long)(F.n / kRTK) * (F.n / kRTJ) * ((F.n + chunk - 1) / chunk) > kMaxReduceBlocks) chunk *= 2;
+    dim3 grid((F.n / kRTK) * (F.n / kRTJ), (F.n + chunk - 1) / chunk);
+    *blocks = grid.x * grid.y;
+    if (*blocks > kMaxReduceBlocks) return MGGLAM_ERR_SHAPE;
+    k_outer_residual_ff<K, kRTJ, kRTK><<<grid, kRTJ * kRTK, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub, F.S32,
+                                                                     ws->partials);
+    return MGGLAM_OK;
+  }
+  const int tk = (F.n % 16 == 0) ? 16 : ((F.n % 8 == 0) ? 8 : ((F.n % 4 == 0) ? 4 : 2));
+  dim3 grid((F.n / tk) * (F.n / 2), 1);
+  *blocks = grid.x;
+  if (*blocks > kMaxReduceBlocks) return MGGLAM_ERR_SHAPE;
+  switch (tk) {
+    case 16: k_outer_residual_ff<K, 2, 16><<<grid, 32, 0, st>>>(ffc, F.n, F.n, field, C.rho, F.ub, F.S32, ws->partials); break;
+    case 8: k_outer_residual_ff<K, 2, 8><<<grid, 16, 0, st>>>(ffc, F.n, F.n, field, C.rho, F.ub, F.S32, ws->partials); break;
+    case 4: k_outer_residual_ff<K, 2, 4><<<grid, 8, 0, st>>>(ffc, F.n, F.n, field, C.rho, F.ub, F.S32, ws->partials); break;
+    default: k_outer_residual_ff<K, 2, 2><<<grid, 4, 0, st>>>(ffc, F.n, F.n, field, C.rho, F.ub, F.S32, ws->partials); break;
+  }
+  return MGGLAM_OK;
+}
+
+template <int K>
 static int launch_outer_residual_t(const MixedCtx& C, double* field, int* blocks, cudaStream_t st) {
   Workspace* ws = C.ws;
   Level& F = ws->lev[0];
+  if constexpr (K != KCQ) {
+    if (C.ff_resid) return launch_outer_residual_ff<K>(C, field, blocks, st);
+  }
   if (F.n % kRTK == 0 && F.n % kRTJ == 0) {
     int chunk = F.n >= 64 ? 64 : F.n;
     while ((long long)(F.n / kRTK) * (F.n / kRTJ) * ((F.n + chunk - 1) / chunk) > kMaxReduceBlocks) chunk *= 2;
@@ -480,7 +515,8 @@ static int launch_outer_residual_t(const MixedCtx& C, double* field, int* blocks
 static int outer_residual(const MixedCtx& C, double* field, cudaStream_t st) {
   Workspace* ws = C.ws;
   Level& F = ws->lev[0];
-  prof_begin(PC_OUTER_RESID, st, 24.0 * F.n3);
+  // bytes per cell: u (8) and the source (float-float: the FP32 density, 4; FP64: src64, 8) in, ub and tau (4 + 4) out
+  prof_begin(PC_OUTER_RESID, st, (C.ff_resid ? 20.0 : 24.0) * F.n3);
   int g = 0, rc = MGGLAM_OK;
   MG_DISPATCH32(C.m.kind, (rc = launch_outer_residual_t<KK>(C, field, &g, st)));
   if (rc) return rc;
@@ -500,6 +536,8 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
   C.prm = prm;
   C.need_rho = (C.m.kind == KSYM) || (C.m.kind == KCQ && C.m.keep_exp);
   C.chunk = prm->sweep_chunk > 0 ? prm->sweep_chunk : 16;  // < 0: per-colour kernels only
+  C.rho = rho;
+  C.ff_resid = C.m.kind != KCQ;
   Workspace* ws = C.ws;
   for (int l = 0; l < ws->nlev; ++l) C.lf[l] = make_levelf(C.m, ws->lev[l].h);
   Level& F = ws->lev[0];
@@ -507,8 +545,13 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
   const int g = stream_grid(n3);
   // FP64 density mean and source term; FP32 normalised pyramid where the inner operator needs it
   if ((rc = launch_density_mean(rho, F.n3, ws->partials, ws->scalars + SC_MEAN, st))) return rc;
-  MG_DISPATCH32(C.m.kind, (k_src64<KK><<<stream_grid(n3), kThreads, 0, st>>>(
-                               C.m, rho, n3, ws->scalars + SC_MEAN, ws->src64)));
+  if (C.ff_resid) {
+    k_ff_consts<<<1, 32, 0, st>>>(C.m, n3, ws->scalars + SC_MEAN, ffc_of(ws));
+    note_launch(1);
+  } else {
+    MG_DISPATCH32(C.m.kind, (k_src64<KK><<<stream_grid(n3), kThreads, 0, st>>>(
+                                 C.m, rho, n3, ws->scalars + SC_MEAN, ws->src64)));
+  }
   if (C.need_rho) {
     k_density_norm32<<<stream_grid(n3), kThreads, 0, st>>>(rho, n3, ws->scalars + SC_MEAN, F.rho32);
     note_launch(1);
