@@ -41,9 +41,15 @@ struct BFine {
   int n, solve;
   ModelDev m;
   double* u;
-  const double* src;
+  const double* src;   // CQ: FP64 source term
+  const FFC* ffc;      // f(R), symmetron: float-float residual constants
+  const float* rho;    // f(R), symmetron: the caller's density
   float *ub, *tau, *e;
 };
+
+// Level layouts of the batched kernels: the quad kernels take levels whose side
+// is a multiple of 4 (>= 8); others fall back to one cell per thread.
+__host__ __device__ __forceinline__ bool quad_level(int n) { return (n & 3) == 0 && n >= 8; }
 
 __device__ __forceinline__ int find_slot(const int* __restrict__ prefix, int cnt, int b) {
   int lo = 0, hi = cnt - 1;
@@ -57,35 +63,61 @@ __device__ __forceinline__ int find_slot(const int* __restrict__ prefix, int cnt
 
 // ---- batched phase kernels (bodies as in solve_mixed.cu) ----
 
-template <int K, int BX>
-__global__ void __launch_bounds__(BX) kb_smooth(const BDesc* __restrict__ D, const int* __restrict__ prefix, int cnt,
-                                                const int* __restrict__ active, int parity) {
+// Block (32, ROWS).  Quad levels: ceil(n/128) x n x ceil(n/ROWS) blocks per
+// solve (lanes along k, ROWS planes i per block); others: one cell of the
+// colour per thread, flat.
+template <int K, int ROWS>
+__global__ void __launch_bounds__(32 * ROWS) kb_smooth(const BDesc* __restrict__ D, const int* __restrict__ prefix,
+                                                       int cnt, const int* __restrict__ active, int parity) {
   const int s = find_slot(prefix, cnt, blockIdx.x);
   const BDesc& d = D[s];
   if (!active[d.solve]) return;
-  const int n = d.n, nxb = ((n >> 1) + BX - 1) / BX;
+  const int n = d.n;
   const int b = blockIdx.x - prefix[s];
-  const int xb = b % nxb, r = b / nxb, j = r % n, i = r / n;
-  const int kk = xb * BX + threadIdx.x;
-  if (kk >= (n >> 1)) return;
+  if (quad_level(n)) {
+    const int nbx = ((n >> 2) + 31) / 32;
+    const int xb = b % nbx, r = b / nbx, j = r % n, i = (r / n) * ROWS + threadIdx.y;
+    if (i >= n) return;  // whole warps
+    smooth_quad<K>(d.lf, n, d.e, d.ub, d.rho, d.S, i, j, xb * 32 + threadIdx.x, threadIdx.x, parity);
+    return;
+  }
+  const long long t = (long long)b * (32 * ROWS) + threadIdx.y * 32 + threadIdx.x;
+  const int h = n >> 1;
+  if (t >= (long long)h * n * n) return;
+  const int kk = (int)(t % h), j = (int)((t / h) % n), i = (int)(t / ((long long)h * n));
   const int k = 2 * kk + ((i + j + parity) & 1);
   const size_t c = cidx(n, i, j, k);
   const float Lnb = nb_sum_g<K>(d.e, d.ub, n, i, j, k);
   d.e[c] = update_e_fast<K>(d.lf, d.ub[c], d.e[c], d.rho ? d.rho[c] : 1.f, d.S[c], Lnb);
 }
 
-// Restriction of level l into l+1 (coarse-cell grid): d = M(e) - S at 8 children.
+static int smooth_blocks(int n, int rows) {
+  if (quad_level(n)) return (((n >> 2) + 31) / 32) * n * ((n + rows - 1) / rows);
+  return (int)(((long long)(n >> 1) * n * n + 32 * rows - 1) / (32 * rows));
+}
+
+// Restriction of level l into l+1, d = M(e) - S at 8 children; block (32, 4).
+// Quad levels: ceil(nf/128) x nc x ceil(nc/4) blocks per solve; others: one
+// coarse cell per thread, flat.
 template <int K>
-__global__ void __launch_bounds__(64) kb_restrict(const BDesc* __restrict__ D, const int* __restrict__ prefix, int cnt,
-                                                  const int* __restrict__ active) {
+__global__ void __launch_bounds__(128) kb_restrict(const BDesc* __restrict__ D, const int* __restrict__ prefix, int cnt,
+                                                   const int* __restrict__ active) {
   const int s = find_slot(prefix, cnt, blockIdx.x);
   const BDesc& d = D[s];
   if (!active[d.solve]) return;
-  const int nf = d.n, nc = nf >> 1, nxb = (nc + 63) / 64;
+  const int nf = d.n, nc = nf >> 1;
   const int b = blockIdx.x - prefix[s];
-  const int xb = b % nxb, r = b / nxb, J = r % nc, I = r / nc;
-  const int Kc = xb * 64 + threadIdx.x;
-  if (Kc >= nc) return;
+  if (quad_level(nf)) {
+    const int nbx = ((nf >> 2) + 31) / 32;
+    const int xb = b % nbx, r = b / nbx, J = r % nc, I = (r / nc) * 4 + threadIdx.y;
+    if (I >= nc) return;  // whole warps
+    restrict_quad<K>(d.lf, nf, d.e, d.ub, d.rho, d.S, d.ReH, d.eH, d.ubH, d.SH, I, J, xb * 32 + threadIdx.x,
+                     threadIdx.x);
+    return;
+  }
+  const long long t = (long long)b * 128 + threadIdx.y * 32 + threadIdx.x;
+  if (t >= (long long)nc * nc * nc) return;
+  const int Kc = (int)(t % nc), J = (int)((t / nc) % nc), I = (int)(t / ((long long)nc * nc));
   float se = 0.f, su = 0.f, sd = 0.f;
   for (int di = 0; di < 2; ++di)
     for (int dj = 0; dj < 2; ++dj)
@@ -97,11 +129,17 @@ __global__ void __launch_bounds__(64) kb_restrict(const BDesc* __restrict__ D, c
         su += uc;
         sd += local_M<K>(d.lf, uc, ec, d.rho ? d.rho[c] : 1.f, nb_sum_g<K>(d.e, d.ub, nf, i, j, k)) - d.S[c];
       }
-  const size_t t = cidx(nc, I, J, Kc);
-  d.ReH[t] = 0.125f * se;
-  d.eH[t] = 0.125f * se;
-  d.ubH[t] = 0.125f * su;
-  d.SH[t] = 0.125f * sd;
+  const size_t o = cidx(nc, I, J, Kc);
+  d.ReH[o] = 0.125f * se;
+  d.eH[o] = 0.125f * se;
+  d.ubH[o] = 0.125f * su;
+  d.SH[o] = 0.125f * sd;
+}
+
+static int restrict_blocks(int nf) {
+  const int nc = nf >> 1;
+  if (quad_level(nf)) return (((nf >> 2) + 31) / 32) * nc * ((nc + 3) / 4);
+  return (int)(((long long)nc * nc * nc + 127) / 128);
 }
 
 // Coarse source on level l (descriptors of level l): S <- M(Re) - S.
@@ -120,18 +158,27 @@ __global__ void __launch_bounds__(64) kb_fas(const BDesc* __restrict__ D, const 
   d.S[t] = local_M<K>(d.lf, d.ub[t], d.Re[t], d.rho ? d.rho[t] : 1.f, nb_sum_g<K>(d.Re, d.ub, n, i, j, k)) - d.S[t];
 }
 
-// Prolongation-correction of level l from l+1 (fine-cell grid).
+// Prolongation-correction of level l from l+1; block (32, 4).  Quad levels:
+// ceil(nf/128) x nf x ceil(nf/4) blocks per solve; others: one fine cell per
+// thread, flat.
 template <bool FR>
-__global__ void __launch_bounds__(64) kb_prolong(const BDesc* __restrict__ D, const int* __restrict__ prefix, int cnt,
-                                                 const int* __restrict__ active) {
+__global__ void __launch_bounds__(128) kb_prolong(const BDesc* __restrict__ D, const int* __restrict__ prefix, int cnt,
+                                                  const int* __restrict__ active) {
   const int s = find_slot(prefix, cnt, blockIdx.x);
   const BDesc& d = D[s];
   if (!active[d.solve]) return;
-  const int nf = d.n, nc = nf >> 1, nxb = (nf + 63) / 64;
+  const int nf = d.n, nc = nf >> 1;
   const int b = blockIdx.x - prefix[s];
-  const int xb = b % nxb, r = b / nxb, j = r % nf, i = r / nf;
-  const int k = xb * 64 + threadIdx.x;
-  if (k >= nf) return;
+  if (quad_level(nf)) {
+    const int nbx = ((nf >> 2) + 31) / 32;
+    const int xb = b % nbx, r = b / nbx, j = r % nf, i = (r / nf) * 4 + threadIdx.y;
+    if (i >= nf) return;  // whole warps
+    prolong_quad<FR>(nc, d.eH, d.ReH, d.ub, d.e, i, j, xb * 32 + threadIdx.x, threadIdx.x);
+    return;
+  }
+  const long long t = (long long)b * 128 + threadIdx.y * 32 + threadIdx.x;
+  if (t >= (long long)nf * nf * nf) return;
+  const int k = (int)(t % nf), j = (int)((t / nf) % nf), i = (int)(t / ((long long)nf * nf));
   const int I = i >> 1, J = j >> 1, Kc = k >> 1;
   const int I2 = wrapi(I + ((i & 1) ? 1 : -1), nc);
   const int J2 = wrapi(J + ((j & 1) ? 1 : -1), nc);
@@ -141,11 +188,16 @@ __global__ void __launch_bounds__(64) kb_prolong(const BDesc* __restrict__ D, co
                       3.f * (EH(I2, J2, Kc) + EH(I2, J, K2) + EH(I, J2, K2)) + EH(I2, J2, K2)) *
                      (1.f / 64.f);
 #undef EH
-  const size_t t = cidx(nf, i, j, k);
-  const float old = d.e[t];
+  const size_t o = cidx(nf, i, j, k);
+  const float old = d.e[o];
   float v = old + corr;
-  if (FR && !(d.ub[t] + v > 0.f)) v = 0.5f * (old - d.ub[t]);
-  d.e[t] = v;
+  if (FR && !(d.ub[o] + v > 0.f)) v = 0.5f * (old - d.ub[o]);
+  d.e[o] = v;
+}
+
+static int prolong_blocks(int nf) {
+  if (quad_level(nf)) return (((nf >> 2) + 31) / 32) * nf * ((nf + 3) / 4);
+  return (int)(((long long)nf * nf * nf + 127) / 128);
 }
 
 // Coarsest levels: one CTA per solve.
@@ -178,7 +230,12 @@ __global__ void __launch_bounds__(256) kb_outer_residual(const BFine* __restrict
   double a = 0.0;
   if (active[f.solve]) {
     const int tiles = (f.n / 32) * (f.n / 8);
-    a = outer_residual_tile<K, 8, 32>(f.m, f.n, 64, f.u, f.src, f.ub, f.tau, b % tiles, b / tiles);
+    if constexpr (K == KCQ) {
+      a = outer_residual_tile<K, 8, 32>(f.m, f.n, 64, f.u, f.src, f.ub, f.tau, b % tiles, b / tiles);
+    } else {
+      const FFC c = *f.ffc;
+      a = outer_residual_tile_ff<K, 8, 32>(c, f.n, 64, f.u, f.rho, f.ub, f.tau, b % tiles, b / tiles);
+    }
   }
   if (threadIdx.x == 0) partials[blockIdx.x] = a;
 }
@@ -242,7 +299,8 @@ struct Batch {
   cudaStream_t cap = nullptr;
   unsigned long long vsig = 0;
   long long vlaunches = 0;
-  int bx = 0;                  // autotuned smoother block width
+  int rows = 0;                // autotuned smoother block height (planes per block)
+  FFC* ffc = nullptr;          // per solve: float-float residual constants
 };
 
 static std::mutex g_bmu;
@@ -309,6 +367,7 @@ static int get_batch(int count, const int* N, const mgglam_params* prm, Batch** 
   }
   const size_t o_part = take(std::max<size_t>(total_blocks, kMaxReduceBlocks) * 8);
   const size_t o_sums = take(count * 8), o_ssum = take(count * 8), o_rmean = take(count * 8), o_act = take(count * 4);
+  const size_t o_ffc = take(count * sizeof(FFC));
   if (cudaMalloc(&b->base, off) != cudaSuccess) {
     cudaGetLastError();
     delete b;
@@ -338,6 +397,7 @@ static int get_batch(int count, const int* N, const mgglam_params* prm, Batch** 
   b->ssum = (double*)(base + o_ssum);
   b->rmean = (double*)(base + o_rmean);
   b->active = (int*)(base + o_act);
+  b->ffc = (FFC*)(base + o_ffc);
   g_batches.push_back(b);
   *out = b;
   return MGGLAM_OK;
@@ -369,7 +429,7 @@ struct Plan {
 // Build all descriptor tables in one device allocation.
 static int build_plan(Batch* B, const std::vector<ModelDev>& models, const std::vector<std::vector<LevelF>>& lfs,
                       const std::vector<const float*>& rho_in, double* const* field, const mgglam_params* prm,
-                      bool need_rho_any, int bx, Plan* P, cudaStream_t st) {
+                      bool need_rho_any, int rows, Plan* P, cudaStream_t st) {
   (void)need_rho_any;
   (void)prm;
   const int count = B->count;
@@ -429,9 +489,9 @@ static int build_plan(Batch* B, const std::vector<ModelDev>& models, const std::
         const int n = B->sv[s].N >> l;
         if (l < last) {
           sm.push_back(desc(s, l));
-          bsm.push_back(((n / 2 + bx - 1) / bx) * n * n);
-          bre.push_back(((n / 2 + 63) / 64) * (n / 2) * (n / 2));
-          bpr.push_back(((n + 63) / 64) * n * n);
+          bsm.push_back(smooth_blocks(n, rows));
+          bre.push_back(restrict_blocks(n));
+          bpr.push_back(prolong_blocks(n));
           fa.push_back(desc(s, l + 1));
           bfa.push_back(((n / 2 + 63) / 64) * (n / 2) * (n / 2));
         } else if (l == last) {
@@ -466,9 +526,9 @@ static int build_plan(Batch* B, const std::vector<ModelDev>& models, const std::
         const int n = B->sv[s].N >> l;
         if (l < last) {
           sm.push_back(desc(s, l));
-          bsm.push_back(((n / 2 + bx - 1) / bx) * n * n);
-          bre.push_back(((n / 2 + 63) / 64) * (n / 2) * (n / 2));
-          bpr.push_back(((n + 63) / 64) * n * n);
+          bsm.push_back(smooth_blocks(n, rows));
+          bre.push_back(restrict_blocks(n));
+          bpr.push_back(prolong_blocks(n));
           fa.push_back(desc(s, l + 1));
           bfa.push_back(((n / 2 + 63) / 64) * (n / 2) * (n / 2));
         } else if (l == last) {
@@ -503,6 +563,8 @@ static int build_plan(Batch* B, const std::vector<ModelDev>& models, const std::
       f.m = models[s];
       f.u = field[s];
       f.src = v.src64;
+      f.ffc = B->ffc + s;
+      f.rho = rho_in[s];
       f.ub = v.ub[0];
       f.tau = v.S32[0];
       f.e = v.e[0];
@@ -555,26 +617,26 @@ static int build_plan(Batch* B, const std::vector<ModelDev>& models, const std::
   return MGGLAM_OK;
 }
 
-static void launch_smooth_phase(const Phase& ph, int bx, const int* active, int parity, cudaStream_t st) {
+static void launch_smooth_phase(const Phase& ph, int rows, const int* active, int parity, cudaStream_t st) {
   if (ph.blocks == 0) return;
-  switch (bx) {
-    case 32: MG_BDISPATCH(ph.kind, (kb_smooth<KK, 32><<<ph.blocks, 32, 0, st>>>(ph.d, ph.prefix, ph.cnt, active, parity))); break;
-    case 128: MG_BDISPATCH(ph.kind, (kb_smooth<KK, 128><<<ph.blocks, 128, 0, st>>>(ph.d, ph.prefix, ph.cnt, active, parity))); break;
-    default: MG_BDISPATCH(ph.kind, (kb_smooth<KK, 64><<<ph.blocks, 64, 0, st>>>(ph.d, ph.prefix, ph.cnt, active, parity))); break;
+  switch (rows) {
+    case 2: MG_BDISPATCH(ph.kind, (kb_smooth<KK, 2><<<ph.blocks, dim3(32, 2), 0, st>>>(ph.d, ph.prefix, ph.cnt, active, parity))); break;
+    case 8: MG_BDISPATCH(ph.kind, (kb_smooth<KK, 8><<<ph.blocks, dim3(32, 8), 0, st>>>(ph.d, ph.prefix, ph.cnt, active, parity))); break;
+    default: MG_BDISPATCH(ph.kind, (kb_smooth<KK, 4><<<ph.blocks, dim3(32, 4), 0, st>>>(ph.d, ph.prefix, ph.cnt, active, parity))); break;
   }
   note_launch(1);
 }
 
 // One V-cycle of every active solve.
-static void batch_vcycle(const Plan& P, const int* active, const mgglam_params& prm, int bx, cudaStream_t st) {
+static void batch_vcycle(const Plan& P, const int* active, const mgglam_params& prm, int rows, cudaStream_t st) {
   const int Lmax = (int)P.lv.size();
   for (int l = 0; l < Lmax; ++l) {
     const auto& L = P.lv[l];
     for (size_t g = 0; g < L.smooth.size(); ++g) {
       for (int s = 0; s < prm.nu1; ++s)
-        for (int par = 0; par < 2; ++par) launch_smooth_phase(L.smooth[g], bx, active, par, st);
+        for (int par = 0; par < 2; ++par) launch_smooth_phase(L.smooth[g], rows, active, par, st);
       const Phase& r = L.restrict_[g];
-      MG_BDISPATCH(r.kind, (kb_restrict<KK><<<r.blocks, 64, 0, st>>>(r.d, r.prefix, r.cnt, active)));
+      MG_BDISPATCH(r.kind, (kb_restrict<KK><<<r.blocks, dim3(32, 4), 0, st>>>(r.d, r.prefix, r.cnt, active)));
       const Phase& f = L.fas[g];
       MG_BDISPATCH(f.kind, (kb_fas<KK><<<f.blocks, 64, 0, st>>>(f.d, f.prefix, f.cnt, active)));
       note_launch(2);
@@ -588,11 +650,11 @@ static void batch_vcycle(const Plan& P, const int* active, const mgglam_params& 
     const auto& L = P.lv[l];
     for (size_t g = 0; g < L.prolong.size(); ++g) {
       const Phase& p = L.prolong[g];
-      if (is_fr(p.kind)) kb_prolong<true><<<p.blocks, 64, 0, st>>>(p.d, p.prefix, p.cnt, active);
-      else kb_prolong<false><<<p.blocks, 64, 0, st>>>(p.d, p.prefix, p.cnt, active);
+      if (is_fr(p.kind)) kb_prolong<true><<<p.blocks, dim3(32, 4), 0, st>>>(p.d, p.prefix, p.cnt, active);
+      else kb_prolong<false><<<p.blocks, dim3(32, 4), 0, st>>>(p.d, p.prefix, p.cnt, active);
       note_launch(1);
       for (int s = 0; s < prm.nu2; ++s)
-        for (int par = 0; par < 2; ++par) launch_smooth_phase(L.smooth[g], bx, active, par, st);
+        for (int par = 0; par < 2; ++par) launch_smooth_phase(L.smooth[g], rows, active, par, st);
     }
   }
 }
@@ -616,8 +678,12 @@ int solve_batch(int count, const mgglam_params* prm, const double* a, const floa
     const Batch::S& v = B->sv[s];
     const long long n3 = (long long)v.N * v.N * v.N;
     if ((rc = launch_density_mean(rho[s], (size_t)n3, B->partials, B->rmean + s, st))) return rc;
-    MG_BDISPATCH(models[s].kind, (k_src64<KK><<<stream_grid(n3), kThreads, 0, st>>>(
-                                     models[s], rho[s], n3, B->rmean + s, v.src64)));
+    if (models[s].kind == KCQ) {
+      MG_BDISPATCH(models[s].kind, (k_src64<KK><<<stream_grid(n3), kThreads, 0, st>>>(
+                                       models[s], rho[s], n3, B->rmean + s, v.src64)));
+    } else {
+      k_ff_consts<<<1, 32, 0, st>>>(models[s], n3, B->rmean + s, B->ffc + s);
+    }
     k_density_norm32<<<stream_grid(n3), kThreads, 0, st>>>(rho[s], n3, B->rmean + s, v.rho32[0]);
     for (int l = 1; l < v.nlev; ++l) {
       const int nc = v.N >> l;
@@ -632,7 +698,7 @@ int solve_batch(int count, const mgglam_params* prm, const double* a, const floa
   }
   Plan P;
   if ((rc = build_plan(B, models, lfs, std::vector<const float*>(rho, rho + count), field, prm, false,
-                       B->bx ? B->bx : 64, &P, st)))
+                       B->rows ? B->rows : 4, &P, st)))
     return rc;
   const int ng = (int)P.outer.size();
   auto outer_residual = [&]() -> int {
@@ -655,12 +721,12 @@ int solve_batch(int count, const mgglam_params* prm, const double* a, const floa
   for (int s = 0; s < count; ++s) B->h_active[s] = 1;
   MG_CUDA_TRY(cudaMemcpyAsync(B->active, B->h_active, count * 4, cudaMemcpyHostToDevice, st));
   if ((rc = outer_residual())) return rc;
-  // autotune the smoother's block width once per batch (timed on the fine levels'
-  // sweeps, after the first residual has set the base field and source)
-  if (B->bx == 0) {
-    int best = 64;
+  // autotune the smoother's block height once per batch (timed on the fine
+  // levels' sweeps, after the first residual has set the base field and source)
+  if (B->rows == 0) {
+    int best = 4;
     float best_ms = 1e30f;
-    for (int cand : {32, 64, 128}) {
+    for (int cand : {2, 4, 8}) {
       Plan Pt;
       if ((rc = build_plan(B, models, lfs, std::vector<const float*>(rho, rho + count), field, prm, false, cand, &Pt, st)))
         return rc;
@@ -681,11 +747,11 @@ int solve_batch(int count, const mgglam_params* prm, const double* a, const floa
       cudaEventDestroy(e1);
       if (ms < best_ms) { best_ms = ms; best = cand; }
     }
-    B->bx = best;
+    B->rows = best;
     // the timing sweeps changed e on the fine levels: start again from zero
     for (int s = 0; s < count; ++s)
       MG_CUDA_TRY(cudaMemsetAsync(B->sv[s].e[0], 0, (size_t)B->sv[s].N * B->sv[s].N * B->sv[s].N * 4, st));
-    if ((rc = build_plan(B, models, lfs, std::vector<const float*>(rho, rho + count), field, prm, false, B->bx, &P,
+    if ((rc = build_plan(B, models, lfs, std::vector<const float*>(rho, rho + count), field, prm, false, B->rows, &P,
                          st)))
       return rc;
   }
@@ -712,7 +778,7 @@ int solve_batch(int count, const mgglam_params* prm, const double* a, const floa
     mix(&models[s].kind, sizeof(int));
     mix(&field[s], sizeof(double*));
   }
-  const int shape[4] = {prm[0].nu1, prm[0].nu2, prm[0].coarse_sweeps, B->bx};
+  const int shape[4] = {prm[0].nu1, prm[0].nu2, prm[0].coarse_sweeps, B->rows};
   mix(shape, sizeof(shape));
   mix(&B->tables, sizeof(void*));
   if (!(B->vexec && B->vsig == sig)) {
@@ -721,7 +787,7 @@ int solve_batch(int count, const mgglam_params* prm, const double* a, const floa
     cudaGraph_t g = nullptr;
     bool ok = cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
-      batch_vcycle(P, B->active, prm[0], B->bx, B->cap);
+      batch_vcycle(P, B->active, prm[0], B->rows, B->cap);
       ok = cudaStreamEndCapture(B->cap, &g) == cudaSuccess && g;
     }
     B->vlaunches = launch_count() - n0;
