@@ -90,7 +90,11 @@ typedef struct {
                          one pass per colour (measured faster at 256^3: the kernel is bound
                          by instruction issue, and the extra launches cost more than the
                          DRAM traffic they save) */
-  int reserved[2];
+  int tail_cells;     /* MIXED: the coarsest levels, from the first level (below the finest)
+                         with at most this many cells, run as one thread block with the
+                         levels in shared memory (same arithmetic, fewer launches).
+                         0 (default) = 512; < 0 = off; at most 4096 */
+  int reserved[1];
 } mgglam_params;
 
 /* Per-solve statistics.  resid values are the relative global residual:

@@ -38,7 +38,8 @@ class CParams(ctypes.Structure):
                 ("levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("coarse_sweeps", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("sweep_chunk", ctypes.c_int), ("sweep_slab", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("sweep_chunk", ctypes.c_int), ("sweep_slab", ctypes.c_int), ("tail_cells", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
 class CStats(ctypes.Structure):
@@ -75,6 +76,7 @@ class Params:
     check_every: int = 1
     sweep_chunk: int = 0
     sweep_slab: int = 0
+    tail_cells: int = 0
 
     def c(self) -> CParams:
         p = CParams()

@@ -31,6 +31,7 @@
 #include "mg_internal.h"
 #include "mixed_common.cuh"
 #include "sweep32.cuh"
+#include "tail32.cuh"
 
 namespace mg {
 
@@ -227,6 +228,7 @@ struct MixedCtx {
   int chunk;          // planes per CTA of the fused sweep
   const float* rho;   // the caller's density (the float-float residual forms its source from it)
   bool ff_resid;      // fine residual in float-float (f(R), symmetron) rather than FP64 (CQ)
+  int tail_level;     // first level (>= 1) run by the one-block tail kernel, or -1
 };
 
 static FFC* ffc_of(Workspace* ws) { return reinterpret_cast<FFC*>(ws->scalars + SC_FFC); }
@@ -340,8 +342,8 @@ static unsigned long long coarse_signature(const MixedCtx& C) {
   };
   mix(&C.m.kind, sizeof(int));
   mix(C.lf, sizeof(LevelF) * C.ws->nlev);
-  const int shape[6] = {C.prm->nu1, C.prm->nu2, C.prm->coarse_sweeps, C.chunk, C.need_rho ? 1 : 0,
-                        C.prm->sweep_slab};
+  const int shape[7] = {C.prm->nu1, C.prm->nu2, C.prm->coarse_sweeps, C.chunk, C.need_rho ? 1 : 0,
+                        C.prm->sweep_slab, C.tail_level};
   mix(shape, sizeof(shape));
   const int forced = C.prm->sweep_chunk > 0;
   mix(&forced, sizeof(int));
@@ -397,11 +399,48 @@ static int coarse_part(const MixedCtx& C, cudaStream_t st) {
   return MGGLAM_OK;
 }
 
+// Levels tail_level .. coarsest in one CTA (tail32.cuh).
+template <int K>
+static void launch_tail_t(const TailArgs& A, cudaStream_t st) {
+  k_tail32<K><<<1, kTailThreads, tail_smem_bytes(A), st>>>(A);
+}
+
+static int launch_tail(const MixedCtx& C, int l, cudaStream_t st) {
+  Workspace* ws = C.ws;
+  TailArgs A;
+  memset(&A, 0, sizeof(A));
+  A.T = ws->nlev - l;
+  for (int m = 0; m < A.T; ++m) {
+    A.n[m] = ws->lev[l + m].n;
+    A.lf[m] = C.lf[l + m];
+    A.rho[m] = C.need_rho ? ws->lev[l + m].rho32 : nullptr;
+  }
+  A.e = ws->lev[l].e;
+  A.ub = ws->lev[l].ub;
+  A.S = ws->lev[l].S32;
+  A.nu1 = C.prm->nu1;
+  A.nu2 = C.prm->nu2;
+  A.coarse_sweeps = C.prm->coarse_sweeps;
+  MG_DISPATCH32(C.m.kind, (launch_tail_t<KK>(A, st)));
+  return MGGLAM_OK;
+}
+
+// The tail's shared memory can exceed the 48 KB default (at most ~94 KB).
+static void tail_allow_smem() {
+  const int bytes = 96 * 1024;
+  cudaFuncSetAttribute(k_tail32<KFR0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_tail32<KFR1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_tail32<KFR2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_tail32<KSYM>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_tail32<KCQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 static int vcycle32(const MixedCtx& C, int l, cudaStream_t st) {
   Workspace* ws = C.ws;
   Level& L = ws->lev[l];
   const float* rho = C.need_rho ? L.rho32 : nullptr;
   int rc;
+  if (l == C.tail_level) return launch_tail(C, l, st);
   if (l == ws->nlev - 1) {
     if ((long long)L.n3 > 4096) return smooth32(C, l, C.prm->coarse_sweeps, st);
     MG_DISPATCH32(C.m.kind, (k_coarse32<KK><<<1, 512, 0, st>>>(C.lf[l], L.n, L.e, L.ub, rho, L.S32,
@@ -538,6 +577,14 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
   C.chunk = prm->sweep_chunk > 0 ? prm->sweep_chunk : 16;  // < 0: per-colour kernels only
   C.rho = rho;
   C.ff_resid = C.m.kind != KCQ;
+  C.tail_level = -1;
+  const long long tail_cells = prm->tail_cells == 0 ? 512 : (prm->tail_cells > kTailMaxCells ? kTailMaxCells : prm->tail_cells);
+  for (int l = 1; l < C.ws->nlev && tail_cells > 0; ++l)
+    if ((long long)C.ws->lev[l].n3 <= tail_cells && C.ws->nlev - l <= kTailMaxLevels) {
+      C.tail_level = l;
+      break;
+    }
+  if (C.tail_level > 0) tail_allow_smem();
   Workspace* ws = C.ws;
   for (int l = 0; l < ws->nlev; ++l) C.lf[l] = make_levelf(C.m, ws->lev[l].h);
   Level& F = ws->lev[0];
