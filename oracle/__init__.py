@@ -109,6 +109,8 @@ def lib():
         _lib.or_num_threads.restype = i
         _lib.or_local_root.argtypes = [i, i, d, d, d]
         _lib.or_local_root.restype = d
+        _lib.or_cq_background.argtypes = [d, d, d, d, d, d, d, d, i, dp, dp, dp, dp]
+        _lib.or_cq_background.restype = i
     return _lib
 
 
@@ -229,6 +231,31 @@ def gather_force(p: Params, u, pos, prefactor: float = 1.0, phiN=None):
 def local_root(model: int, n: int, p: float, q: float, u_old: float = 1.0) -> float:
     """The admissible root of the local polynomial (u^{n+2} or u^3) + p u + q = 0."""
     return lib().or_local_root(model, n, p, q, u_old)
+
+
+def radiation_density(h: float, T_cmb: float = 2.7255, N_eff: float = 3.046) -> float:
+    """Omega_r today: CMB photons at T_cmb plus N_eff massless neutrino species (Sec. 3.2.3).
+
+    rho_gamma = (4 sigma_SB / c) T^4 (radiation constant), rho_crit = 3 H0^2 / (8 pi G),
+    neutrinos add N_eff (7/8) (4/11)^(4/3) of the photon density."""
+    import math
+    sigma_sb, c, G = 5.670374419e-8, 299792458.0, 6.67430e-11
+    mpc = 3.0856775814913673e22
+    H0 = 100.0 * h * 1e3 / mpc
+    rho_gamma = 4.0 * sigma_sb / c ** 3 * T_cmb ** 4        # kg m^-3
+    rho_crit = 3.0 * H0 * H0 / (8.0 * math.pi * G)
+    return rho_gamma / rho_crit * (1.0 + N_eff * 7.0 / 8.0 * (4.0 / 11.0) ** (4.0 / 3.0))
+
+
+def cq_background(alpha: float, beta: float, omega_m: float, omega_r: float, a: float = 1.0,
+                  z_init: float = 1e5, phi_init: float = 1e-4, dphi_init: float = 0.0, steps: int = 50000):
+    """Coupled-quintessence background by RK4 shooting: (lambda, phibar(a), dphibar/dlna(a), H(a)/H0)."""
+    lam, ph, dph, E = (ctypes.c_double() for _ in range(4))
+    it = lib().or_cq_background(alpha, beta, omega_m, omega_r, a, z_init, phi_init, dphi_init, steps,
+                                ctypes.byref(lam), ctypes.byref(ph), ctypes.byref(dph), ctypes.byref(E))
+    if it < 0:
+        raise RuntimeError("no bracket for lambda")
+    return lam.value, ph.value, dph.value, E.value
 
 
 def num_threads() -> int:

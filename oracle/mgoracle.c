@@ -612,3 +612,101 @@ double or_local_root(int model, int n, double pp, double qq, double u_old) {
   p.n = n;
   return local_root(&p, pp, qq, u_old);
 }
+
+/*
+ * Coupled-quintessence background (Sec. 3.2.3, "background cosmology solver").
+ *
+ * The paper's equations in N = ln a, conformal form:
+ *   H^2/H0^2  = [1 - x^2/6]^{-1} [Or e^{-2N} + e^{beta phi} Om e^{-N} + L e^{2N} phi^{-alpha}]
+ *   H'/H0^2   = -x^2/3 H^2/H0^2 + L e^{2N} phi^{-alpha} - Or e^{-2N} - Om e^{-N} e^{beta phi}/2
+ *   (H^2/H0^2) phi_NN + [2 H^2/H0^2 + H'/H0^2] phi_N - 3 alpha L e^{2N} phi^{-(1+alpha)}
+ *        + 3 beta e^{-N} Om e^{beta phi} = 0        (Eq. csf_background_eom_codeunit)
+ * with x = dphi/dN and H the conformal Hubble rate.  L is the potential
+ * amplitude of these code-unit equations; reading: L = lambda^2/3 with lambda
+ * of Eq. csf_param_lambda (V = Lambda^4/phi^alpha, Lambda^4/M_Pl^2 = H0^2
+ * lambda^2), which is what the physical Friedmann and field equations give
+ * for this potential.
+ *
+ * Integration: classical fourth-order Runge-Kutta with a fixed step in N from
+ * z_init to the requested a.  lambda is found as in the paper by shooting: the
+ * H(a=1) the integration predicts must equal H0 (E(N=0) = 1), and E(0) grows
+ * with lambda; the root is bracketed and bisected.
+ */
+typedef struct { double alpha, beta, om, orad, L; } cq_bg;
+
+static double cq_H2(const cq_bg* c, double N, double phi, double x) {
+  return (c->orad * exp(-2.0 * N) + exp(c->beta * phi) * c->om * exp(-N) + c->L * exp(2.0 * N) * pow(phi, -c->alpha)) /
+         (1.0 - x * x / 6.0);
+}
+
+static void cq_rhs(const cq_bg* c, double N, const double y[2], double dy[2]) {
+  const double phi = y[0], x = y[1];
+  const double H2 = cq_H2(c, N, phi, x);
+  const double Hp = -x * x / 3.0 * H2 + c->L * exp(2.0 * N) * pow(phi, -c->alpha) - c->orad * exp(-2.0 * N) -
+                    0.5 * c->om * exp(-N) * exp(c->beta * phi);
+  dy[0] = x;
+  dy[1] = (3.0 * c->alpha * c->L * exp(2.0 * N) * pow(phi, -(1.0 + c->alpha)) -
+           3.0 * c->beta * exp(-N) * c->om * exp(c->beta * phi) - (2.0 * H2 + Hp) * x) /
+          H2;
+}
+
+/* Integrate from N0 to N1 with 'steps' RK4 steps; y in/out. */
+static void cq_integrate(const cq_bg* c, double N0, double N1, int steps, double y[2]) {
+  const double h = (N1 - N0) / steps;
+  double N = N0;
+  for (int s = 0; s < steps; ++s) {
+    double k1[2], k2[2], k3[2], k4[2], t[2];
+    cq_rhs(c, N, y, k1);
+    t[0] = y[0] + 0.5 * h * k1[0]; t[1] = y[1] + 0.5 * h * k1[1];
+    cq_rhs(c, N + 0.5 * h, t, k2);
+    t[0] = y[0] + 0.5 * h * k2[0]; t[1] = y[1] + 0.5 * h * k2[1];
+    cq_rhs(c, N + 0.5 * h, t, k3);
+    t[0] = y[0] + h * k3[0]; t[1] = y[1] + h * k3[1];
+    cq_rhs(c, N + h, t, k4);
+    y[0] += h / 6.0 * (k1[0] + 2.0 * k2[0] + 2.0 * k3[0] + k4[0]);
+    y[1] += h / 6.0 * (k1[1] + 2.0 * k2[1] + 2.0 * k3[1] + k4[1]);
+    N += h;
+  }
+}
+
+/* E(a=1) - 1 for a trial lambda. */
+static double cq_mismatch(cq_bg* c, double lambda, double Ni, double phi_i, double x_i, int steps) {
+  c->L = lambda * lambda / 3.0;
+  double y[2] = {phi_i, x_i};
+  cq_integrate(c, Ni, 0.0, steps, y);
+  /* E^2 = H^2/H0^2 at N = 0 (conformal and cosmic rates agree at a = 1) */
+  return sqrt(cq_H2(c, 0.0, y[0], y[1])) - 1.0;
+}
+
+/* lambda, and at scale factor a: phibar, dphibar/dlna, E = H/H0.  Returns the
+ * number of bisection steps, or -1 if no bracket was found. */
+int or_cq_background(double alpha, double beta, double omega_m, double omega_r, double a, double z_init,
+                     double phi_init, double dphi_init, int steps, double* lambda, double* phibar,
+                     double* dphibar, double* E) {
+  cq_bg c = {alpha, beta, omega_m, omega_r, 0.0};
+  const double Ni = -log(1.0 + z_init);
+  double lo = 1.0, hi = 1.0;
+  double flo = cq_mismatch(&c, lo, Ni, phi_init, dphi_init, steps), fhi = flo;
+  int k = 0;
+  while (flo > 0.0 && k++ < 60) { hi = lo; fhi = flo; lo *= 0.5; flo = cq_mismatch(&c, lo, Ni, phi_init, dphi_init, steps); }
+  k = 0;
+  while (fhi < 0.0 && k++ < 60) { lo = hi; flo = fhi; hi *= 2.0; fhi = cq_mismatch(&c, hi, Ni, phi_init, dphi_init, steps); }
+  if (!(flo <= 0.0 && fhi >= 0.0)) return -1;
+  int it = 0;
+  while (hi - lo > 1e-14 * hi && it < 200) {
+    const double mid = 0.5 * (lo + hi);
+    const double f = cq_mismatch(&c, mid, Ni, phi_init, dphi_init, steps);
+    if (f > 0.0) hi = mid; else lo = mid;
+    ++it;
+  }
+  const double lam = 0.5 * (lo + hi);
+  c.L = lam * lam / 3.0;
+  double y[2] = {phi_init, dphi_init};
+  const double Na = log(a);
+  cq_integrate(&c, Ni, Na, (int)ceil(steps * (Na - Ni) / (0.0 - Ni)), y);
+  *lambda = lam;
+  *phibar = y[0];
+  *dphibar = y[1];
+  *E = sqrt(cq_H2(&c, Na, y[0], y[1])) * exp(-Na);  /* conformal H / a = H */
+  return it;
+}

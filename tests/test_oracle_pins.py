@@ -418,3 +418,62 @@ def test_gather_force_single_mode(orc):
     expect = 2.0 * 0.5 * b["c2"] * 1e-5 * 0.2 * np.sin(k) * np.sin(k * x)
     np.testing.assert_allclose(F[:, 0], expect, rtol=1e-9, atol=1e-12 * b["c2"])
     np.testing.assert_allclose(F[:, 1:], 0.0, atol=1e-9 * np.abs(expect).max())
+
+
+# ---------------------------------------------------------------------------
+# Coupled-quintessence background (Sec. 3.2.3, background cosmology solver)
+# ---------------------------------------------------------------------------
+
+H_CQ = 0.6774
+
+
+def test_radiation_density_matches_the_standard_photon_value(orc):
+    """Omega_gamma h^2 for T_CMB = 2.7255 K is the textbook 2.473e-5; neutrinos
+    (3.046 species) multiply it by 1 + 3.046 * 7/8 * (4/11)^(4/3) = 1.6918."""
+    Or = orc.radiation_density(H_CQ)
+    assert Or * H_CQ ** 2 / 1.69178 == pytest.approx(2.4730e-5, rel=2e-4)
+
+
+def test_cq_background_reduces_to_lcdm(orc):
+    """alpha -> 0, beta = 0: a constant potential and no coupling is a
+    cosmological constant, so lambda^2/3 = Omega_Lambda = 1 - Om - Or and
+    E(a)^2 = Or a^-4 + Om a^-3 + Omega_Lambda exactly."""
+    Or = orc.radiation_density(H_CQ)
+    lam, phi, dphi, E = orc.cq_background(1e-9, 0.0, 0.3, Or, a=0.5)
+    OL = 1.0 - 0.3 - Or
+    assert lam == pytest.approx(np.sqrt(3.0 * OL), rel=1e-7)
+    assert E == pytest.approx(np.sqrt(Or * 16 + 0.3 * 8 + OL), rel=1e-9)
+
+
+def test_cq_background_satisfies_the_raychaudhuri_equation(orc):
+    """The oracle integrates the field equation and takes H from the Friedmann
+    constraint; the Raychaudhuri equation is not used.  Energy conservation
+    with the coupled matter density A(phi) rho_m makes d ln H / d ln a =
+    -[2 Or a^-4 + 3/2 Om a^-3 e^{beta phi}] / E^2 - x^2/2 hold only if the
+    field equation (with its coupling term) is right.  Checked by central
+    differences along the alpha = 0.1, beta = -0.05 solution at a = 0.5, and
+    dphi/dln a against the returned x."""
+    Or = orc.radiation_density(H_CQ)
+    alpha, beta, Om = 0.1, -0.05, 0.3
+    N0, d = np.log(0.5), 2e-3
+    res = {s: orc.cq_background(alpha, beta, Om, Or, a=float(np.exp(N0 + s * d))) for s in (-1, 0, 1)}
+    lam, phi, x, E = res[0]
+    assert res[-1][0] == lam == res[1][0]
+    dlnE = (np.log(res[1][3]) - np.log(res[-1][3])) / (2 * d)
+    a = np.exp(N0)
+    ray = -(2 * Or * a ** -4 + 1.5 * Om * a ** -3 * np.exp(beta * phi)) / E ** 2 - x * x / 2
+    assert dlnE == pytest.approx(ray, rel=1e-5)
+    assert (res[1][1] - res[-1][1]) / (2 * d) == pytest.approx(x, rel=1e-5)
+    # the coupling and the potential both matter: dropping the coupling moves H
+    assert abs(dlnE - (ray + 1.5 * Om * a ** -3 * (np.exp(beta * phi) - 1) / E ** 2)) > 1e-4
+
+
+def test_cq_background_forgets_its_initial_field(orc):
+    """The initial field at z = 1e5 does not matter as long as it is small
+    (Sec. 3.2.3): 1e-5 and 1e-6 give the same lambda and phibar(1)."""
+    Or = orc.radiation_density(H_CQ)
+    r1 = orc.cq_background(0.1, -0.05, 0.3, Or, phi_init=1e-5)
+    r2 = orc.cq_background(0.1, -0.05, 0.3, Or, phi_init=1e-6)
+    assert r1[0] == pytest.approx(r2[0], rel=1e-6)
+    assert r1[1] == pytest.approx(r2[1], rel=2e-5)
+    assert r1[3] == pytest.approx(1.0, abs=1e-12)
