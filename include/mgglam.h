@@ -291,6 +291,31 @@ int mgglam_prolong_correct(const mgglam_params* prm, int n, const double* uH, co
 /* Free every cached scratch allocation on the current device. */
 int mgglam_release(void);
 
+/* ---- Coupled-quintessence background (host code, once per parameter set) --
+ *
+ * Sec. 3.2.3 ("background cosmology solver"), Eqs. csf_background_eom,
+ * csf_background_Friedmann, csf_background_Raychaudhuri and their code-unit
+ * form Eq. csf_background_eom_codeunit, for A(phi) = exp(beta phi) and
+ * V = Lambda^4/phi^alpha (Eqs. csf_coupling_function, csf_potential) with
+ * Lambda^4/M_Pl^2 = H0^2 lambda^2 (Eq. csf_param_lambda).  Flat universe,
+ * radiation = CMB photons at 2.7255 K plus 3.046 massless neutrino species.
+ * lambda is not free: it is found, as in the paper, by shooting until the
+ * H(a=1) of the integration from z = 1e5 equals H0.
+ *
+ * alpha > 0, beta, omega_m in (0,1), h = H0/(100 km/s/Mpc) > 0, a in (0, 1].
+ * Outputs (host scalars): lambda; phibar(a); dphibar/dln a at a; E = H(a)/H0.
+ * phibar and lambda are what mgglam_params.phibar and .lambda take for the CQ
+ * solve; dphibar/dln a and E enter the particle update (Eq.
+ * csf_particle_geodesic_code2).  Returns MGGLAM_ERR_ARG for invalid inputs,
+ * MGGLAM_ERR_NONFINITE if an integration fails, MGGLAM_ERR_NOT_CONVERGED if
+ * no lambda in [2^-60, 2^60] matches H0.  Touches no GPU state. */
+int mgglam_cq_background(double alpha, double beta, double omega_m, double h, double a, double* lambda,
+                         double* phibar, double* dphibar_dlna, double* E);
+
+/* Present-day radiation density parameter Omega_r for H0 = 100 h km/s/Mpc
+ * (photons at 2.7255 K, 3.046 massless neutrinos; Sec. 3.2.3). */
+double mgglam_radiation_density(double h);
+
 /* ---- tracing (not part of the paper's method: measurement support) ---- */
 
 /* Accumulated CUDA-event timing of one class of kernel launches. */

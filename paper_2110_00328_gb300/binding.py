@@ -101,7 +101,7 @@ EXPORTS = ["mgglam_version", "mgglam_status_string", "mgglam_default_params", "m
            "mgglam_solve_scalar", "mgglam_gather_force", "mgglam_smooth", "mgglam_residual",
            "mgglam_restrict", "mgglam_prolong_correct", "mgglam_release", "mgglam_profile_start",
            "mgglam_profile_stop", "mgglam_launch_count", "mgglam_deposit_cic_static",
-           "mgglam_solve_adjoint", "mgglam_solve_batch"]
+           "mgglam_solve_adjoint", "mgglam_solve_batch", "mgglam_cq_background", "mgglam_radiation_density"]
 
 
 class CKernelProfile(ctypes.Structure):
@@ -307,6 +307,24 @@ def solve_adjoint(prm: Params, a: float, field, rho, grad_field, tol: float = 1e
     nh = min(64, st.outer + 1)
     return grad_rho, gth.value, Stats(st.cycles, st.outer, bool(st.converged), st.resid0, st.resid, st.seconds,
                                       list(st.resid_hist[:nh]))
+
+
+def cq_background(alpha: float, beta: float, omega_m: float = 0.3, h: float = 0.6774, a: float = 1.0):
+    """Coupled-quintessence background (mgglam_cq_background): dict with lambda,
+    phibar(a), dphibar_dlna(a) and E = H(a)/H0."""
+    lib = load()
+    lam, ph, dph, E = (ctypes.c_double() for _ in range(4))
+    _check("mgglam_cq_background",
+           lib.mgglam_cq_background(ctypes.c_double(alpha), ctypes.c_double(beta), ctypes.c_double(omega_m),
+                                    ctypes.c_double(h), ctypes.c_double(a), ctypes.byref(lam), ctypes.byref(ph),
+                                    ctypes.byref(dph), ctypes.byref(E)))
+    return {"lambda": lam.value, "phibar": ph.value, "dphibar_dlna": dph.value, "E": E.value}
+
+
+def radiation_density(h: float = 0.6774) -> float:
+    lib = load()
+    lib.mgglam_radiation_density.restype = ctypes.c_double
+    return lib.mgglam_radiation_density(ctypes.c_double(h))
 
 
 def solve_batch(prms, a_list, rhos, fields, tol: float, stream=None, allow_unconverged=False):
