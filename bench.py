@@ -258,6 +258,42 @@ def run_batch_extra(mg, torch, dev, tol=TOL) -> dict:
             "fp64_all_converged": bool(all(s.converged for s in st_fp64))}
 
 
+def run_models_extra(mg, torch, dev, tol=TOL) -> dict:
+    """256^3, box 256 Mpc/h, lognormal density (sigma_g = 2.0, P ~ k^-1.5 with a
+    Gaussian cut at half the Nyquist wavenumber, seed 2): symmetron (a* = 0.5,
+    beta* = 1, range 1 Mpc/h) and coupled quintessence (alpha = 0.1, beta = -0.05,
+    phibar(1) and lambda from the background solver), mixed precision vs plain
+    FP64, from the background field to relative residual 1e-8."""
+    from paper_2110_00328_gb300 import inputs
+    N = 256
+    rho = torch.from_numpy(inputs.lognormal_density(N, 2.0, seed=2).astype(np.float32)).to(dev)
+    bg = mg.cq_background(0.1, -0.05, 0.3, 0.6774, 1.0)
+    cases = {"symmetron": dict(model=mg.SYMMETRON, a_star=0.5, beta_star=1.0, xi=100.0 / 299792.458, box=256.0),
+             "cq": dict(model=mg.CQ, alpha=0.1, beta=-0.05, lam=bg["lambda"], phibar=bg["phibar"], box=256.0)}
+    out = {"workload": "256^3 lognormal sigma_g 2.0 seed 2, tol 1e-8; CQ background: lambda %.6f phibar(1) %.6f"
+                       % (bg["lambda"], bg["phibar"])}
+    field = torch.empty((N,) * 3, dtype=torch.float64, device=dev)
+    for name, kw in cases.items():
+        res = {}
+        for prec, pname in ((mg.MIXED, "mixed"), (mg.FP64, "fp64")):
+            p = mg.Params(**kw, precision=prec, max_cycles=80, nu2=1, coarse_sweeps=4)
+            times = []
+            for rep in range(3):
+                field.fill_(float("nan"))
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                st = mg.solve_scalar(p, 1.0, rho, field, tol, allow_unconverged=True)
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            res[pname] = {"time_to_tol_ms": round(min(times[1:]), 3), "cycles": st.cycles, "converged": bool(st.converged),
+                          "resid": st.resid}
+        res["speedup_mixed_vs_fp64"] = round(res["fp64"]["time_to_tol_ms"] / res["mixed"]["time_to_tol_ms"], 2)
+        out[name] = res
+    return out
+
+
 def run_adjoint_extra(mg, torch, dev) -> dict:
     """Gradient of sum_b log P_F(k_b) (fifth-force power, 32 log bins) w.r.t. the
     density and ln|fR0| at 512^3 (f(R) n=1, |fR0| = 1e-5, box 512 Mpc/h, lognormal
@@ -456,13 +492,15 @@ def run_ours(args) -> None:
                 "d2h_bytes_per_step": int(force_host.numel() * 4), "ms_per_step": round(e2e_total / len(e2e_ms), 3)},
         "clocks": clk,
     }
-    extras = {"all": ("batch", "adjoint"), "none": ()}.get(args.extras, (args.extras,))
+    extras = {"all": ("batch", "adjoint", "models"), "none": ()}.get(args.extras, (args.extras,))
     if args.no_extras:
         extras = ()
     if "batch" in extras:
         line["batch"] = run_batch_extra(mg, torch, dev)
     if "adjoint" in extras:
         line["adjoint"] = run_adjoint_extra(mg, torch, dev)
+    if "models" in extras:
+        line["models"] = run_models_extra(mg, torch, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = run_oracle_baseline(pos_h)
     print(json.dumps(line), flush=True)
@@ -486,8 +524,9 @@ def main():
                     help="red-black sweeps on the coarsest level (4 reach the same cycle count and residual as 16 here)")
     ap.add_argument("--tail-cells", type=int, default=0, help="largest level run by the one-block tail (0 = default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", choices=["all", "none", "batch", "adjoint"], default="all",
-                    help="extra measurements after the main step: the 48-solve batch, the 512^3 adjoint")
+    ap.add_argument("--extras", choices=["all", "none", "batch", "adjoint", "models"], default="all",
+                    help="extra measurements after the main step: the 48-solve batch, the 512^3 adjoint, "
+                         "the symmetron and CQ solves at 256^3")
     ap.add_argument("--no-extras", action="store_true", help="same as --extras none")
     args = ap.parse_args()
     if args.impl == "reference":
