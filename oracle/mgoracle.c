@@ -386,8 +386,14 @@ typedef struct {
   int nu1, nu2, coarse_sweeps, kind, levels;
 } or_cycle_opts;
 
+/* One multigrid cycle from level l (Sec. 3.2.1, Fig. multigrid_cycles): the
+ * coarse-grid correction of level l calls the cycle of level l+1 once
+ * (mode 0, V-cycle), twice as W-cycles (mode 2, W-cycle), or once as an
+ * F-cycle and then once as a V-cycle (mode 1, F-cycle).  The second call
+ * continues from the coarse solution the first one left, with the same
+ * coarse source. */
 static void vcycle(const or_params* p, const or_background* b, or_hier* H, int l,
-                   const or_cycle_opts* o, long* guarded) {
+                   const or_cycle_opts* o, long* guarded, int mode) {
   int n = H->n[l];
   double h = H->h[l];
   if (l == H->nlev - 1) {
@@ -408,7 +414,9 @@ static void vcycle(const or_params* p, const or_background* b, or_hier* H, int l
   free(Rd);
   /* coarse initial guess = R u^h */
   memcpy(H->u[l + 1], H->Ru[l + 1], nc3 * sizeof(double));
-  vcycle(p, b, H, l + 1, o, guarded);
+  vcycle(p, b, H, l + 1, o, guarded, mode);
+  if (mode == 2) vcycle(p, b, H, l + 1, o, guarded, 2);
+  if (mode == 1) vcycle(p, b, H, l + 1, o, guarded, 0);
   *guarded += or_prolong_correct(p, nc, H->u[l + 1], H->Ru[l + 1], H->u[l]);
   or_smooth(p, b, n, h, H->u[l], H->rho[l], H->S[l], o->nu2, o->kind);
 }
@@ -452,9 +460,9 @@ static int count_levels(int N, int levels) {
  * hist[0..max_cycles]: relative global residual before each cycle and at the end.
  * Returns the number of V-cycles run; *eps_out = final relative residual.
  */
-int or_solve(const or_params* p, int N, const double* rho_in, double* u, double tol,
-             int max_cycles, int nu1, int nu2, int coarse_sweeps, int kind, int levels,
-             double* hist, double* eps_out, long* guarded_out) {
+int or_solve_cycle(const or_params* p, int N, const double* rho_in, double* u, double tol,
+                   int max_cycles, int nu1, int nu2, int coarse_sweeps, int kind, int levels, int cycle,
+                   double* hist, double* eps_out, long* guarded_out) {
   or_background b;
   or_compute_background(p, N, &b);
   or_hier H;
@@ -487,7 +495,7 @@ int or_solve(const or_params* p, int N, const double* rho_in, double* u, double 
   double eps = sqrt(or_residual(p, &b, N, 1.0, u, H.rho[0], NULL, NULL) / (double)N3) / snorm;
   if (hist) hist[0] = eps;
   while (cyc < max_cycles && !(eps <= tol)) {
-    vcycle(p, &b, &H, 0, &o, &guarded);
+    vcycle(p, &b, &H, 0, &o, &guarded, cycle);
     ++cyc;
     eps = sqrt(or_residual(p, &b, N, 1.0, u, H.rho[0], NULL, NULL) / (double)N3) / snorm;
     if (hist) hist[cyc] = eps;
@@ -499,6 +507,13 @@ int or_solve(const or_params* p, int N, const double* rho_in, double* u, double 
   if (eps_out) *eps_out = eps;
   if (guarded_out) *guarded_out = guarded;
   return cyc;
+}
+
+int or_solve(const or_params* p, int N, const double* rho_in, double* u, double tol,
+             int max_cycles, int nu1, int nu2, int coarse_sweeps, int kind, int levels,
+             double* hist, double* eps_out, long* guarded_out) {
+  return or_solve_cycle(p, N, rho_in, u, tol, max_cycles, nu1, nu2, coarse_sweeps, kind, levels, 0, hist,
+                        eps_out, guarded_out);
 }
 
 /* Relative-residual normaliser, exposed so tests can form the same ratio. */

@@ -477,3 +477,27 @@ def test_cq_background_forgets_its_initial_field(orc):
     assert r1[0] == pytest.approx(r2[0], rel=1e-6)
     assert r1[1] == pytest.approx(r2[1], rel=2e-5)
     assert r1[3] == pytest.approx(1.0, abs=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# F- and W-cycles (Sec. 3.2.1: the arrangements MG-GLAM implements besides V)
+# ---------------------------------------------------------------------------
+
+def test_f_and_w_cycles_reach_the_same_discrete_solution_faster(orc):
+    """The cycle shape changes how the fixed point is approached, not the fixed
+    point: V, F and W cycles converge to the same discrete solution.  F and W
+    solve the coarse-grid problem more accurately than one V visit, so each of
+    their cycles contracts the residual at least as much as a V-cycle, and the
+    history differs from the V-cycle's (the recursion is really different)."""
+    from paper_2110_00328_gb300 import inputs
+    rho = inputs.lognormal_density(32, 1.0, seed=0)
+    p = orc.Params(model=0, n=1, fR0_abs=1e-5, box=64.0)
+    res = {c: orc.solve(p, rho, tol=1e-12, max_cycles=40, cycle=c) for c in (0, 1, 2)}
+    for c in (1, 2):
+        assert np.linalg.norm(res[c].u - res[0].u) <= 1e-10 * np.linalg.norm(res[0].u)
+        assert res[c].hist[3] < res[0].hist[3]
+        assert not np.allclose(res[c].hist[1:4], res[0].hist[1:4], rtol=1e-3)
+    # with 5 levels (32 -> 2) the F and W recursions visit the coarse levels differently
+    r1 = orc.solve(p, rho, tol=0.0, max_cycles=2, cycle=1, levels=5, coarse_sweeps=2)
+    r2 = orc.solve(p, rho, tol=0.0, max_cycles=2, cycle=2, levels=5, coarse_sweeps=2)
+    assert not np.array_equal(r1.u, r2.u)
