@@ -82,9 +82,20 @@ def level_sizes(N: int):
     return ns
 
 
-def updates_per_cycle(N: int, nu1=2, nu2=2, coarse=16) -> int:
+def level_visits(l: int, cycle: int) -> int:
+    """Visits of level l in one cycle: V once; W 2^l; F l + 1 (F then V below the finest)."""
+    if cycle == 2:
+        return 2 ** l
+    if cycle == 1:
+        return l + 1
+    return 1
+
+
+def updates_per_cycle(N: int, nu1=2, nu2=2, coarse=16, cycle=0) -> int:
     ns = level_sizes(N)
-    return sum((nu1 + nu2) * n ** 3 for n in ns[:-1]) + coarse * ns[-1] ** 3
+    L = len(ns)
+    return (sum(level_visits(l, cycle) * (nu1 + nu2) * ns[l] ** 3 for l in range(L - 1)) +
+            level_visits(L - 1, cycle) * coarse * ns[-1] ** 3)
 
 
 class ClockSampler:
@@ -391,7 +402,7 @@ def run_ours(args) -> None:
     prec = mg.FP64 if args.precision == "fp64" else mg.MIXED
     prm = mg.Params(model=mg.FR, n=1, fR0_abs=FR0, box=BOX, precision=prec, max_cycles=60,
                     inner_cycles=args.inner_cycles, sweep_chunk=args.chunk, nu1=args.nu1, nu2=args.nu2,
-                    coarse_sweeps=args.coarse_sweeps, tail_cells=args.tail_cells)
+                    coarse_sweeps=args.coarse_sweeps, tail_cells=args.tail_cells, cycle="VFW".index(args.cycle))
     pos_h = inputs.zeldovich_positions(N_MESH, seed=1 + rank, sigma=SIGMA)
     npart = pos_h.shape[0]
     pos = torch.from_numpy(pos_h).to(dev)
@@ -443,7 +454,7 @@ def run_ours(args) -> None:
     total_ms = dep + sol + gat
     total_ms = reduce_max(total_ms, world, dev)
     cycles = [st.cycles for st, _ in recs]
-    ups_rank = sum(c * updates_per_cycle(N_MESH, prm.nu1, prm.nu2, prm.coarse_sweeps) for c in cycles)
+    ups_rank = sum(c * updates_per_cycle(N_MESH, prm.nu1, prm.nu2, prm.coarse_sweeps, prm.cycle) for c in cycles)
     value = ups_rank * world / (total_ms * 1e-3) / 1e6
 
     # end to end through the public API with host buffers (pinned), H2D + D2H inside the timing
@@ -464,7 +475,7 @@ def run_ours(args) -> None:
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_total = reduce_max(sum(e2e_ms), world, dev)
-    e2e_value = st.cycles * updates_per_cycle(N_MESH, prm.nu1, prm.nu2, prm.coarse_sweeps) * len(e2e_ms) * world / (e2e_total * 1e-3) / 1e6
+    e2e_value = st.cycles * updates_per_cycle(N_MESH, prm.nu1, prm.nu2, prm.coarse_sweeps, prm.cycle) * len(e2e_ms) * world / (e2e_total * 1e-3) / 1e6
 
     if rank != 0:
         if world > 1:
@@ -500,7 +511,7 @@ def run_ours(args) -> None:
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N_MESH, "box_mpch": BOX, "fR0": FR0, "n": 1, "tol": TOL,
                    "particles": npart, "precision": args.precision, "inner_cycles": args.inner_cycles, "sweep_chunk": args.chunk,
-                   "nu1": prm.nu1, "nu2": prm.nu2, "coarse_sweeps": prm.coarse_sweeps, "tail_cells": prm.tail_cells,
+                   "nu1": prm.nu1, "nu2": prm.nu2, "coarse_sweeps": prm.coarse_sweeps, "tail_cells": prm.tail_cells, "cycle": args.cycle,
                    "levels": level_sizes(N_MESH),
                    "l2": "512 MB written between timed steps; positions (201 MB) exceed L2",
                    "parallelism": f"independent realisation per GPU x{world}"},
@@ -544,6 +555,7 @@ def main():
     ap.add_argument("--coarse-sweeps", type=int, default=4,
                     help="red-black sweeps on the coarsest level (4 reach the same cycle count and residual as 16 here)")
     ap.add_argument("--tail-cells", type=int, default=0, help="largest level run by the one-block tail (0 = default)")
+    ap.add_argument("--cycle", choices=["V", "F", "W"], default="V", help="multigrid cycle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--extras", choices=["all", "none", "batch", "adjoint", "models"], default="all",
                     help="extra measurements after the main step: the 48-solve batch, the 512^3 adjoint, "

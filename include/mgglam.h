@@ -94,7 +94,8 @@ typedef struct {
                          with at most this many cells, run as one thread block with the
                          levels in shared memory (same arithmetic, fewer launches).
                          0 (default) = 512; < 0 = off; at most 4096 */
-  int reserved[1];
+  int cycle;          /* multigrid cycle: 0 (default) V, 1 F, 2 W (Sec. 3.2.1; each level
+                         recurses once (V), twice (W), or F then V (F)) */
 } mgglam_params;
 
 /* Per-solve statistics.  resid values are the relative global residual:
@@ -246,7 +247,8 @@ int mgglam_solve_adjoint(const mgglam_params* prm, double a, const double* field
  * and converged solves drop out (their blocks exit at once).
  *   count   number of solves (>= 1)
  *   prm     host array [count]; nu1, nu2, coarse_sweeps must agree across solves;
- *           inner_cycles and max_cycles are taken from prm[0]
+ *           inner_cycles and max_cycles are taken from prm[0]; cycle must be 0
+ *           (V-cycles)
  *   a       host array [count]
  *   rho     host array [count] of device float32 N[s]^3 pointers
  *   N       host array [count]; each a multiple of 32, 32..2048

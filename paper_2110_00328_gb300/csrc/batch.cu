@@ -875,6 +875,7 @@ extern "C" int mgglam_solve_batch(int count, const mgglam_params* prm, const dou
     if (prm[s].nu1 != prm[0].nu1 || prm[s].nu2 != prm[0].nu2 || prm[s].coarse_sweeps != prm[0].coarse_sweeps)
       return MGGLAM_ERR_ARG;
     if (prm[s].nu1 < 0 || prm[s].nu2 < 0 || prm[s].coarse_sweeps < 0) return MGGLAM_ERR_ARG;
+    if (prm[s].cycle != 0) return MGGLAM_ERR_ARG;  // batched solves run V-cycles
   }
   return mg::solve_batch(count, prm, a, rho, N, field, tol, stats, (cudaStream_t)stream);
 }

@@ -410,7 +410,10 @@ int launch_init_background(const ModelDev& m, double* field, size_t n3, cudaStre
 // FP64 solver
 // ---------------------------------------------------------------------------
 
-static int vcycle64(const ModelDev& m, Workspace* ws, int l, const mgglam_params* prm, cudaStream_t st) {
+// One multigrid cycle from level l (Sec. 3.2.1): mode 0 V, 1 F, 2 W.
+static int vcycle64(const ModelDev& m, Workspace* ws, int l, const mgglam_params* prm, cudaStream_t st,
+                    int mode = -1) {
+  if (mode < 0) mode = prm->cycle;
   Level& L = ws->lev[l];
   int rc;
   if (l == ws->nlev - 1) return launch_coarse64(m, L.n, L.h, L.u, L.rho, L.S, prm->coarse_sweeps, st);
@@ -423,7 +426,8 @@ static int vcycle64(const ModelDev& m, Workspace* ws, int l, const mgglam_params
   if ((rc = launch_residual_restrict64(m, L.n, L.h, L.u, L.rho, L.S, C.Ru, C.u, C.S, st))) return rc;
   if (l == 0) { prof_end(st); prof_begin(PC_COARSE_LEVELS, st, 0.0); }
   if ((rc = launch_fas_source64(m, C.n, C.h, C.Ru, C.rho, C.S, st))) return rc;
-  if ((rc = vcycle64(m, ws, l + 1, prm, st))) return rc;
+  if ((rc = vcycle64(m, ws, l + 1, prm, st, mode))) return rc;
+  if (mode != 0 && (rc = vcycle64(m, ws, l + 1, prm, st, mode == 2 ? 2 : 0))) return rc;
   if (l == 0) { prof_end(st); prof_begin(PC_PROLONG64_FINE, st, (16.0 + 2.0) * L.n3); }
   if ((rc = launch_prolong_correct64(m, C.n, C.u, C.Ru, L.u, st))) return rc;
   if (l == 0) { prof_end(st); prof_begin(PC_SMOOTH64_FINE, st, 24.0 * L.n3 * prm->nu2); }

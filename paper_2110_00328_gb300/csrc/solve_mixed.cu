@@ -319,17 +319,20 @@ static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
   return MGGLAM_OK;
 }
 
-static int vcycle32(const MixedCtx& C, int l, cudaStream_t st);
+static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode);
 
-// Coarse part of a V-cycle seen from the finest level: the FAS source on level 1
-// and the cycle on levels >= 1, enqueued directly.
+// Coarse-grid correction seen from the finest level: the FAS source on level 1
+// and the cycle(s) on levels >= 1 (V: one; W: two W; F: F then V), enqueued directly.
 static int coarse_part_direct(const MixedCtx& C, cudaStream_t st) {
   Level& H = C.ws->lev[1];
   const float* rhoH = C.need_rho ? H.rho32 : nullptr;
   const int bh = bx_for(H.n);
   MG_DISPATCH32(C.m.kind, (k_fas_source32<KK><<<grid3(H.n, H.n, H.n, bh), bh, 0, st>>>(C.lf[1], H.n, H.Re, H.ub,
                                                                                       rhoH, H.S32)));
-  return vcycle32(C, 1, st);
+  const int mode = C.prm->cycle;
+  int rc = vcycle32(C, 1, st, mode);
+  if (rc || mode == 0) return rc;
+  return vcycle32(C, 1, st, mode == 2 ? 2 : 0);
 }
 
 // Signature of everything the coarse graph bakes in (kernel constants and the
@@ -342,8 +345,8 @@ static unsigned long long coarse_signature(const MixedCtx& C) {
   };
   mix(&C.m.kind, sizeof(int));
   mix(C.lf, sizeof(LevelF) * C.ws->nlev);
-  const int shape[7] = {C.prm->nu1, C.prm->nu2, C.prm->coarse_sweeps, C.chunk, C.need_rho ? 1 : 0,
-                        C.prm->sweep_slab, C.tail_level};
+  const int shape[8] = {C.prm->nu1, C.prm->nu2, C.prm->coarse_sweeps, C.chunk, C.need_rho ? 1 : 0,
+                        C.prm->sweep_slab, C.tail_level, C.prm->cycle};
   mix(shape, sizeof(shape));
   const int forced = C.prm->sweep_chunk > 0;
   mix(&forced, sizeof(int));
@@ -435,7 +438,8 @@ static void tail_allow_smem() {
   cudaFuncSetAttribute(k_tail32<KCQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-static int vcycle32(const MixedCtx& C, int l, cudaStream_t st) {
+// One multigrid cycle from level l: mode 0 V, 1 F, 2 W (Sec. 3.2.1).
+static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode) {
   Workspace* ws = C.ws;
   Level& L = ws->lev[l];
   const float* rho = C.need_rho ? L.rho32 : nullptr;
@@ -469,7 +473,8 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st) {
   } else {
     MG_DISPATCH32(C.m.kind, (k_fas_source32<KK><<<grid3(H.n, H.n, H.n, bh), bh, 0, st>>>(C.lf[l + 1], H.n, H.Re,
                                                                                         H.ub, rhoH, H.S32)));
-    if ((rc = vcycle32(C, l + 1, st))) return rc;
+    if ((rc = vcycle32(C, l + 1, st, mode))) return rc;
+    if (mode != 0 && (rc = vcycle32(C, l + 1, st, mode == 2 ? 2 : 0))) return rc;
   }
   if (l == 0) { prof_end(st); prof_begin(PC_PROLONG32_FINE, st, 13.0 * L.n3); }
   const int bf = bx_for(L.n);
@@ -577,9 +582,9 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
   C.chunk = prm->sweep_chunk > 0 ? prm->sweep_chunk : 16;  // < 0: per-colour kernels only
   C.rho = rho;
   C.ff_resid = C.m.kind != KCQ;
-  C.tail_level = -1;
+  C.tail_level = -1;  // the one-block tail runs V-cycles only
   const long long tail_cells = prm->tail_cells == 0 ? 512 : (prm->tail_cells > kTailMaxCells ? kTailMaxCells : prm->tail_cells);
-  for (int l = 1; l < C.ws->nlev && tail_cells > 0; ++l)
+  for (int l = 1; l < C.ws->nlev && tail_cells > 0 && prm->cycle == 0; ++l)
     if ((long long)C.ws->lev[l].n3 <= tail_cells && C.ws->nlev - l <= kTailMaxLevels) {
       C.tail_level = l;
       break;
@@ -647,7 +652,7 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
     int done = 0;
     MG_CUDA_TRY(cudaMemsetAsync(F.e, 0, F.n3 * sizeof(float), st));
     for (int c = 0; c < inner && cyc < prm->max_cycles; ++c, ++cyc, ++done)
-      if ((rc = vcycle32(C, 0, st))) return rc;
+      if ((rc = vcycle32(C, 0, st, C.prm->cycle))) return rc;
     prof_begin(PC_APPLY_CORR, st, 20.0 * n3);
     k_apply_correction<<<stream_grid(n3), kThreads, 0, st>>>(field, F.e, n3);
     note_launch(1);
