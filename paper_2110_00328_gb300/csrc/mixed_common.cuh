@@ -90,7 +90,7 @@ __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast
 // k-neighbours outside the quad come from the adjacent lanes by shuffles.  All
 // 32 lanes of a warp take part (same I, J); lanes past the row end work on a
 // clamped quad and store nothing.
-template <int K>
+template <int K, class FL = NatLayout>
 __device__ __forceinline__ void restrict_quad(const LevelF& f, int nf, const float* __restrict__ e,
                                               const float* __restrict__ ub, const float* __restrict__ rho,
                                               const float* __restrict__ S, float* __restrict__ Re,
@@ -104,27 +104,27 @@ __device__ __forceinline__ void restrict_quad(const LevelF& f, int nf, const flo
   const int i0 = 2 * I, j0 = 2 * J;
   const int iA = i0 == 0 ? nf - 1 : i0 - 1, iB = i0 + 2 == nf ? 0 : i0 + 2;
   const int jA = j0 == 0 ? nf - 1 : j0 - 1, jB = j0 + 2 == nf ? 0 : j0 + 2;
-  auto row = [&](int i, int j) { return ((long long)i * nf + j) * nf + k0; };
-  auto q4 = [&](long long c) {
-    const float4 E = ld4(e + c);
+  auto q4 = [&](int i, int j) {
+    const float4 E = FL::q(e, nf, i, j, k0);
     if constexpr (FR) {
-      const float4 U = ld4(ub + c);
+      const float4 U = FL::q(ub, nf, i, j, k0);
       return make_float4(dw<K>(U.x, E.x), dw<K>(U.y, E.y), dw<K>(U.z, E.z), dw<K>(U.w, E.w));
     } else {
       return E;
     }
   };
-  auto q1 = [&](long long c) { return nbq<K>(FR ? ub[c] : 0.f, e[c]); };
+  auto q1 = [&](int i, int j, int k) {
+    const long long c = FL::idx(nf, i, j, k);
+    return nbq<K>(FR ? ub[c] : 0.f, e[c]);
+  };
   // own rows (a, b) and their quads
-  long long co[2][2];
   float4 E[2][2], U[2][2], Q[2][2];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
-      co[a][b] = row(i0 + a, j0 + b);
-      E[a][b] = ld4(e + co[a][b]);
-      U[a][b] = ld4(ub + co[a][b]);
+      E[a][b] = FL::q(e, nf, i0 + a, j0 + b, k0);
+      U[a][b] = FL::q(ub, nf, i0 + a, j0 + b, k0);
       Q[a][b] = FR ? make_float4(dw<K>(U[a][b].x, E[a][b].x), dw<K>(U[a][b].y, E[a][b].y),
                                  dw<K>(U[a][b].z, E[a][b].z), dw<K>(U[a][b].w, E[a][b].w))
                    : E[a][b];
@@ -133,13 +133,13 @@ __device__ __forceinline__ void restrict_quad(const LevelF& f, int nf, const flo
   float4 qi[2][2], qj[2][2];
 #pragma unroll
   for (int b = 0; b < 2; ++b) {
-    qi[0][b] = q4(row(iA, j0 + b));
-    qi[1][b] = q4(row(iB, j0 + b));
+    qi[0][b] = q4(iA, j0 + b);
+    qi[1][b] = q4(iB, j0 + b);
   }
 #pragma unroll
   for (int a = 0; a < 2; ++a) {
-    qj[a][0] = q4(row(i0 + a, jA));
-    qj[a][1] = q4(row(i0 + a, jB));
+    qj[a][0] = q4(i0 + a, jA);
+    qj[a][1] = q4(i0 + a, jB);
   }
   float se0 = 0.f, se1 = 0.f, su0 = 0.f, su1 = 0.f, sd0 = 0.f, sd1 = 0.f;
 #pragma unroll
@@ -149,16 +149,16 @@ __device__ __forceinline__ void restrict_quad(const LevelF& f, int nf, const flo
       const float4 q = Q[a][b];
       float qm = __shfl_up_sync(0xffffffffu, q.w, 1);
       float qp = __shfl_down_sync(0xffffffffu, q.x, 1);
-      if (lane == 0) qm = q1(co[a][b] + (k0 == 0 ? nf - 1 : -1));
-      if (lane == 31 || tq + 1 >= nq) qp = q1(co[a][b] + (k0 + 4 == nf ? 4 - nf : 4));
+      if (lane == 0) qm = q1(i0 + a, j0 + b, k0 == 0 ? nf - 1 : k0 - 1);
+      if (lane == 31 || tq + 1 >= nq) qp = q1(i0 + a, j0 + b, k0 + 4 == nf ? 0 : k0 + 4);
       const float4 ni = a == 0 ? qi[0][b] : Q[0][b];   // i - 1
       const float4 pi = a == 0 ? Q[1][b] : qi[1][b];   // i + 1
       const float4 nj = b == 0 ? qj[a][0] : Q[a][0];   // j - 1
       const float4 pj = b == 0 ? Q[a][1] : qj[a][1];   // j + 1
-      const float4 Sv = ld4(S + co[a][b]);
+      const float4 Sv = FL::q(S, nf, i0 + a, j0 + b, k0);
       float4 R = make_float4(1.f, 1.f, 1.f, 1.f);
       if constexpr (RHO) {
-        if (rho) R = ld4(rho + co[a][b]);
+        if (rho) R = FL::q(rho, nf, i0 + a, j0 + b, k0);
       }
       const float4 Ev = E[a][b], Uv = U[a][b];
       const float dx = local_M<K>(f, Uv.x, Ev.x, R.x, (qm + q.y) + (ni.x + pi.x) + (nj.x + pj.x)) - Sv.x;
@@ -192,7 +192,7 @@ __device__ __forceinline__ void restrict_quad(const LevelF& f, int nf, const flo
 // (2tq, 2tq+1), takes the combinations at 2tq-1 and 2tq+2 from the adjacent
 // lanes, and weights (3, 1) along k.  f(R): where u + e would not be positive
 // the total field is halved instead (e <- (e_old - u)/2).
-template <bool FR>
+template <bool FR, class FL = NatLayout>
 __device__ __forceinline__ void prolong_quad(int nc, const float* __restrict__ eH, const float* __restrict__ Re,
                                              const float* __restrict__ ub, float* __restrict__ ef, int i, int j,
                                              int tq, int lane) {
@@ -225,18 +225,17 @@ __device__ __forceinline__ void prolong_quad(int nc, const float* __restrict__ e
     Rp = 9.f * d1(rA, Kp) + 3.f * (d1(rB, Kp) + d1(rC, Kp)) + d1(rD, Kp);
   }
   constexpr float w = 1.f / 64.f;
-  const long long c = ((long long)i * nf + j) * nf + k0;
-  const float4 old = ld4(ef + c);
+  const float4 old = FL::q(ef, nf, i, j, k0);
   float4 v = make_float4(old.x + (3.f * Rx + Rm) * w, old.y + (3.f * Rx + Ry) * w, old.z + (3.f * Ry + Rx) * w,
                          old.w + (3.f * Ry + Rp) * w);
   if constexpr (FR) {
-    const float4 u = ld4(ub + c);
+    const float4 u = FL::q(ub, nf, i, j, k0);
     if (!(u.x + v.x > 0.f)) v.x = 0.5f * (old.x - u.x);
     if (!(u.y + v.y > 0.f)) v.y = 0.5f * (old.y - u.y);
     if (!(u.z + v.z > 0.f)) v.z = 0.5f * (old.z - u.z);
     if (!(u.w + v.w > 0.f)) v.w = 0.5f * (old.w - u.w);
   }
-  if (act) *reinterpret_cast<float4*>(ef + c) = v;
+  if (act) FL::st(ef, nf, i, j, k0, v);
 }
 
 // 1/x in FP64 by one Newton-Raphson refinement y1 = y0 (2 - x y0) of a
@@ -372,7 +371,7 @@ __device__ __forceinline__ ff ff_w(ff u) {
 // The CTA marches up its chunk of planes with a three-plane ring of w and u in
 // shared memory; the doubles of plane i+2 are loaded into registers while
 // plane i is computed, so the global-load latency overlaps the arithmetic.
-template <int K, int TJ, int TK>
+template <int K, int TJ, int TK, bool SPLIT = false>
 __device__ __forceinline__ double outer_residual_tile_ff(const FFC& C, int n, int chunk, const double* __restrict__ u,
                                                          const float* __restrict__ rho, float* __restrict__ ub,
                                                          float* __restrict__ tau, int tile, int cb) {
@@ -452,22 +451,23 @@ __device__ __forceinline__ double outer_residual_tile_ff(const FFC& C, int n, in
       v = ff_sub(ff_mul(C.c2, L), ff_mul(C.msym, b));
     }
     const float tv = -ff_to_float(v);
-    ub[g] = ff_to_float(uc);
-    tau[g] = tv;
+    const long long o = SPLIT ? split_idx(n, i, jg, kg) : (long long)g;  // the level's layout
+    ub[o] = ff_to_float(uc);
+    tau[o] = tv;
     acc += tv * tv;
     __syncthreads();
   }
   return block_sum((double)acc);
 }
 
-template <int K, int TJ, int TK>
+template <int K, int TJ, int TK, bool SPLIT = false>
 __global__ void __launch_bounds__(TJ* TK) k_outer_residual_ff(const FFC* __restrict__ C, int n, int chunk,
                                                               const double* __restrict__ u,
                                                               const float* __restrict__ rho,
                                                               float* __restrict__ ub, float* __restrict__ tau,
                                                               double* __restrict__ partials) {
   const FFC c = *C;
-  const double a = outer_residual_tile_ff<K, TJ, TK>(c, n, chunk, u, rho, ub, tau, blockIdx.x, blockIdx.y);
+  const double a = outer_residual_tile_ff<K, TJ, TK, SPLIT>(c, n, chunk, u, rho, ub, tau, blockIdx.x, blockIdx.y);
   if (threadIdx.x == 0) partials[blockIdx.x + blockIdx.y * gridDim.x] = a;
 }
 
@@ -489,6 +489,32 @@ static __global__ void k_density_norm32(const float* __restrict__ rho, long long
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
        t += (long long)gridDim.x * blockDim.x)
     out[t] = rho[t] * im;
+}
+
+// rho32 normalised to mean 1 into a red-black split fine level (n % 8 == 0).
+static __global__ void k_density_norm32_split(const float* __restrict__ rho, int n, const double* __restrict__ sum,
+                                              float* __restrict__ out) {
+  const long long n3 = (long long)n * n * n;
+  const float im = (float)((double)n3 / *sum);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(t % n), j = (int)((t / n) % n), i = (int)(t / ((long long)n * n));
+    out[split_idx(n, i, j, k)] = rho[t] * im;
+  }
+}
+
+// 8-child mean from a split fine level into a natural coarse level.
+static __global__ void __launch_bounds__(128) k_restrict32_from_split(int nf, const float* __restrict__ fine,
+                                                                      float* __restrict__ coarse) {
+  const int nc = nf >> 1;
+  const int I = blockIdx.z, J = blockIdx.y;
+  const int Kc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (Kc >= nc) return;
+  float s = 0.f;
+  for (int di = 0; di < 2; ++di)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int dk = 0; dk < 2; ++dk) s += fine[split_idx(nf, 2 * I + di, 2 * J + dj, 2 * Kc + dk)];
+  coarse[cidx(nc, I, J, Kc)] = 0.125f * s;
 }
 
 static __global__ void __launch_bounds__(128) k_restrict32(int nf, const float* __restrict__ fine, float* __restrict__ coarse) {

@@ -57,6 +57,55 @@ __global__ void __launch_bounds__(64) k_smooth32(LevelF f, int n, float* __restr
   e[c] = update_e_fast<K>(f, ub[c], e[c], rho ? rho[c] : 1.f, S[c], Lnb);
 }
 
+// Red-black split fine level (n % 8 == 0), one colour on the planes
+// i0 .. i0+np-1 (mod n): rows of n/8 lanes packed into warps (several short rows
+// per warp, a long row over several warps), four cells per lane; block (32, 4),
+// 1D grid over warps.
+template <int K>
+__global__ void __launch_bounds__(128) k_smooth32s(LevelF f, int n, float* __restrict__ e,
+                                                   const float* __restrict__ ub, const float* __restrict__ rho,
+                                                   const float* __restrict__ S, int colour, int i0, int np) {
+  const int nq = n >> 3, lane = threadIdx.x;
+  const long long warp = (long long)blockIdx.x * 4 + threadIdx.y;
+  const long long rows = (long long)np * n;
+  long long r;
+  int seg;
+  bool act;
+  if (nq <= 32) {
+    const int per = 32 / nq, sub = lane / nq;
+    r = warp * per + sub;
+    seg = lane - sub * nq;
+    act = sub < per;
+    if (!act) {
+      r = warp * per + per - 1;
+      seg = nq - 1;
+    }
+  } else {
+    const int W = (nq + 31) / 32;
+    r = warp / W;
+    seg = (int)(warp % W) * 32 + lane;
+    act = seg < nq;
+    if (!act) seg = nq - 1;
+  }
+  if (r >= rows) {
+    r = rows - 1;
+    act = false;
+  }
+  int i = i0 + (int)(r / n);
+  if (i >= n) i -= n;
+  smooth_split<K>(f, n, e, ub, rho, S, i, (int)(r % n), seg, act, colour, lane);
+}
+
+static long long split_warps(int n, int np) {
+  const int nq = n >> 3;
+  const long long rows = (long long)np * n;
+  if (nq <= 32) {
+    const int per = 32 / nq;
+    return (rows + per - 1) / per;
+  }
+  return rows * ((nq + 31) / 32);
+}
+
 // Quad version (levels with n % 4 == 0) on the planes i0 .. i0+np-1 (mod n):
 // block (32, 4) = four rows (i, j), grid (ceil(n/128), n, ceil(np/4)).
 template <int K>
@@ -125,9 +174,9 @@ __global__ void __launch_bounds__(128) k_residual_restrict32(LevelF f, int nf, c
   SH[t] = 0.125f * sd;
 }
 
-// Quad versions (fine side % 4 == 0): block (32, 4), lanes along k.
-// Restriction: grid (ceil(nf/128), nc [J], ceil(nc/4) [I]).
-template <int K>
+// Quad versions (fine side % 4 == 0): block (32, 4), lanes along k; FL is the
+// fine level's layout.  Restriction: grid (ceil(nf/128), nc [J], ceil(nc/4) [I]).
+template <int K, class FL = NatLayout>
 __global__ void __launch_bounds__(128) k_residual_restrict32q(LevelF f, int nf, const float* __restrict__ e,
                                                               const float* __restrict__ ub,
                                                               const float* __restrict__ rho,
@@ -136,16 +185,16 @@ __global__ void __launch_bounds__(128) k_residual_restrict32q(LevelF f, int nf, 
                                                               float* __restrict__ SH) {
   const int I = blockIdx.z * 4 + threadIdx.y;
   if (I >= (nf >> 1)) return;  // whole warps
-  restrict_quad<K>(f, nf, e, ub, rho, S, Re, eH, ubH, SH, I, blockIdx.y, blockIdx.x * 32 + threadIdx.x,
-                   threadIdx.x);
+  restrict_quad<K, FL>(f, nf, e, ub, rho, S, Re, eH, ubH, SH, I, blockIdx.y, blockIdx.x * 32 + threadIdx.x,
+                       threadIdx.x);
 }
 
 // Prolongation: grid (ceil(nf/128), nf [j], nf/4 [i]).
-template <bool FR>
+template <bool FR, class FL = NatLayout>
 __global__ void __launch_bounds__(128) k_prolong_correct32q(int nc, const float* __restrict__ eH,
                                                             const float* __restrict__ Re,
                                                             const float* __restrict__ ub, float* __restrict__ ef) {
-  prolong_quad<FR>(nc, eH, Re, ub, ef, blockIdx.z * 4 + threadIdx.y, blockIdx.y, blockIdx.x * 32 + threadIdx.x,
+  prolong_quad<FR, FL>(nc, eH, Re, ub, ef, blockIdx.z * 4 + threadIdx.y, blockIdx.y, blockIdx.x * 32 + threadIdx.x,
                    threadIdx.x);
 }
 
@@ -192,6 +241,16 @@ __global__ void __launch_bounds__(128) k_prolong_correct32(int nc, const float* 
 // FP64 outer-loop kernels (fine level)
 // ---------------------------------------------------------------------------
 
+// u64 += e with e in the split layout.
+__global__ void k_apply_correction_split(double* __restrict__ u, const float* __restrict__ e, int n) {
+  const long long n3 = (long long)n * n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(t % n), j = (int)((t / n) % n), i = (int)(t / ((long long)n * n));
+    u[t] += (double)e[split_idx(n, i, j, k)];
+  }
+}
+
 // u64 += e (the correction of one inner solve).
 __global__ void k_apply_correction(double* __restrict__ u, const float* __restrict__ e, long long n3) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
@@ -227,6 +286,7 @@ struct MixedCtx {
   bool need_rho;
   int chunk;          // planes per CTA of the fused sweep
   const float* rho;   // the caller's density (the float-float residual forms its source from it)
+  bool split;         // the finest level in the red-black split layout
   bool ff_resid;      // fine residual in float-float (f(R), symmetron) rather than FP64 (CQ)
   int tail_level;     // first level (>= 1) run by the one-block tail kernel, or -1
 };
@@ -288,8 +348,15 @@ static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
       L.e_alt = tmp;
     } else if (L.n % 4 == 0 && L.n >= 16) {
       const int P = slab_planes(C, L.n);
+      const bool split = l == 0 && C.split;
       auto colour = [&](int parity, int i0, int np) -> int {
         if (np <= 0) return MGGLAM_OK;
+        if (split) {
+          const unsigned blocks = (unsigned)((split_warps(L.n, np) + 3) / 4);
+          MG_DISPATCH32(C.m.kind, (k_smooth32s<KK><<<blocks, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, rho,
+                                                                                   L.S32, parity, i0, np)));
+          return MGGLAM_OK;
+        }
         const dim3 g((L.n / 4 + 31) / 32, L.n, (np + 3) / 4);
         MG_DISPATCH32(C.m.kind, (k_smooth32q<KK><<<g, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, rho, L.S32,
                                                                             parity, i0, np)));
@@ -458,7 +525,11 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode) {
   const float* rhoH = C.need_rho ? H.rho32 : nullptr;
   const int bh = bx_for(H.n);
   if (l == 0) prof_begin(PC_RESTRICT32_FINE, st, 14.0 * L.n3);
-  if (L.n % 4 == 0 && L.n >= 8) {
+  if (l == 0 && C.split) {
+    const dim3 g((L.n / 4 + 31) / 32, H.n, (H.n + 3) / 4);
+    MG_DISPATCH32(C.m.kind, (k_residual_restrict32q<KK, SplitLayout><<<g, dim3(32, 4), 0, st>>>(
+                                 C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32)));
+  } else if (L.n % 4 == 0 && L.n >= 8) {
     const dim3 g((L.n / 4 + 31) / 32, H.n, (H.n + 3) / 4);
     MG_DISPATCH32(C.m.kind, (k_residual_restrict32q<KK><<<g, dim3(32, 4), 0, st>>>(
                                  C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32)));
@@ -478,7 +549,11 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode) {
   }
   if (l == 0) { prof_end(st); prof_begin(PC_PROLONG32_FINE, st, 13.0 * L.n3); }
   const int bf = bx_for(L.n);
-  if (L.n % 4 == 0 && L.n >= 8) {
+  if (l == 0 && C.split) {
+    const dim3 g((L.n / 4 + 31) / 32, L.n, L.n / 4);
+    if (is_fr(C.m.kind)) k_prolong_correct32q<true, SplitLayout><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
+    else k_prolong_correct32q<false, SplitLayout><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
+  } else if (L.n % 4 == 0 && L.n >= 8) {
     const dim3 g((L.n / 4 + 31) / 32, L.n, L.n / 4);
     if (is_fr(C.m.kind)) k_prolong_correct32q<true><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
     else k_prolong_correct32q<false><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
@@ -508,8 +583,12 @@ static int launch_outer_residual_ff(const MixedCtx& C, double* field, int* block
     dim3 grid((F.n / kRTK) * (F.n / kRTJ), (F.n + chunk - 1) / chunk);
     *blocks = grid.x * grid.y;
     if (*blocks > kMaxReduceBlocks) return MGGLAM_ERR_SHAPE;
-    k_outer_residual_ff<K, kRTJ, kRTK><<<grid, kRTJ * kRTK, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub, F.S32,
-                                                                     ws->partials);
+    if (C.split)
+      k_outer_residual_ff<K, kRTJ, kRTK, true><<<grid, kRTJ * kRTK, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub,
+                                                                             F.S32, ws->partials);
+    else
+      k_outer_residual_ff<K, kRTJ, kRTK><<<grid, kRTJ * kRTK, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub, F.S32,
+                                                                       ws->partials);
     return MGGLAM_OK;
   }
   const int tk = (F.n % 16 == 0) ? 16 : ((F.n % 8 == 0) ? 8 : ((F.n % 4 == 0) ? 4 : 2));
@@ -582,6 +661,8 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
   C.chunk = prm->sweep_chunk > 0 ? prm->sweep_chunk : 16;  // < 0: per-colour kernels only
   C.rho = rho;
   C.ff_resid = C.m.kind != KCQ;
+  // red-black split fine level: float-float residual with its 8 x 32 tiles, per-colour smoothing
+  C.split = C.ff_resid && prm->sweep_chunk <= 0 && C.ws->lev[0].n % 32 == 0;
   C.tail_level = -1;  // the one-block tail runs V-cycles only
   const long long tail_cells = prm->tail_cells == 0 ? 512 : (prm->tail_cells > kTailMaxCells ? kTailMaxCells : prm->tail_cells);
   for (int l = 1; l < C.ws->nlev && tail_cells > 0 && prm->cycle == 0; ++l)
@@ -605,12 +686,17 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
                                  C.m, rho, n3, ws->scalars + SC_MEAN, ws->src64)));
   }
   if (C.need_rho) {
-    k_density_norm32<<<stream_grid(n3), kThreads, 0, st>>>(rho, n3, ws->scalars + SC_MEAN, F.rho32);
+    if (C.split) k_density_norm32_split<<<stream_grid(n3), kThreads, 0, st>>>(rho, F.n, ws->scalars + SC_MEAN, F.rho32);
+    else k_density_norm32<<<stream_grid(n3), kThreads, 0, st>>>(rho, n3, ws->scalars + SC_MEAN, F.rho32);
     note_launch(1);
     for (int l = 1; l < ws->nlev; ++l) {
       const int b = bx_for(ws->lev[l].n);
-      k_restrict32<<<grid3(ws->lev[l].n, ws->lev[l].n, ws->lev[l].n, b), b, 0, st>>>(
-          ws->lev[l - 1].n, ws->lev[l - 1].rho32, ws->lev[l].rho32);
+      if (l == 1 && C.split)
+        k_restrict32_from_split<<<grid3(ws->lev[l].n, ws->lev[l].n, ws->lev[l].n, b), b, 0, st>>>(
+            ws->lev[l - 1].n, ws->lev[l - 1].rho32, ws->lev[l].rho32);
+      else
+        k_restrict32<<<grid3(ws->lev[l].n, ws->lev[l].n, ws->lev[l].n, b), b, 0, st>>>(
+            ws->lev[l - 1].n, ws->lev[l - 1].rho32, ws->lev[l].rho32);
       note_launch(1);
     }
   }
@@ -654,7 +740,8 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
     for (int c = 0; c < inner && cyc < prm->max_cycles; ++c, ++cyc, ++done)
       if ((rc = vcycle32(C, 0, st, C.prm->cycle))) return rc;
     prof_begin(PC_APPLY_CORR, st, 20.0 * n3);
-    k_apply_correction<<<stream_grid(n3), kThreads, 0, st>>>(field, F.e, n3);
+    if (C.split) k_apply_correction_split<<<stream_grid(n3), kThreads, 0, st>>>(field, F.e, F.n);
+    else k_apply_correction<<<stream_grid(n3), kThreads, 0, st>>>(field, F.e, n3);
     note_launch(1);
     prof_end(st);
     ++outer;

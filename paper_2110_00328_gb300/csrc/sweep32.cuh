@@ -292,6 +292,144 @@ __device__ __forceinline__ void smooth_quad(const LevelF& f, int n, float* __res
   }
 }
 
+// ---------------------------------------------------------------------------
+// Red-black split layout (the finest level)
+// ---------------------------------------------------------------------------
+//
+// A level of side n (n % 8 == 0) stores each colour contiguously: cell
+// (i, j, k) of colour c = (i+j+k) & 1 at c H + (i n + j) h + k/2, with h = n/2
+// and H = n^2 h.  A colour pass then reads only that colour's u and S and the
+// other colour's e and u (its neighbours): ~10 bytes a cell instead of the
+// ~14 a pass over interleaved colours moves.  The neighbours (i, j+-1, k) and
+// (i+-1, j, k) of a cell sit at the same k/2 of the other colour's adjacent
+// rows; (i, j, k+-1) at k/2 - 1 + p and k/2 + p of the same row, p = k & 1.
+
+__device__ __forceinline__ long long split_idx(int n, int i, int j, int k) {
+  const int h = n >> 1;
+  return (long long)((i + j + k) & 1) * ((long long)n * n * h) + ((long long)i * n + j) * h + (k >> 1);
+}
+
+__device__ __forceinline__ float2 ld2s(const float* p) { return *reinterpret_cast<const float2*>(p); }
+
+// The interleaved quad k0 .. k0+3 (k0 % 4 == 0) of row (i, j) of a split array.
+__device__ __forceinline__ float4 ld4_split(const float* a, int n, int i, int j, int k0) {
+  const int h = n >> 1;
+  const long long H = (long long)n * n * h, r = ((long long)i * n + j) * h + (k0 >> 1);
+  const float2 b = ld2s(a + r), q = ld2s(a + H + r);
+  return ((i + j) & 1) ? make_float4(q.x, b.x, q.y, b.y) : make_float4(b.x, q.x, b.y, q.y);
+}
+
+__device__ __forceinline__ void st4_split(float* a, int n, int i, int j, int k0, float4 v) {
+  const int h = n >> 1;
+  const long long H = (long long)n * n * h, r = ((long long)i * n + j) * h + (k0 >> 1);
+  float2 b, q;
+  if ((i + j) & 1) {
+    q = make_float2(v.x, v.z);
+    b = make_float2(v.y, v.w);
+  } else {
+    b = make_float2(v.x, v.z);
+    q = make_float2(v.y, v.w);
+  }
+  *reinterpret_cast<float2*>(a + r) = b;
+  *reinterpret_cast<float2*>(a + H + r) = q;
+}
+
+// Access to a level as interleaved quads: natural layout or red-black split.
+struct NatLayout {
+  static __device__ __forceinline__ float4 q(const float* a, int n, int i, int j, int k0) {
+    return ld4(a + ((long long)i * n + j) * n + k0);
+  }
+  static __device__ __forceinline__ void st(float* a, int n, int i, int j, int k0, float4 v) {
+    *reinterpret_cast<float4*>(a + ((long long)i * n + j) * n + k0) = v;
+  }
+  static __device__ __forceinline__ long long idx(int n, int i, int j, int k) { return ((long long)i * n + j) * n + k; }
+};
+struct SplitLayout {
+  static __device__ __forceinline__ float4 q(const float* a, int n, int i, int j, int k0) {
+    return ld4_split(a, n, i, j, k0);
+  }
+  static __device__ __forceinline__ void st(float* a, int n, int i, int j, int k0, float4 v) {
+    st4_split(a, n, i, j, k0, v);
+  }
+  static __device__ __forceinline__ long long idx(int n, int i, int j, int k) { return split_idx(n, i, j, k); }
+};
+
+// One colour pass on a split level: a lane owns four consecutive cells
+// m0 .. m0+3 (k = 2m + p, p = (i+j+colour) & 1) of the colour being updated
+// in row (i, j).  Rows are packed into warps in segments of nq = n/8 lanes
+// ('seg' = the lane's position in its row, 'nq' lanes per row; a row longer
+// than a warp continues in the next warp); all 32 lanes call this together
+// (the shuffles), idle lanes with act = false and a valid (clamped) cell.  Reads: the
+// colour's u, S (and e, rho where the model uses them) at m0 .. m0+3, the other
+// colour's e and u at m0 .. m0+3 of the same row and of the rows (i, j+-1),
+// (i+-1, j); the one k-neighbour outside that window comes from the adjacent
+// lane (p = 0: m0 - 1; p = 1: m0 + 4), or a load at a row end.
+template <int K>
+__device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __restrict__ e,
+                                             const float* __restrict__ ub, const float* __restrict__ rho,
+                                             const float* __restrict__ S, int i, int j, int seg, bool act,
+                                             int colour, int lane) {
+  constexpr bool FR = is_fr(K);
+  constexpr bool RHO = (K == KSYM) || (K == KCQ);
+  const int h = n >> 1, nq = h >> 2;
+  const int m0 = 4 * seg;
+  const long long H = (long long)n * n * h;
+  const long long r0 = ((long long)i * n + j) * h + m0;
+  const long long djp = (j + 1 < n) ? (long long)h : -(long long)(n - 1) * h;
+  const long long djm = (j > 0) ? -(long long)h : (long long)(n - 1) * h;
+  const long long nh = (long long)n * h;
+  const long long dip = (i + 1 < n) ? nh : -(long long)(n - 1) * nh;
+  const long long dim = (i > 0) ? -nh : (long long)(n - 1) * nh;
+  const int p = (i + j + colour) & 1;
+  float* eo = e + (long long)colour * H + r0;               // own colour
+  const float* e1 = e + (long long)(colour ^ 1) * H + r0;   // other colour
+  const float* uo = ub + (long long)colour * H + r0;
+  const float* u1 = ub + (long long)(colour ^ 1) * H + r0;
+  const float4 U = ld4(uo), Sv = ld4(S + (long long)colour * H + r0);
+  float4 E = make_float4(0.f, 0.f, 0.f, 0.f);
+  if constexpr (!FR) E = ld4(eo);
+  float4 R = make_float4(1.f, 1.f, 1.f, 1.f);
+  if constexpr (RHO) {
+    if (rho) R = ld4(rho + (long long)colour * H + r0);
+  }
+  const float4 Er = ld4(e1);
+  const float4 Ejp = ld4(e1 + djp), Ejm = ld4(e1 + djm), Eip = ld4(e1 + dip), Eim = ld4(e1 + dim);
+  float4 Ur = make_float4(0.f, 0.f, 0.f, 0.f), Ujp = Ur, Ujm = Ur, Uip = Ur, Uim = Ur;
+  if constexpr (FR) {
+    Ur = ld4(u1);
+    Ujp = ld4(u1 + djp);
+    Ujm = ld4(u1 + djm);
+    Uip = ld4(u1 + dip);
+    Uim = ld4(u1 + dim);
+  }
+  const float4 Q = make_float4(nbq<K>(Ur.x, Er.x), nbq<K>(Ur.y, Er.y), nbq<K>(Ur.z, Er.z), nbq<K>(Ur.w, Er.w));
+  float qm = __shfl_up_sync(0xffffffffu, Q.w, 1);    // other colour at m0 - 1
+  float qp = __shfl_down_sync(0xffffffffu, Q.x, 1);  // other colour at m0 + 4
+  if (p == 0 && (seg == 0 || lane == 0)) {
+    const long long c = r0 + (m0 == 0 ? h - 1 : -1);
+    qm = nbq<K>(FR ? ub[(long long)(colour ^ 1) * H + c] : 0.f, e[(long long)(colour ^ 1) * H + c]);
+  }
+  if (p == 1 && (seg == nq - 1 || lane == 31)) {
+    const long long c = r0 + (m0 + 4 == h ? 4 - h : 4);
+    qp = nbq<K>(FR ? ub[(long long)(colour ^ 1) * H + c] : 0.f, e[(long long)(colour ^ 1) * H + c]);
+  }
+  // the two k-neighbours of own cell t: other-colour m0+t-1+p and m0+t+p
+  const float k0s = p ? Q.x + Q.y : qm + Q.x;
+  const float k1s = p ? Q.y + Q.z : Q.x + Q.y;
+  const float k2s = p ? Q.z + Q.w : Q.y + Q.z;
+  const float k3s = p ? Q.w + qp : Q.z + Q.w;
+  const float L0 = k0s + (nbq<K>(Ujp.x, Ejp.x) + nbq<K>(Ujm.x, Ejm.x)) + (nbq<K>(Uip.x, Eip.x) + nbq<K>(Uim.x, Eim.x));
+  const float L1 = k1s + (nbq<K>(Ujp.y, Ejp.y) + nbq<K>(Ujm.y, Ejm.y)) + (nbq<K>(Uip.y, Eip.y) + nbq<K>(Uim.y, Eim.y));
+  const float L2 = k2s + (nbq<K>(Ujp.z, Ejp.z) + nbq<K>(Ujm.z, Ejm.z)) + (nbq<K>(Uip.z, Eip.z) + nbq<K>(Uim.z, Eim.z));
+  const float L3 = k3s + (nbq<K>(Ujp.w, Ejp.w) + nbq<K>(Ujm.w, Ejm.w)) + (nbq<K>(Uip.w, Eip.w) + nbq<K>(Uim.w, Eim.w));
+  float4 out;
+  out.x = update_e_fast<K>(f, U.x, E.x, R.x, Sv.x, L0);
+  out.y = update_e_fast<K>(f, U.y, E.y, R.y, Sv.y, L1);
+  out.z = update_e_fast<K>(f, U.z, E.z, R.z, Sv.z, L2);
+  out.w = update_e_fast<K>(f, U.w, E.w, R.w, Sv.w, L3);
+  if (act) *reinterpret_cast<float4*>(eo) = out;
+}
+
 }  // namespace mg
 
 namespace mg {

@@ -172,19 +172,22 @@ def test_mixed_solve_matches_oracle(orc, mg, key):
         assert abs(got.mean() - ref.u.mean()) <= bound
 
 
+@pytest.mark.parametrize("chunk", [8, 0])
 @pytest.mark.parametrize("key", ["fr1", "sym"])
 @pytest.mark.parametrize("N", [64, 96])
-def test_mixed_iterates_follow_oracle_vcycles(orc, mg, key, N):
+def test_mixed_iterates_follow_oracle_vcycles(orc, mg, key, N, chunk):
     """One inner FP32 V-cycle in correction form reproduces, up to single
     precision, the oracle's FP64 V-cycle on the total field (same red-black
-    order, transfers and coarse solve): compare after 1, 2 and 3 cycles.  The
-    64^3 and 96^3 meshes run the fused sweep kernel on their fine levels."""
+    order, transfers and coarse solve): compare after 1, 2 and 3 cycles.
+    chunk = 8: the fused sweep kernel on every tileable level (natural layout);
+    chunk = 0: per-colour kernels with the fine level in the red-black split
+    layout (several 8-lane rows per warp at 64^3, 12-lane rows at 96^3)."""
     rho = inputs.lognormal_density(N, 1.0, seed=50 + N)
     rho32 = rho.astype(np.float32)
     box = float(N) if key == "sym" else 2.0 * N
     for cycles in (1, 2, 3):
         # sweep_chunk > 0 forces the fused sweep kernel on every tileable level
-        po, pg = both_params(orc, mg, key, box=box, precision=1, max_cycles=cycles, sweep_chunk=8)
+        po, pg = both_params(orc, mg, key, box=box, precision=1, max_cycles=cycles, sweep_chunk=chunk)
         ref = orc.solve(po, rho32.astype(np.float64), tol=0.0, max_cycles=cycles)
         field = torch.full((N, N, N), float("nan"), dtype=torch.float64, device="cuda")
         mg.solve_scalar(pg, 1.0, cuda32(rho32), field, 0.0, allow_unconverged=True)
