@@ -63,6 +63,12 @@ __device__ __forceinline__ float fsqrt(float x) {
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(fmaxf(x, 0.f)));
   return y;
 }
+// sqrt(x) for x known to be >= 0
+__device__ __forceinline__ float fsqrt_nn(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 // Newton polishing steps after the closed-form start of the local solve.  The
 // start inherits the single-precision cancellation in the polynomial's
@@ -99,7 +105,7 @@ __device__ __forceinline__ float fr_root_scaled_fast(float p) {
     const float p3 = p * (1.f / 3.f);
     const float D = 0.25f + p3 * p3 * p3;
     if (D >= 0.f) {
-      const float A = fcbrt_pos(0.5f + fsqrt(D));
+      const float A = fcbrt_pos(0.5f + fsqrt_nn(D));
       const float B = fdiv(p3, A);
       return frcp(A * A + p3 + B * B);
     }
@@ -160,8 +166,11 @@ __device__ __forceinline__ float update_e_fast(const LevelF& f, float u, float e
     const float U = f.fr_s * fr_root_scaled_fast<K>(p * f.fr_is1);
     float x = U - u;
     // Newton steps on G(x) = Delta w(x) + al K x/(u(u+x)) - B (no cancellation
-    // in x) bring x to single-precision relative accuracy
+    // in x) bring x to single-precision relative accuracy.  From the closed-form
+    // start (relative error <= ~1e-4) they stay on the positive branch; should
+    // the result not be a positive total field, the closed-form root is kept.
     const float ru = frcp(u);
+    const float x0 = x;
 #pragma unroll
     for (int it = 0; it < kPolishSteps; ++it) {
       const float Ue = u + x;
@@ -171,10 +180,9 @@ __device__ __forceinline__ float update_e_fast(const LevelF& f, float u, float e
       if constexpr (K == KFR0) dG += 1.f;
       else if constexpr (K == KFR1) dG += 2.f * Ue;
       else dG += 3.f * Ue * Ue;
-      const float xn = x - fdiv(G, dG);
-      x = (u + xn > 0.f) ? xn : x;
+      x -= fdiv(G, dG);
     }
-    return x;
+    return (u + x > 0.f) ? x : x0;
   } else if constexpr (K == KSYM) {
     const float p = rho * f.rat3 - 1.f + 12.f * f.al;
     const float B = 2.f * f.al * Lnb - fdiv(s, f.msym);
