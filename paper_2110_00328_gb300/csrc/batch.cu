@@ -31,6 +31,7 @@ namespace mg {
 struct BDesc {
   int n;      // level side
   int solve;  // index of the solve in the batch
+  int split;  // this level (the finest) in the red-black split layout
   LevelF lf;  // constants of this level
   float *e, *ub, *S, *rho, *Re;      // this level
   float *eH, *ubH, *SH, *ReH;        // next coarser level (if any)
@@ -74,6 +75,14 @@ __global__ void __launch_bounds__(32 * ROWS) kb_smooth(const BDesc* __restrict__
   if (!active[d.solve]) return;
   const int n = d.n;
   const int b = blockIdx.x - prefix[s];
+  if (d.split) {
+    long long r;
+    int seg;
+    bool act;
+    split_lane(n, n, (long long)b * ROWS + threadIdx.y, threadIdx.x, &r, &seg, &act);
+    smooth_split<K>(d.lf, n, d.e, d.ub, d.rho, d.S, (int)(r / n), (int)(r % n), seg, act, parity, threadIdx.x);
+    return;
+  }
   if (quad_level(n)) {
     const int nbx = ((n >> 2) + 31) / 32;
     const int xb = b % nbx, r = b / nbx, j = r % n, i = (r / n) * ROWS + threadIdx.y;
@@ -91,7 +100,8 @@ __global__ void __launch_bounds__(32 * ROWS) kb_smooth(const BDesc* __restrict__
   d.e[c] = update_e_fast<K>(d.lf, d.ub[c], d.e[c], d.rho ? d.rho[c] : 1.f, d.S[c], Lnb);
 }
 
-static int smooth_blocks(int n, int rows) {
+static int smooth_blocks(int n, int rows, bool split) {
+  if (split) return (int)((split_warps(n, n) + rows - 1) / rows);
   if (quad_level(n)) return (((n >> 2) + 31) / 32) * n * ((n + rows - 1) / rows);
   return (int)(((long long)(n >> 1) * n * n + 32 * rows - 1) / (32 * rows));
 }
@@ -111,8 +121,12 @@ __global__ void __launch_bounds__(128) kb_restrict(const BDesc* __restrict__ D, 
     const int nbx = ((nf >> 2) + 31) / 32;
     const int xb = b % nbx, r = b / nbx, J = r % nc, I = (r / nc) * 4 + threadIdx.y;
     if (I >= nc) return;  // whole warps
-    restrict_quad<K>(d.lf, nf, d.e, d.ub, d.rho, d.S, d.ReH, d.eH, d.ubH, d.SH, I, J, xb * 32 + threadIdx.x,
-                     threadIdx.x);
+    if (d.split)
+      restrict_quad<K, SplitLayout>(d.lf, nf, d.e, d.ub, d.rho, d.S, d.ReH, d.eH, d.ubH, d.SH, I, J,
+                                    xb * 32 + threadIdx.x, threadIdx.x);
+    else
+      restrict_quad<K>(d.lf, nf, d.e, d.ub, d.rho, d.S, d.ReH, d.eH, d.ubH, d.SH, I, J, xb * 32 + threadIdx.x,
+                       threadIdx.x);
     return;
   }
   const long long t = (long long)b * 128 + threadIdx.y * 32 + threadIdx.x;
@@ -173,7 +187,8 @@ __global__ void __launch_bounds__(128) kb_prolong(const BDesc* __restrict__ D, c
     const int nbx = ((nf >> 2) + 31) / 32;
     const int xb = b % nbx, r = b / nbx, j = r % nf, i = (r / nf) * 4 + threadIdx.y;
     if (i >= nf) return;  // whole warps
-    prolong_quad<FR>(nc, d.eH, d.ReH, d.ub, d.e, i, j, xb * 32 + threadIdx.x, threadIdx.x);
+    if (d.split) prolong_quad<FR, SplitLayout>(nc, d.eH, d.ReH, d.ub, d.e, i, j, xb * 32 + threadIdx.x, threadIdx.x);
+    else prolong_quad<FR>(nc, d.eH, d.ReH, d.ub, d.e, i, j, xb * 32 + threadIdx.x, threadIdx.x);
     return;
   }
   const long long t = (long long)b * 128 + threadIdx.y * 32 + threadIdx.x;
@@ -234,7 +249,7 @@ __global__ void __launch_bounds__(256) kb_outer_residual(const BFine* __restrict
       a = outer_residual_tile<K, 8, 32>(f.m, f.n, 64, f.u, f.src, f.ub, f.tau, b % tiles, b / tiles);
     } else {
       const FFC c = *f.ffc;
-      a = outer_residual_tile_ff<K, 8, 32>(c, f.n, 64, f.u, f.rho, f.ub, f.tau, b % tiles, b / tiles);
+      a = outer_residual_tile_ff<K, 8, 32, true>(c, f.n, 64, f.u, f.rho, f.ub, f.tau, b % tiles, b / tiles);
     }
   }
   if (threadIdx.x == 0) partials[blockIdx.x] = a;
@@ -259,8 +274,12 @@ __global__ void __launch_bounds__(256) kb_apply(const BFine* __restrict__ F, con
   const size_t n3 = (size_t)f.n * f.n * f.n;
   const size_t t = (size_t)(blockIdx.x - prefix[s]) * 256 + threadIdx.x;
   if (t >= n3) return;
-  if (!clear_only) f.u[t] += (double)f.e[t];
-  f.e[t] = 0.f;
+  // f(R) and symmetron fine levels are split (float-float residual); CQ keeps the natural layout
+  const long long c = f.m.kind == KCQ ? (long long)t
+                                      : split_idx(f.n, (int)(t / ((size_t)f.n * f.n)), (int)((t / f.n) % f.n),
+                                                  (int)(t % f.n));
+  if (!clear_only) f.u[t] += (double)f.e[c];
+  f.e[c] = 0.f;
 }
 
 // ---------------------------------------------------------------------------
@@ -460,6 +479,7 @@ static int build_plan(Batch* B, const std::vector<ModelDev>& models, const std::
     memset(&d, 0, sizeof(d));
     d.n = v.N >> l;
     d.solve = s;
+    d.split = (l == 0 && models[s].kind != KCQ) ? 1 : 0;  // split finest level (float-float residual)
     d.lf = lfs[s][l];
     d.e = v.e[l];
     d.ub = v.ub[l];
@@ -489,7 +509,7 @@ static int build_plan(Batch* B, const std::vector<ModelDev>& models, const std::
         const int n = B->sv[s].N >> l;
         if (l < last) {
           sm.push_back(desc(s, l));
-          bsm.push_back(smooth_blocks(n, rows));
+          bsm.push_back(smooth_blocks(n, rows, l == 0 && models[s].kind != KCQ));
           bre.push_back(restrict_blocks(n));
           bpr.push_back(prolong_blocks(n));
           fa.push_back(desc(s, l + 1));
@@ -526,7 +546,7 @@ static int build_plan(Batch* B, const std::vector<ModelDev>& models, const std::
         const int n = B->sv[s].N >> l;
         if (l < last) {
           sm.push_back(desc(s, l));
-          bsm.push_back(smooth_blocks(n, rows));
+          bsm.push_back(smooth_blocks(n, rows, l == 0 && models[s].kind != KCQ));
           bre.push_back(restrict_blocks(n));
           bpr.push_back(prolong_blocks(n));
           fa.push_back(desc(s, l + 1));
@@ -684,10 +704,15 @@ int solve_batch(int count, const mgglam_params* prm, const double* a, const floa
     } else {
       k_ff_consts<<<1, 32, 0, st>>>(models[s], n3, B->rmean + s, B->ffc + s);
     }
-    k_density_norm32<<<stream_grid(n3), kThreads, 0, st>>>(rho[s], n3, B->rmean + s, v.rho32[0]);
+    const bool split = models[s].kind != KCQ;
+    if (split) k_density_norm32_split<<<stream_grid(n3), kThreads, 0, st>>>(rho[s], v.N, B->rmean + s, v.rho32[0]);
+    else k_density_norm32<<<stream_grid(n3), kThreads, 0, st>>>(rho[s], n3, B->rmean + s, v.rho32[0]);
     for (int l = 1; l < v.nlev; ++l) {
       const int nc = v.N >> l;
-      k_restrict32<<<dim3((nc + 63) / 64, nc, nc), 64, 0, st>>>(v.N >> (l - 1), v.rho32[l - 1], v.rho32[l]);
+      if (l == 1 && split)
+        k_restrict32_from_split<<<dim3((nc + 63) / 64, nc, nc), 64, 0, st>>>(v.N, v.rho32[0], v.rho32[1]);
+      else
+        k_restrict32<<<dim3((nc + 63) / 64, nc, nc), 64, 0, st>>>(v.N >> (l - 1), v.rho32[l - 1], v.rho32[l]);
     }
     if ((rc = launch_init_background(models[s], field[s], (size_t)n3, st))) return rc;
     MG_BDISPATCH(models[s].kind, (k_src_sumsq32<KK><<<stream_grid(n3), kThreads, 0, st>>>(

@@ -65,45 +65,15 @@ template <int K>
 __global__ void __launch_bounds__(128) k_smooth32s(LevelF f, int n, float* __restrict__ e,
                                                    const float* __restrict__ ub, const float* __restrict__ rho,
                                                    const float* __restrict__ S, int colour, int i0, int np) {
-  const int nq = n >> 3, lane = threadIdx.x;
+  const int lane = threadIdx.x;
   const long long warp = (long long)blockIdx.x * 4 + threadIdx.y;
-  const long long rows = (long long)np * n;
   long long r;
   int seg;
   bool act;
-  if (nq <= 32) {
-    const int per = 32 / nq, sub = lane / nq;
-    r = warp * per + sub;
-    seg = lane - sub * nq;
-    act = sub < per;
-    if (!act) {
-      r = warp * per + per - 1;
-      seg = nq - 1;
-    }
-  } else {
-    const int W = (nq + 31) / 32;
-    r = warp / W;
-    seg = (int)(warp % W) * 32 + lane;
-    act = seg < nq;
-    if (!act) seg = nq - 1;
-  }
-  if (r >= rows) {
-    r = rows - 1;
-    act = false;
-  }
+  split_lane(n, np, warp, lane, &r, &seg, &act);
   int i = i0 + (int)(r / n);
   if (i >= n) i -= n;
   smooth_split<K>(f, n, e, ub, rho, S, i, (int)(r % n), seg, act, colour, lane);
-}
-
-static long long split_warps(int n, int np) {
-  const int nq = n >> 3;
-  const long long rows = (long long)np * n;
-  if (nq <= 32) {
-    const int per = 32 / nq;
-    return (rows + per - 1) / per;
-  }
-  return rows * ((nq + 31) / 32);
 }
 
 // Quad version (levels with n % 4 == 0) on the planes i0 .. i0+np-1 (mod n):

@@ -342,6 +342,47 @@ __device__ __forceinline__ void st4_split(float* a, int n, int i, int j, int k0,
   *reinterpret_cast<float2*>(a + H + r) = q;
 }
 
+// Lane -> (row, position in row) of a split-level colour pass over np planes:
+// rows of nq = n/8 lanes packed 32/nq to a warp (nq <= 32), or spread over
+// ceil(nq/32) warps.  Lanes with nothing to do get act = false and a valid
+// (clamped) cell, since all 32 lanes take part in the pass's shuffles.
+__device__ __forceinline__ void split_lane(int n, int np, long long warp, int lane, long long* r, int* seg,
+                                           bool* act) {
+  const int nq = n >> 3;
+  const long long rows = (long long)np * n;
+  if (nq <= 32) {
+    const int per = 32 / nq, sub = lane / nq;
+    *r = warp * per + sub;
+    *seg = lane - sub * nq;
+    *act = sub < per;
+    if (!*act) {
+      *r = warp * per + per - 1;
+      *seg = nq - 1;
+    }
+  } else {
+    const int W = (nq + 31) / 32;
+    *r = warp / W;
+    *seg = (int)(warp % W) * 32 + lane;
+    *act = *seg < nq;
+    if (!*act) *seg = nq - 1;
+  }
+  if (*r >= rows) {
+    *r = rows - 1;
+    *act = false;
+  }
+}
+
+// Warps of one split-level colour pass over np planes.
+static inline long long split_warps(int n, int np) {
+  const int nq = n >> 3;
+  const long long rows = (long long)np * n;
+  if (nq <= 32) {
+    const int per = 32 / nq;
+    return (rows + per - 1) / per;
+  }
+  return rows * ((nq + 31) / 32);
+}
+
 // Access to a level as interleaved quads: natural layout or red-black split.
 struct NatLayout {
   static __device__ __forceinline__ float4 q(const float* a, int n, int i, int j, int k0) {
