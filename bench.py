@@ -157,6 +157,12 @@ def reduce_max(x: float, world: int, device) -> float:
     return float(t.item())
 
 
+def job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job throughput in millions per second: every rank processes
+    units_per_rank; the job takes the slowest rank's time (max over ranks)."""
+    return units_per_rank * world / (max_ms * 1e-3) / 1e6
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -374,9 +380,27 @@ def run_adjoint_extra(mg, torch, dev) -> dict:
     mg.solve_scalar(p64, 1.0, rho0, f64, tol, allow_unconverged=True)
     torch.cuda.synchronize()
     fp64_ms = (time.perf_counter() - a) * 1e3
+    # the library calls alone (no loss, no torch glue): forward solve and adjoint solve
+    pf = mg.Params(**{**prm.__dict__, "fR0_abs": 1e-5})
+    fld = torch.full((N,) * 3, float("nan"), dtype=torch.float64, device=dev)
+    g = torch.from_numpy(np.random.default_rng(6).normal(size=(N, N, N))).to(dev)
+    raw = {}
+    for rep in range(2):
+        fld.fill_(float("nan"))
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        st_f = mg.solve_scalar(pf, 1.0, rho0, fld, tol)
+        torch.cuda.synchronize()
+        b = time.perf_counter()
+        mg.solve_adjoint(pf, 1.0, fld, rho0, g, tol=tol * 0.1)
+        torch.cuda.synchronize()
+        c = time.perf_counter()
+        raw = {"solve_ms": round((b - a) * 1e3, 2), "adjoint_solve_ms": round((c - b) * 1e3, 2),
+               "solve_cycles": st_f.cycles}
     return {"workload": "fR n=1 |fR0|=1e-5 512^3 box 512 lognormal sigma_g 1.5 seed 3; loss sum_b log P_F(k_b), "
                         "32 log bins; tol 1e-10",
             "forward_ms": round(f_ms, 2), "backward_ms": round(b_ms, 2), "plain_fp64_forward_ms": round(fp64_ms, 2),
+            "library_calls": raw,
             "grad_logfR0": g_th, "fd_logfR0": fdt, "rel_err_logfR0": abs(g_th - fdt) / abs(fdt),
             "grad_dir": adj, "fd_dir": fdd, "rel_err_density_dir": abs(adj - fdd) / abs(fdd)}
 
@@ -455,7 +479,7 @@ def run_ours(args) -> None:
     total_ms = reduce_max(total_ms, world, dev)
     cycles = [st.cycles for st, _ in recs]
     ups_rank = sum(c * updates_per_cycle(N_MESH, prm.nu1, prm.nu2, prm.coarse_sweeps, prm.cycle) for c in cycles)
-    value = ups_rank * world / (total_ms * 1e-3) / 1e6
+    value = job_rate(ups_rank, world, total_ms)
 
     # end to end through the public API with host buffers (pinned), H2D + D2H inside the timing
     pos_host = torch.from_numpy(pos_h).pin_memory()
