@@ -27,8 +27,10 @@
 #include <chrono>
 #include <mutex>
 
+#include "ff.cuh"
 #include "mg_common.cuh"
 #include "mg_internal.h"
+#include "sweep32.cuh"
 
 namespace mg {
 
@@ -95,6 +97,77 @@ __global__ void k_adj_residual64(int n, double kappa, const double* __restrict__
   if (threadIdx.x == 0) partials2[blockIdx.x] = acc2;
 }
 
+// The same fine-level residual in float-float arithmetic (lambda, m and rhs
+// split exactly from FP64; ~2^-48 per operation): z-marching 8 x 32 tiles with
+// a three-plane ring of lambda in shared memory.  Writes b = float(r) and
+// per-block partial sums of r^2.
+template <int TJ, int TK>
+__global__ void __launch_bounds__(TJ* TK) k_adj_residual_ff(int n, int chunk, ff kappa, const double* __restrict__ lam,
+                                                            const double* __restrict__ m64,
+                                                            const double* __restrict__ rhs, float* __restrict__ b,
+                                                            double* __restrict__ partials) {
+  constexpr int PJ = TJ + 2, PK = TK + 2, PS = PJ * PK, NT = TJ * TK;
+  __shared__ float s_h[3][PS], s_l[3][PS];
+  const int tiles_k = n / TK;
+  const int tile = blockIdx.x, cb = blockIdx.y;
+  const int k0 = (tile % tiles_k) * TK, j0 = (tile / tiles_k) * TJ;
+  const int i0 = cb * chunk, i1 = min(i0 + chunk, n);
+  const int t = threadIdx.x, tj = t / TK, tk = t - tj * TK;
+  const int jg = j0 + tj, kg = k0 + tk, cc = (tj + 1) * PK + tk + 1;
+  const size_t nn = (size_t)n * n;
+  auto load = [&](int p) {
+    const int ig = p < 0 ? p + n : (p >= n ? p - n : p);
+    const int slot = (p + 3) % 3;
+    for (int c = t; c < PS; c += NT) {
+      const int jj = c / PK, kk = c - jj * PK;
+      const ff v = ff_from_double(lam[(size_t)ig * nn + (size_t)wrapi(j0 + jj - 1, n) * n + wrapi(k0 + kk - 1, n)]);
+      s_h[slot][c] = v.hi;
+      s_l[slot][c] = v.lo;
+    }
+  };
+  auto W = [&](int slot, int c) { return ff{s_h[slot][c], s_l[slot][c]}; };
+  float acc = 0.f;
+  load(i0 - 1);
+  load(i0);
+  for (int i = i0; i < i1; ++i) {
+    load(i + 1);
+    __syncthreads();
+    const int sl = (i + 3) % 3, sm = (i + 2) % 3, sp = (i + 4) % 3;
+    const size_t g = (size_t)i * nn + (size_t)jg * n + kg;
+    const ff lc = W(sl, cc);
+    ff L = ff_add(W(sm, cc), W(sp, cc));
+    L = ff_add(L, ff_add(W(sl, cc - PK), W(sl, cc + PK)));
+    L = ff_add(L, ff_add(W(sl, cc - 1), W(sl, cc + 1)));
+    L = ff_sub(L, ff_mul_f(lc, 6.f));
+    // r = rhs + kappa (L - 6 lambda) - m lambda
+    ff r = ff_add(ff_from_double(rhs[g]), ff_mul(kappa, L));
+    r = ff_sub(r, ff_mul(ff_from_double(m64[g]), lc));
+    const float rv = ff_to_float(r);
+    b[g] = rv;
+    acc += rv * rv;
+    __syncthreads();
+  }
+  const double a = block_sum((double)acc);
+  if (threadIdx.x == 0) partials[blockIdx.x + blockIdx.y * gridDim.x] = a;
+}
+
+// sum of rhs^2 (once per solve: the residual's normaliser)
+__global__ void k_adj_rhs_sumsq(long long n3, const double* __restrict__ rhs, double* __restrict__ partials) {
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
+       t += (long long)gridDim.x * blockDim.x)
+    acc += rhs[t] * rhs[t];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void k_adj_sum(const double* __restrict__ p, int count, double* __restrict__ out) {
+  double a = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) a += p[i];
+  a = block_sum(a);
+  if (threadIdx.x == 0) *out = a;
+}
+
 __global__ void k_adj_finalize(const double* __restrict__ p, const double* __restrict__ p2, int count,
                                double* __restrict__ out) {
   double a = 0.0, a2 = 0.0;
@@ -108,9 +181,16 @@ __global__ void k_adj_finalize(const double* __restrict__ p, const double* __res
   if (threadIdx.x == 0) out[1] = a2;
 }
 
+// 1 / (6 kh + m), the inverse diagonal of one level (kh = kappa/h^2).
+__global__ void k_adj_dinv32(long long n3, float kh, const float* __restrict__ m32, float* __restrict__ dinv) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
+       t += (long long)gridDim.x * blockDim.x)
+    dinv[t] = 1.f / (6.f * kh + m32[t]);
+}
+
 // Red-black Gauss-Seidel on one colour: x_i = (b_i + kh sum_nb x) / (6 kh + m_i), kh = kappa/h^2.
 __global__ void __launch_bounds__(64) k_adj_smooth32(int n, float kh, float* __restrict__ x, const float* __restrict__ b,
-                                                     const float* __restrict__ m32, int parity) {
+                                                     const float* __restrict__ dinv, int parity) {
   const int i = blockIdx.z, j = blockIdx.y;
   const int kk = blockIdx.x * blockDim.x + threadIdx.x;
   if (kk >= (n >> 1)) return;
@@ -119,11 +199,54 @@ __global__ void __launch_bounds__(64) k_adj_smooth32(int n, float kh, float* __r
   const float L = x[cidx(n, wrapi(i + 1, n), j, k)] + x[cidx(n, wrapi(i - 1, n), j, k)] +
                   x[cidx(n, i, wrapi(j + 1, n), k)] + x[cidx(n, i, wrapi(j - 1, n), k)] +
                   x[cidx(n, i, j, wrapi(k + 1, n))] + x[cidx(n, i, j, wrapi(k - 1, n))];
-  x[c] = (b[c] + kh * L) / (6.f * kh + m32[c]);
+  x[c] = (b[c] + kh * L) * dinv[c];
+}
+
+// The same colour step, four cells per lane (n % 4 == 0, n >= 8; as smooth_quad):
+// block (32, 4), grid (ceil(n/128), n, n/4).
+__global__ void __launch_bounds__(128) k_adj_smooth32q(int n, float kh, float* __restrict__ x,
+                                                       const float* __restrict__ b, const float* __restrict__ dinv,
+                                                       int parity) {
+  const int i = blockIdx.z * 4 + threadIdx.y;
+  if (i >= n) return;  // whole warps
+  const int j = blockIdx.y, lane = threadIdx.x, tq = blockIdx.x * 32 + lane;
+  const int nq = n >> 2;
+  const bool act = tq < nq;
+  const int k0 = 4 * (act ? tq : nq - 1);
+  const long long nn = (long long)n * n;
+  const long long c0 = (long long)i * nn + (long long)j * n + k0;
+  const long long djp = (j + 1 < n) ? (long long)n : -(long long)(n - 1) * n;
+  const long long djm = (j > 0) ? -(long long)n : (long long)(n - 1) * n;
+  const long long dip = (i + 1 < n) ? nn : -(long long)(n - 1) * nn;
+  const long long dim = (i > 0) ? -nn : (long long)(n - 1) * nn;
+  float* x0 = x + c0;
+  const float4 X = ld4(x0), B = ld4(b + c0), D = ld4(dinv + c0);
+  const float4 P = ld4(x0 + djp), M = ld4(x0 + djm), Q = ld4(x0 + dip), R = ld4(x0 + dim);
+  if (((i + j + parity) & 1) == 0) {
+    // cells k0 and k0+2
+    float km = __shfl_up_sync(0xffffffffu, X.w, 1);
+    if (lane == 0) km = x[c0 + (k0 == 0 ? n - 1 : -1)];
+    const float LA = (km + X.y) + (P.x + M.x) + (Q.x + R.x);
+    const float LB = (X.y + X.w) + (P.z + M.z) + (Q.z + R.z);
+    if (act) {
+      x0[0] = (B.x + kh * LA) * D.x;
+      x0[2] = (B.z + kh * LB) * D.z;
+    }
+  } else {
+    // cells k0+1 and k0+3
+    float kp = __shfl_down_sync(0xffffffffu, X.x, 1);
+    if (lane == 31 || tq + 1 >= nq) kp = x[c0 + (k0 + 4 == n ? 4 - n : 4)];
+    const float LA = (X.x + X.z) + (P.y + M.y) + (Q.y + R.y);
+    const float LB = (X.z + kp) + (P.w + M.w) + (Q.w + R.w);
+    if (act) {
+      x0[1] = (B.y + kh * LA) * D.y;
+      x0[3] = (B.w + kh * LB) * D.w;
+    }
+  }
 }
 
 __global__ void __launch_bounds__(512) k_adj_coarse32(int n, float kh, float* __restrict__ x,
-                                                      const float* __restrict__ b, const float* __restrict__ m32,
+                                                      const float* __restrict__ b, const float* __restrict__ dinv,
                                                       int sweeps) {
   const int n3 = n * n * n;
   for (int s = 0; s < sweeps; ++s)
@@ -134,7 +257,7 @@ __global__ void __launch_bounds__(512) k_adj_coarse32(int n, float kh, float* __
         const float L = x[cidx(n, wrapi(i + 1, n), j, k)] + x[cidx(n, wrapi(i - 1, n), j, k)] +
                         x[cidx(n, i, wrapi(j + 1, n), k)] + x[cidx(n, i, wrapi(j - 1, n), k)] +
                         x[cidx(n, i, j, wrapi(k + 1, n))] + x[cidx(n, i, j, wrapi(k - 1, n))];
-        x[t] = (b[t] + kh * L) / (6.f * kh + m32[t]);
+        x[t] = (b[t] + kh * L) * dinv[t];
       }
       __syncthreads();
     }
@@ -163,6 +286,104 @@ __global__ void __launch_bounds__(64) k_adj_restrict_resid32(int nf, float kh, c
   const size_t t = cidx(nc, I, J, Kc);
   bH[t] = 0.125f * s;
   xH[t] = 0.f;
+}
+
+// The same restriction, sixteen fine cells per lane (nf % 4 == 0, as
+// restrict_quad): block (32, 4), grid (ceil(nf/128), nc [J], ceil(nc/4) [I]).
+__global__ void __launch_bounds__(128) k_adj_restrict_resid32q(int nf, float kh, const float* __restrict__ x,
+                                                               const float* __restrict__ b,
+                                                               const float* __restrict__ m32, float* __restrict__ bH,
+                                                               float* __restrict__ xH) {
+  const int nc = nf >> 1, nq = nf >> 2;
+  const int I = blockIdx.z * 4 + threadIdx.y;
+  if (I >= nc) return;  // whole warps
+  const int J = blockIdx.y, lane = threadIdx.x, tq = blockIdx.x * 32 + lane;
+  const bool act = tq < nq;
+  const int k0 = 4 * (act ? tq : nq - 1);
+  const int i0 = 2 * I, j0 = 2 * J;
+  const int iA = i0 == 0 ? nf - 1 : i0 - 1, iB = i0 + 2 == nf ? 0 : i0 + 2;
+  const int jA = j0 == 0 ? nf - 1 : j0 - 1, jB = j0 + 2 == nf ? 0 : j0 + 2;
+  auto row = [&](int i, int j) { return ((long long)i * nf + j) * nf + k0; };
+  float4 X[2][2];
+  long long co[2][2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      co[a][c] = row(i0 + a, j0 + c);
+      X[a][c] = ld4(x + co[a][c]);
+    }
+  float4 xi[2][2], xj[2][2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    xi[0][c] = ld4(x + row(iA, j0 + c));
+    xi[1][c] = ld4(x + row(iB, j0 + c));
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    xj[a][0] = ld4(x + row(i0 + a, jA));
+    xj[a][1] = ld4(x + row(i0 + a, jB));
+  }
+  float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float4 q = X[a][c];
+      float qm = __shfl_up_sync(0xffffffffu, q.w, 1);
+      float qp = __shfl_down_sync(0xffffffffu, q.x, 1);
+      if (lane == 0) qm = x[co[a][c] + (k0 == 0 ? nf - 1 : -1)];
+      if (lane == 31 || tq + 1 >= nq) qp = x[co[a][c] + (k0 + 4 == nf ? 4 - nf : 4)];
+      const float4 ni = a == 0 ? xi[0][c] : X[0][c], pi = a == 0 ? X[1][c] : xi[1][c];
+      const float4 nj = c == 0 ? xj[a][0] : X[a][0], pj = c == 0 ? X[a][1] : xj[a][1];
+      const float4 Bv = ld4(b + co[a][c]), Mv = ld4(m32 + co[a][c]);
+      auto d = [&](float bb, float mm, float xc, float L) { return bb + kh * (L - 6.f * xc) - mm * xc; };
+      s0 += d(Bv.x, Mv.x, q.x, (qm + q.y) + (ni.x + pi.x) + (nj.x + pj.x)) +
+            d(Bv.y, Mv.y, q.y, (q.x + q.z) + (ni.y + pi.y) + (nj.y + pj.y));
+      s1 += d(Bv.z, Mv.z, q.z, (q.y + q.w) + (ni.z + pi.z) + (nj.z + pj.z)) +
+            d(Bv.w, Mv.w, q.w, (q.z + qp) + (ni.w + pi.w) + (nj.w + pj.w));
+    }
+  if (act) {
+    const long long t = ((long long)I * nc + J) * nc + (k0 >> 1);
+    *reinterpret_cast<float2*>(bH + t) = make_float2(0.125f * s0, 0.125f * s1);
+    *reinterpret_cast<float2*>(xH + t) = make_float2(0.f, 0.f);
+  }
+}
+
+// x^h += P x^H, four fine cells per lane (as prolong_quad, without the
+// restricted-solution term): block (32, 4), grid (ceil(nf/128), nf, nf/4).
+__global__ void __launch_bounds__(128) k_adj_prolong32q(int nc, const float* __restrict__ xH, float* __restrict__ xf) {
+  const int nf = nc << 1, nq = nf >> 2;
+  const int i = blockIdx.z * 4 + threadIdx.y, j = blockIdx.y, lane = threadIdx.x, tq = blockIdx.x * 32 + lane;
+  const bool act = tq < nq;
+  const int t = act ? tq : nq - 1;
+  const int k0 = 4 * t, K0 = 2 * t;
+  const int I = i >> 1, J = j >> 1;
+  int I2 = I + ((i & 1) ? 1 : -1), J2 = J + ((j & 1) ? 1 : -1);
+  I2 = I2 < 0 ? nc - 1 : (I2 >= nc ? 0 : I2);
+  J2 = J2 < 0 ? nc - 1 : (J2 >= nc ? 0 : J2);
+  const long long rA = ((long long)I * nc + J) * nc, rB = ((long long)I2 * nc + J) * nc,
+                  rC = ((long long)I * nc + J2) * nc, rD = ((long long)I2 * nc + J2) * nc;
+  auto two = [&](long long r) { return *reinterpret_cast<const float2*>(xH + r + K0); };
+  const float2 A = two(rA), B = two(rB), C = two(rC), D = two(rD);
+  const float Rx = 9.f * A.x + 3.f * (B.x + C.x) + D.x;
+  const float Ry = 9.f * A.y + 3.f * (B.y + C.y) + D.y;
+  float Rm = __shfl_up_sync(0xffffffffu, Ry, 1);
+  float Rp = __shfl_down_sync(0xffffffffu, Rx, 1);
+  if (lane == 0) {
+    const int Km = K0 == 0 ? nc - 1 : K0 - 1;
+    Rm = 9.f * xH[rA + Km] + 3.f * (xH[rB + Km] + xH[rC + Km]) + xH[rD + Km];
+  }
+  if (lane == 31 || tq + 1 >= nq) {
+    const int Kp = K0 + 2 == nc ? 0 : K0 + 2;
+    Rp = 9.f * xH[rA + Kp] + 3.f * (xH[rB + Kp] + xH[rC + Kp]) + xH[rD + Kp];
+  }
+  constexpr float w = 1.f / 64.f;
+  float* p = xf + ((long long)i * nf + j) * nf + k0;
+  const float4 old = ld4(p);
+  if (act)
+    *reinterpret_cast<float4*>(p) = make_float4(old.x + (3.f * Rx + Rm) * w, old.y + (3.f * Rx + Ry) * w,
+                                                old.z + (3.f * Ry + Rx) * w, old.w + (3.f * Ry + Rp) * w);
 }
 
 // x^h += P x^H (27/9/3/1 weights).
@@ -227,7 +448,7 @@ struct AdjWork {
   double *lam = nullptr, *m64 = nullptr, *rhs = nullptr, *gam = nullptr, *tq = nullptr;
   double *partials = nullptr, *partials2 = nullptr, *scal = nullptr, *h_scal = nullptr;
   int n[kMaxLevels];
-  float *x[kMaxLevels], *b[kMaxLevels], *m32[kMaxLevels];
+  float *x[kMaxLevels], *b[kMaxLevels], *m32[kMaxLevels], *dinv[kMaxLevels];
 };
 
 static std::mutex g_adj_mu;
@@ -255,13 +476,14 @@ static int adj_work(int N, int levels, AdjWork** out) {
   const size_t o_lam = take(n3 * 8), o_m = take(n3 * 8), o_rhs = take(n3 * 8), o_gam = take(n3 * 8),
                o_tq = take(n3 * 8), o_p = take(kMaxReduceBlocks * 8), o_p2 = take(kMaxReduceBlocks * 8),
                o_s = take(64);
-  size_t ox[kMaxLevels], ob[kMaxLevels], om[kMaxLevels];
+  size_t ox[kMaxLevels], ob[kMaxLevels], om[kMaxLevels], od[kMaxLevels];
   for (int l = 0, nn = N; l < nlev; ++l, nn /= 2) {
     const size_t c = (size_t)nn * nn * nn;
     w->n[l] = nn;
     ox[l] = take(c * 4);
     ob[l] = take(c * 4);
     om[l] = take(c * 4);
+    od[l] = take(c * 4);
   }
   if (cudaMalloc(&w->base, off) != cudaSuccess) {
     cudaGetLastError();
@@ -287,6 +509,7 @@ static int adj_work(int N, int levels, AdjWork** out) {
     w->x[l] = (float*)(b + ox[l]);
     w->b[l] = (float*)(b + ob[l]);
     w->m32[l] = (float*)(b + om[l]);
+    w->dinv[l] = (float*)(b + od[l]);
   }
   g_adj[g_nadj++] = w;
   *out = w;
@@ -312,39 +535,47 @@ void release_adjoint_work() {
 
 static dim3 grid_k(int n_k, int n_j, int n_i) { return dim3((n_k + 63) / 64, n_j, n_i); }
 
+static void adj_smooth(AdjWork* w, int l, float kh, int sweeps, cudaStream_t st) {
+  const int n = w->n[l];
+  for (int s = 0; s < sweeps; ++s)
+    for (int par = 0; par < 2; ++par) {
+      if (n % 4 == 0 && n >= 8)
+        k_adj_smooth32q<<<dim3((n / 4 + 31) / 32, n, n / 4), dim3(32, 4), 0, st>>>(n, kh, w->x[l], w->b[l],
+                                                                                 w->dinv[l], par);
+      else
+        k_adj_smooth32<<<grid_k(n / 2, n, n), 64, 0, st>>>(n, kh, w->x[l], w->b[l], w->dinv[l], par);
+      note_launch(1);
+    }
+}
+
 static void adj_vcycle(AdjWork* w, int l, double kappa, const mgglam_params* prm, cudaStream_t st) {
   const int n = w->n[l];
   const float kh = (float)(kappa / ((double)(1 << l) * (double)(1 << l)));
   if (l == w->nlev - 1) {
     if ((long long)n * n * n <= 4096) {
-      k_adj_coarse32<<<1, 512, 0, st>>>(n, kh, w->x[l], w->b[l], w->m32[l], prm->coarse_sweeps);
+      k_adj_coarse32<<<1, 512, 0, st>>>(n, kh, w->x[l], w->b[l], w->dinv[l], prm->coarse_sweeps);
       note_launch(1);
     } else {
-      for (int s = 0; s < prm->coarse_sweeps; ++s)
-        for (int par = 0; par < 2; ++par) {
-          k_adj_smooth32<<<grid_k(n / 2, n, n), 64, 0, st>>>(n, kh, w->x[l], w->b[l], w->m32[l], par);
-          note_launch(1);
-        }
+      adj_smooth(w, l, kh, prm->coarse_sweeps, st);
     }
     return;
   }
-  for (int s = 0; s < prm->nu1; ++s)
-    for (int par = 0; par < 2; ++par) {
-      k_adj_smooth32<<<grid_k(n / 2, n, n), 64, 0, st>>>(n, kh, w->x[l], w->b[l], w->m32[l], par);
-      note_launch(1);
-    }
+  adj_smooth(w, l, kh, prm->nu1, st);
   const int nc = w->n[l + 1];
-  k_adj_restrict_resid32<<<grid_k(nc, nc, nc), 64, 0, st>>>(n, kh, w->x[l], w->b[l], w->m32[l], w->b[l + 1],
-                                                             w->x[l + 1]);
+  if (n % 4 == 0 && n >= 8)
+    k_adj_restrict_resid32q<<<dim3((n / 4 + 31) / 32, nc, (nc + 3) / 4), dim3(32, 4), 0, st>>>(
+        n, kh, w->x[l], w->b[l], w->m32[l], w->b[l + 1], w->x[l + 1]);
+  else
+    k_adj_restrict_resid32<<<grid_k(nc, nc, nc), 64, 0, st>>>(n, kh, w->x[l], w->b[l], w->m32[l], w->b[l + 1],
+                                                               w->x[l + 1]);
   note_launch(1);
   adj_vcycle(w, l + 1, kappa, prm, st);
-  k_adj_prolong32<<<grid_k(n, n, n), 64, 0, st>>>(nc, w->x[l + 1], w->x[l]);
+  if (n % 4 == 0 && n >= 8)
+    k_adj_prolong32q<<<dim3((n / 4 + 31) / 32, n, n / 4), dim3(32, 4), 0, st>>>(nc, w->x[l + 1], w->x[l]);
+  else
+    k_adj_prolong32<<<grid_k(n, n, n), 64, 0, st>>>(nc, w->x[l + 1], w->x[l]);
   note_launch(1);
-  for (int s = 0; s < prm->nu2; ++s)
-    for (int par = 0; par < 2; ++par) {
-      k_adj_smooth32<<<grid_k(n / 2, n, n), 64, 0, st>>>(n, kh, w->x[l], w->b[l], w->m32[l], par);
-      note_launch(1);
-    }
+  adj_smooth(w, l, kh, prm->nu2, st);
 }
 
 int solve_adjoint(const mgglam_params* prm, double a, const double* field, const float* rho, int N,
@@ -373,13 +604,35 @@ int solve_adjoint(const mgglam_params* prm, double a, const double* field, const
     k_adj_restrict_m32<<<grid_k(w->n[l], w->n[l], w->n[l]), 64, 0, st>>>(w->n[l - 1], w->m32[l - 1], w->m32[l]);
     note_launch(1);
   }
+  for (int l = 0; l < w->nlev; ++l) {
+    const long long nl3 = (long long)w->n[l] * w->n[l] * w->n[l];
+    const float kh = (float)(m.c2 / ((double)(1 << l) * (double)(1 << l)));
+    k_adj_dinv32<<<stream_grid(nl3), kThreads, 0, st>>>(nl3, kh, w->m32[l], w->dinv[l]);
+    note_launch(1);
+  }
   MG_CUDA_TRY(cudaMemsetAsync(w->lam, 0, (size_t)n3 * 8, st));
   const double kappa = m.c2;
   const int gr = N * N < 2048 ? N * N : 2048;
   const int bt = N >= 256 ? 256 : (N <= 32 ? 32 : ((N + 31) / 32) * 32);
+  // the fine residual in float-float on meshes its 8 x 32 tiles divide, else FP64
+  const bool ffr = N % 32 == 0;
+  int chunk = N >= 64 ? 64 : N;
+  while ((long long)(N / 32) * (N / 8) * ((N + chunk - 1) / chunk) > kMaxReduceBlocks) chunk *= 2;
+  const dim3 gff((N / 32) * (N / 8), (N + chunk - 1) / chunk);
+  const ff kappa_ff = {(float)kappa, (float)(kappa - (double)(float)kappa)};
+  if (ffr) {
+    k_adj_rhs_sumsq<<<stream_grid(n3), kThreads, 0, st>>>(n3, w->rhs, w->partials2);
+    k_adj_sum<<<1, 1024, 0, st>>>(w->partials2, stream_grid(n3), w->scal + 1);
+    note_launch(2);
+  }
   auto residual = [&]() -> int {
-    k_adj_residual64<<<gr, bt, 0, st>>>(N, kappa, w->lam, w->m64, w->rhs, w->b[0], w->partials, w->partials2);
-    k_adj_finalize<<<1, 1024, 0, st>>>(w->partials, w->partials2, gr, w->scal);
+    if (ffr) {
+      k_adj_residual_ff<8, 32><<<gff, 256, 0, st>>>(N, chunk, kappa_ff, w->lam, w->m64, w->rhs, w->b[0], w->partials);
+      k_adj_sum<<<1, 1024, 0, st>>>(w->partials, (int)(gff.x * gff.y), w->scal);
+    } else {
+      k_adj_residual64<<<gr, bt, 0, st>>>(N, kappa, w->lam, w->m64, w->rhs, w->b[0], w->partials, w->partials2);
+      k_adj_finalize<<<1, 1024, 0, st>>>(w->partials, w->partials2, gr, w->scal);
+    }
     note_launch(2);
     MG_CUDA_TRY(cudaMemcpyAsync(w->h_scal, w->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     MG_CUDA_TRY(cudaStreamSynchronize(st));
@@ -396,18 +649,32 @@ int solve_adjoint(const mgglam_params* prm, double a, const double* field, const
   S->resid0 = eps;
   S->resid_hist[0] = eps;
   int cyc = 0, outer = 0, nh = 1;
-  const int inner = prm->inner_cycles > 0 ? prm->inner_cycles : 3;
+  // inner FP32 cycles per FP64/float-float step: fixed, or (inner_cycles = 0)
+  // enough for tol at the observed contraction, capped where one single-
+  // precision correction stops gaining (~1e-6), as in the forward solve
+  double rho_est = 0.1;
   int status = MGGLAM_OK;
   while (!(eps <= tol) && cyc < prm->max_cycles) {
     if (!isfinite(eps)) { status = MGGLAM_ERR_NONFINITE; break; }
+    int inner = prm->inner_cycles;
+    if (inner <= 0) {
+      const double lr = log(rho_est);
+      const int need = (int)ceil(log(fmax(tol, 1e-300) / eps) / lr - 1e-9);
+      const int cap = (int)ceil(log(1e-6) / lr);
+      inner = need < 1 ? 1 : (need > cap ? cap : need);
+    }
+    const double eps_before = eps;
+    int done = 0;
     MG_CUDA_TRY(cudaMemsetAsync(w->x[0], 0, (size_t)n3 * 4, st));
-    for (int c = 0; c < inner && cyc < prm->max_cycles; ++c, ++cyc) adj_vcycle(w, 0, kappa, prm, st);
+    for (int c = 0; c < inner && cyc < prm->max_cycles; ++c, ++cyc, ++done) adj_vcycle(w, 0, kappa, prm, st);
     k_adj_apply<<<stream_grid(n3), kThreads, 0, st>>>(n3, w->lam, w->x[0]);
     note_launch(1);
     ++outer;
     if ((rc = residual())) return rc;
     eps = sqrt(w->h_scal[0] / (double)n3) / snorm;
     if (nh < 64) S->resid_hist[nh++] = eps;
+    if (done > 0 && eps > 0.0 && eps < eps_before && eps / eps_before > 1e-5)
+      rho_est = fmin(0.5, fmax(0.01, pow(eps / eps_before, 1.0 / done)));
   }
   const int go = grid_for(n3);
   k_adj_outputs<<<go, kThreads, 0, st>>>(n3, w->lam, w->gam, w->tq, grad_rho, w->partials);

@@ -83,6 +83,18 @@ def mg():
 @pytest.mark.parametrize("key", list(CASES))
 @pytest.mark.parametrize("N", [16, 24])
 def test_gpu_adjoint_matches_oracle(orc, mg, key, N):
+    """FP64 fine residual (meshes the float-float residual's 8 x 32 tiles do not divide)."""
+    _adjoint_case(orc, mg, key, N)
+
+
+@pytest.mark.gpu
+def test_gpu_adjoint_float_float_residual_matches_oracle(orc, mg):
+    """32^3: the float-float fine residual (one model: the oracle's sparse LU at
+    32^3 takes most of a minute)."""
+    _adjoint_case(orc, mg, "fr1", 32)
+
+
+def _adjoint_case(orc, mg, key, N):
     kw = dict(CASES[key])
     kw["box"] = kw["box"] * N / 8
     p = orc.Params(**kw)

@@ -46,7 +46,7 @@ def _rank_main(rank, world, port, out):
 
 def test_two_rank_barrier_max_reduce_and_job_rate():
     world = 2
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True)
     (mx0, rate0, s0), (mx1, rate1, s1) = out[0], out[1]
     assert mx0 == mx1 == 20.0
