@@ -55,10 +55,10 @@ def measured_peaks():
 
 # DRAM bytes per fine-level sweep of the smoother (dram__bytes_read.sum +
 # dram__bytes_write.sum of both colour launches from the ncu capture summarised
-# in profiles/k_smooth32q_fR256.md), valid while the kernel's sources hash to
+# in profiles/k_smooth32s_fR256.md), valid while the kernel's sources hash to
 # the value recorded there.
-SMOOTHER_TRAFFIC = {"bytes_per_sweep": (202.388224 + 38.553088 + 202.413056 + 38.156288) * 1e6,
-                    "source_sha256_16": "2dc3ed9cab613821"}
+SMOOTHER_TRAFFIC = {"bytes_per_sweep": (134.757120 + 19.657472 + 134.760192 + 19.349248) * 1e6,
+                    "source_sha256_16": "2dcb6d33299bd4e8"}
 
 
 def smoother_traffic_per_sweep():
@@ -520,7 +520,7 @@ def run_ours(args) -> None:
         achieved = alg / per_sweep_s / 1e9
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": smoother_traffic_per_sweep(),
-                "kernel": "k_smooth32q (fine level, one red-black sweep = 2 launches)",
+                "kernel": "k_smooth32s (split fine level, one red-black sweep = 2 launches)",
                 "peak_source": peak_kind, "algorithmic_bytes_per_sweep": alg,
                 "ms_per_sweep": round(per_sweep_s * 1e3, 4)}
     timed_total = sum(v["ms"] for v in prof.values())
