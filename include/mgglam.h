@@ -127,8 +127,10 @@ int mgglam_default_params(mgglam_params* prm);
  * Cloud-in-cell density assignment (Sec. 3.1): each particle adds mass N^3/np
  * shared between the 8 nearest cell centres with weights
  * prod_d (1 - |x_d - (c_d + 1/2)|), periodic, so that the mean density is 1.
- *   pos    device, [np][3] float32 positions in cell units; any real value is
- *          wrapped periodically into [0, N).
+ *   pos    [np][3] float32 positions in cell units; any real value is wrapped
+ *          periodically into [0, N).  Device memory, or page-locked host memory
+ *          (cudaHostAlloc / pinned), which the kernel reads in place over the
+ *          host link (no separate copy).
  *   np     number of particles (>= 1).
  *   N      mesh side, 2 <= N <= 2048.
  *   rho    device, N^3 float32 output (overwritten).
@@ -138,6 +140,21 @@ int mgglam_default_params(mgglam_params* prm);
  * MGGLAM_ERR_OOM, MGGLAM_ERR_CUDA.
  */
 int mgglam_deposit_cic(const float* pos, long long np, int N, float* rho, void* stream);
+
+/*
+ * The same deposit (identical result) for particles in page-locked host memory,
+ * with the host-to-device copy overlapped with the deposit: the positions are
+ * copied in 'chunks' pieces on the library's copy stream into pos_dev, and
+ * each piece is deposited (on 'stream') as soon as it has arrived.
+ *   pos_host  page-locked host, [np][3] float32 (read; unchanged).
+ *   pos_dev   device, [np][3] float32 staging buffer; holds a copy of pos_host
+ *             on return (the gather can use it).  Not touched before earlier
+ *             work on 'stream' completes.
+ *   chunks    1..32, 0 = 8.
+ * Errors as mgglam_deposit_cic; MGGLAM_ERR_ARG for chunks outside 0..32.
+ */
+int mgglam_deposit_cic_host(const float* pos_host, float* pos_dev, long long np, int N, float* rho, int chunks,
+                            void* stream);
 
 /*
  * The same CIC density assignment as mgglam_deposit_cic (identical result, bit
@@ -200,13 +217,31 @@ int mgglam_solve_scalar(const mgglam_params* prm, double a, const float* rho, in
  *   CQ:        F = prefactor * (-beta) grad phi~   (the fifth-force part of Eq. csf_particle_geodesic_code2)
  * prefactor is the caller's time factor (e.g. H0/adot).
  *   field  device, N^3 float64 solution from mgglam_solve_scalar.
- *   pos    device, [np][3] float32 positions (cell units, wrapped periodically).
- *   force  device, [np][3] float32 output (overwritten).
+ *   pos    [np][3] float32 positions (cell units, wrapped periodically); device
+ *          or page-locked host memory (read in place).
+ *   force  [np][3] float32 output (overwritten); device or page-locked host
+ *          memory (written in place).
  * Errors: MGGLAM_ERR_ARG, MGGLAM_ERR_SHAPE (N even, 4..2048), MGGLAM_ERR_OOM, MGGLAM_ERR_CUDA.
  */
 int mgglam_gather_force(const mgglam_params* prm, double a, const double* field, int N,
                         const float* pos, long long np, float* force, double prefactor,
                         void* stream);
+
+/*
+ * The same gather with the forces delivered to page-locked host memory, the
+ * device-to-host copy overlapped with the gather: the particles are gathered
+ * in 'chunks' pieces into force_dev and each piece is copied to force_host on
+ * the library's copy stream while the next is computed.  Work later enqueued
+ * on 'stream' (and a synchronisation of it) waits for the last copy.
+ *   pos_dev     device, [np][3] float32 positions.
+ *   force_dev   device, [np][3] float32 staging buffer (overwritten).
+ *   force_host  page-locked host, [np][3] float32 output.
+ *   chunks      1..32, 0 = 8.
+ * Errors as mgglam_gather_force; MGGLAM_ERR_ARG for chunks outside 0..32.
+ */
+int mgglam_gather_force_host(const mgglam_params* prm, double a, const double* field, int N, const float* pos_dev,
+                             long long np, float* force_dev, float* force_host, double prefactor, int chunks,
+                             void* stream);
 
 /*
  * Adjoint of the solve: gradients of a scalar loss l(u*) with respect to the

@@ -102,7 +102,8 @@ EXPORTS = ["mgglam_version", "mgglam_status_string", "mgglam_default_params", "m
            "mgglam_solve_scalar", "mgglam_gather_force", "mgglam_smooth", "mgglam_residual",
            "mgglam_restrict", "mgglam_prolong_correct", "mgglam_release", "mgglam_profile_start",
            "mgglam_profile_stop", "mgglam_launch_count", "mgglam_deposit_cic_static",
-           "mgglam_solve_adjoint", "mgglam_solve_batch", "mgglam_cq_background", "mgglam_radiation_density"]
+           "mgglam_solve_adjoint", "mgglam_solve_batch", "mgglam_cq_background", "mgglam_radiation_density",
+           "mgglam_deposit_cic_host", "mgglam_gather_force_host"]
 
 
 class CKernelProfile(ctypes.Structure):
@@ -149,12 +150,16 @@ def _check(fn: str, rc: int, allow=(0,)):
     return rc
 
 
-def _ptr(t, dtype=None):
+def _ptr(t, dtype=None, host_ok=False):
+    """Device address of a contiguous tensor.  host_ok: page-locked host tensors
+    are accepted as well (the kernels read or write them directly over the
+    host link); pageable host memory never is (there is no CPU path)."""
     import torch
     if t is None:
         return None
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
-        raise TypeError("expected a CUDA tensor (there is no CPU path)")
+    if not isinstance(t, torch.Tensor) or not (t.is_cuda or (host_ok and t.is_pinned())):
+        raise TypeError("expected a CUDA tensor" + (" or a pinned host tensor" if host_ok else "") +
+                        " (there is no CPU path)")
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
     if dtype is not None and t.dtype != dtype:
@@ -175,13 +180,49 @@ def default_params() -> CParams:
 
 
 def deposit_cic(pos, N: int, rho=None, stream=None):
-    """CIC density (mean 1) of particles pos [np,3] float32 (cell units) on an N^3 float32 mesh."""
+    """CIC density (mean 1) of particles pos [np,3] float32 (cell units) on an N^3 float32 mesh.
+    pos may be a CUDA tensor or a pinned host tensor (read in place by the kernel)."""
     import torch
     if rho is None:
-        rho = torch.empty((N, N, N), dtype=torch.float32, device=pos.device)
-    _check("mgglam_deposit_cic", load().mgglam_deposit_cic(_ptr(pos, torch.float32), pos.shape[0], N,
+        rho = torch.empty((N, N, N), dtype=torch.float32, device="cuda" if not pos.is_cuda else pos.device)
+    _check("mgglam_deposit_cic", load().mgglam_deposit_cic(_ptr(pos, torch.float32, host_ok=True), pos.shape[0], N,
                                                           _ptr(rho, torch.float32), _stream(stream)))
     return rho
+
+
+def deposit_cic_host(pos_host, pos_dev, N: int, rho=None, chunks: int = 8, stream=None):
+    """Deposit from pinned host positions, the copy into pos_dev (device staging)
+    overlapped with the deposit (mgglam_deposit_cic_host)."""
+    import torch
+    if not (isinstance(pos_host, torch.Tensor) and pos_host.is_pinned()):
+        raise TypeError("pos_host must be a pinned host tensor")
+    if rho is None:
+        rho = torch.empty((N, N, N), dtype=torch.float32, device=pos_dev.device)
+    lib = load()
+    lib.mgglam_deposit_cic_host.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
+                                            ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    _check("mgglam_deposit_cic_host",
+           lib.mgglam_deposit_cic_host(ctypes.c_void_p(pos_host.data_ptr()), _ptr(pos_dev, torch.float32),
+                                       pos_host.shape[0], N, _ptr(rho, torch.float32), chunks, _stream(stream)))
+    return rho
+
+
+def gather_force_host(prm: Params, a: float, field, pos_dev, force_dev, force_host, prefactor: float = 1.0,
+                      chunks: int = 8, stream=None):
+    """Gather with the forces delivered to a pinned host tensor, the copy
+    overlapped with the gather (mgglam_gather_force_host)."""
+    import torch
+    if not (isinstance(force_host, torch.Tensor) and force_host.is_pinned()):
+        raise TypeError("force_host must be a pinned host tensor")
+    lib = load()
+    lib.mgglam_gather_force_host.argtypes = [ctypes.POINTER(CParams), ctypes.c_double, ctypes.c_void_p, ctypes.c_int,
+                                             ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_double, ctypes.c_int, ctypes.c_void_p]
+    _check("mgglam_gather_force_host",
+           lib.mgglam_gather_force_host(ctypes.byref(prm.c()), a, _ptr(field, torch.float64), field.shape[0],
+                                        _ptr(pos_dev, torch.float32), pos_dev.shape[0], _ptr(force_dev, torch.float32),
+                                        ctypes.c_void_p(force_host.data_ptr()), prefactor, chunks, _stream(stream)))
+    return force_host
 
 
 def solve_scalar(prm: Params, a: float, rho, field, tol: float, stream=None, allow_unconverged=False) -> Stats:
@@ -198,13 +239,16 @@ def solve_scalar(prm: Params, a: float, rho, field, tol: float, stream=None, all
 
 
 def gather_force(prm: Params, a: float, field, pos, prefactor: float = 1.0, force=None, stream=None):
+    """Fifth force on the particles.  pos and force may be CUDA tensors or pinned
+    host tensors (read and written in place by the kernel)."""
     import torch
     N = field.shape[0]
     if force is None:
-        force = torch.empty((pos.shape[0], 3), dtype=torch.float32, device=pos.device)
+        force = torch.empty((pos.shape[0], 3), dtype=torch.float32, device=field.device)
     _check("mgglam_gather_force", load().mgglam_gather_force(ctypes.byref(prm.c()), a, _ptr(field, torch.float64), N,
-                                                            _ptr(pos, torch.float32), pos.shape[0],
-                                                            _ptr(force, torch.float32), prefactor, _stream(stream)))
+                                                            _ptr(pos, torch.float32, host_ok=True), pos.shape[0],
+                                                            _ptr(force, torch.float32, host_ok=True), prefactor,
+                                                            _stream(stream)))
     return force
 
 

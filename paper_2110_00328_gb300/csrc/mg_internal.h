@@ -119,6 +119,13 @@ int deposit_cic(const float* pos, long long np, int N, float* rho, cudaStream_t 
 int gather_force(const ModelDev& m, int kind, int n_fr, const mgglam_params* prm,
                  const double* field, int N, const float* pos, long long np, float* force,
                  double prefactor, cudaStream_t st);
+int gather_chunk(const ModelDev& m, int kind, const mgglam_params* prm, int N, const float* pos, long long np,
+                 float* force, double prefactor, cudaStream_t st);
+int deposit_cic_host(const float* pos_host, float* pos_dev, long long np, int N, float* rho, int chunks,
+                     cudaStream_t st);
+int gather_force_host(const ModelDev& m, int kind, const mgglam_params* prm, const double* field, int N,
+                      const float* pos_dev, long long np, float* force_dev, float* force_host, double prefactor,
+                      int chunks, cudaStream_t st);
 
 }  // namespace mg
 

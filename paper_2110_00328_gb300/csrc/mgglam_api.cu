@@ -287,6 +287,26 @@ int mgglam_gather_force(const mgglam_params* prm, double a, const double* field,
   return gather_force(m, m.kind, prm->n, prm, field, N, pos, np, force, prefactor, (cudaStream_t)stream);
 }
 
+int mgglam_deposit_cic_host(const float* pos_host, float* pos_dev, long long np, int N, float* rho, int chunks,
+                            void* stream) {
+  if (!pos_host || !pos_dev || !rho || np < 1 || chunks < 0 || chunks > 32) return MGGLAM_ERR_ARG;
+  if (N < 2 || N > 2048) return MGGLAM_ERR_SHAPE;
+  return deposit_cic_host(pos_host, pos_dev, np, N, rho, chunks ? chunks : 8, (cudaStream_t)stream);
+}
+
+int mgglam_gather_force_host(const mgglam_params* prm, double a, const double* field, int N, const float* pos_dev,
+                             long long np, float* force_dev, float* force_host, double prefactor, int chunks,
+                             void* stream) {
+  if (!prm || !field || !pos_dev || !force_dev || !force_host || np < 1 || chunks < 0 || chunks > 32)
+    return MGGLAM_ERR_ARG;
+  int rc = check_mesh(N);
+  if (rc) return rc;
+  ModelDev m;
+  if ((rc = make_model(prm, a, N, &m))) return rc;
+  return gather_force_host(m, m.kind, prm, field, N, pos_dev, np, force_dev, force_host, prefactor,
+                           chunks ? chunks : 8, (cudaStream_t)stream);
+}
+
 int mgglam_smooth(const mgglam_params* prm, double a, int n, double h, double* u, const double* rho,
                   const double* S, int sweeps, void* stream) {
   if (!prm || !u || !rho || sweeps < 0 || !(h >= 1.0)) return MGGLAM_ERR_ARG;

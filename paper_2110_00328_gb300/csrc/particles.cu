@@ -252,6 +252,32 @@ __global__ void __launch_bounds__(kThreads) k_gather(const float* __restrict__ T
   }
 }
 
+// Force prefactor of the gather (the spatial factor of the model's fifth force, times the caller's).
+static double force_scale(const ModelDev& m, int kind, const mgglam_params* prm) {
+  if (is_fr(kind)) return 0.5 * m.c2;  // F = (c~^2/2) grad f_R
+  if (kind == KSYM)
+    return -3.0 * prm->xi * prm->xi * prm->omega_m * prm->beta_star * prm->beta_star * m.c2 /
+           (prm->a_star * prm->a_star * prm->a_star);
+  return -1.0;  // F = -grad(beta phi)
+}
+
+// The gather of a range of particles on the mesh T the last gather_force call
+// on this stream formed (the workspace's scratch mesh).
+int gather_chunk(const ModelDev& m, int kind, const mgglam_params* prm, int N, const float* pos, long long np,
+                 float* force, double prefactor, cudaStream_t st) {
+  Workspace* ws = nullptr;
+  int rc = get_workspace(N, MGGLAM_MIXED, 0, &ws);
+  if (rc) return rc;
+  const float* T = ws->lev[0].ub;
+  prof_begin(PC_GATHER, st, 24.0 * np);
+  k_gather<<<grid_for(np, kThreads, 1 << 20), kThreads, 0, st>>>(T, N, pos, np,
+                                                                 (float)(force_scale(m, kind, prm) * prefactor), force);
+  prof_end(st);
+  note_launch(1);
+  MG_CUDA_TRY(cudaGetLastError());
+  return MGGLAM_OK;
+}
+
 int gather_force(const ModelDev& m, int kind, int n_fr, const mgglam_params* prm, const double* field, int N,
                  const float* pos, long long np, float* force, double prefactor, cudaStream_t st) {
   (void)n_fr;
@@ -271,17 +297,109 @@ int gather_force(const ModelDev& m, int kind, int n_fr, const mgglam_params* prm
     default: k_transform<KCQ><<<g, kThreads, 0, st>>>(field, n3, 0.0, prm->beta, T); break;
   }
   prof_end(st);
-  if (is_fr(kind)) scale = 0.5 * m.c2;  // F = (c~^2/2) grad f_R
-  else if (kind == KSYM)
-    scale = -3.0 * prm->xi * prm->xi * prm->omega_m * prm->beta_star * prm->beta_star * m.c2 /
-            (prm->a_star * prm->a_star * prm->a_star);
-  else
-    scale = -1.0;  // F = -grad(beta phi)
+  scale = force_scale(m, kind, prm);
   prof_begin(PC_GATHER, st, 24.0 * np + 4.0 * n3);
   k_gather<<<grid_for(np, kThreads, 1 << 20), kThreads, 0, st>>>(T, N, pos, np, (float)(scale * prefactor), force);
   prof_end(st);
   note_launch(2);
   MG_CUDA_TRY(cudaGetLastError());
+  return MGGLAM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Host input / output overlapped with the kernels
+// ---------------------------------------------------------------------------
+//
+// The particles live in page-locked host memory.  The deposit copies them to a
+// device buffer in chunks on a second stream, and deposits chunk c as soon as
+// its copy has landed (stream-ordered by an event), so the host-link copy and
+// the atomics overlap; the gather computes chunk c and copies its forces back
+// while chunk c+1 is computed.  One copy stream and an event pool per device.
+
+constexpr int kMaxIoChunks = 32;
+
+struct HostIo {
+  int device = -1;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev[kMaxIoChunks + 2] = {};
+};
+
+static int host_io(HostIo** out) {
+  static std::mutex mu;
+  static HostIo io[16];
+  int dev = 0;
+  MG_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 16) return MGGLAM_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(mu);
+  HostIo& h = io[dev];
+  if (h.device != dev) {
+    MG_CUDA_TRY(cudaStreamCreateWithFlags(&h.cs, cudaStreamNonBlocking));
+    for (int i = 0; i < kMaxIoChunks + 2; ++i)
+      MG_CUDA_TRY(cudaEventCreateWithFlags(&h.ev[i], cudaEventDisableTiming));
+    h.device = dev;
+  }
+  *out = &h;
+  return MGGLAM_OK;
+}
+
+int deposit_cic_host(const float* pos_host, float* pos_dev, long long np, int N, float* rho, int chunks,
+                     cudaStream_t st) {
+  unsigned long long* acc = nullptr;
+  int rc = deposit_scratch(N, &acc);
+  if (rc) return rc;
+  HostIo* io = nullptr;
+  if ((rc = host_io(&io))) return rc;
+  const long long n3 = (long long)N * N * N;
+  const long long per = (np + chunks - 1) / chunks;
+  MG_CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)n3 * sizeof(unsigned long long), st));
+  // the copies must not overwrite pos_dev before earlier work on st is done with it
+  MG_CUDA_TRY(cudaEventRecord(io->ev[kMaxIoChunks], st));
+  MG_CUDA_TRY(cudaStreamWaitEvent(io->cs, io->ev[kMaxIoChunks], 0));
+  prof_begin(PC_DEPOSIT, st, 12.0 * np);
+  for (int c = 0; c < chunks; ++c) {
+    const long long q0 = c * per, cnt = q0 >= np ? 0 : (np - q0 < per ? np - q0 : per);
+    if (cnt <= 0) break;
+    MG_CUDA_TRY(cudaMemcpyAsync(pos_dev + 3 * q0, pos_host + 3 * q0, (size_t)cnt * 12, cudaMemcpyHostToDevice,
+                                io->cs));
+    MG_CUDA_TRY(cudaEventRecord(io->ev[c], io->cs));
+    MG_CUDA_TRY(cudaStreamWaitEvent(st, io->ev[c], 0));
+    k_deposit_fixed<<<grid_for(cnt, kThreads, 1 << 20), kThreads, 0, st>>>(pos_dev + 3 * q0, cnt, N, acc);
+    note_launch(1);
+  }
+  prof_end(st);
+  prof_begin(PC_DEPOSIT_FINISH, st, 12.0 * n3);
+  k_deposit_finish<<<stream_grid(n3), kThreads, 0, st>>>(acc, n3, (double)n3 / (double)np, rho);
+  prof_end(st);
+  note_launch(1);
+  MG_CUDA_TRY(cudaGetLastError());
+  return MGGLAM_OK;
+}
+
+int gather_force_host(const ModelDev& m, int kind, const mgglam_params* prm, const double* field, int N,
+                      const float* pos_dev, long long np, float* force_dev, float* force_host, double prefactor,
+                      int chunks, cudaStream_t st) {
+  HostIo* io = nullptr;
+  int rc = host_io(&io);
+  if (rc) return rc;
+  // the transform and the first chunk's gather, then per chunk: gather, hand the chunk to the copy stream
+  const long long per = (np + chunks - 1) / chunks;
+  for (int c = 0; c < chunks; ++c) {
+    const long long q0 = c * per, cnt = q0 >= np ? 0 : (np - q0 < per ? np - q0 : per);
+    if (cnt <= 0) break;
+    if (c == 0) {
+      // transform + gather of the first chunk through the common path
+      if ((rc = gather_force(m, kind, prm->n, prm, field, N, pos_dev, cnt, force_dev, prefactor, st))) return rc;
+    } else {
+      if ((rc = gather_chunk(m, kind, prm, N, pos_dev + 3 * q0, cnt, force_dev + 3 * q0, prefactor, st))) return rc;
+    }
+    MG_CUDA_TRY(cudaEventRecord(io->ev[c], st));
+    MG_CUDA_TRY(cudaStreamWaitEvent(io->cs, io->ev[c], 0));
+    MG_CUDA_TRY(cudaMemcpyAsync(force_host + 3 * q0, force_dev + 3 * q0, (size_t)cnt * 12, cudaMemcpyDeviceToHost,
+                                io->cs));
+  }
+  // the caller's stream completes after the last copy
+  MG_CUDA_TRY(cudaEventRecord(io->ev[kMaxIoChunks + 1], io->cs));
+  MG_CUDA_TRY(cudaStreamWaitEvent(st, io->ev[kMaxIoChunks + 1], 0));
   return MGGLAM_OK;
 }
 

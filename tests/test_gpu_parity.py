@@ -310,3 +310,53 @@ def test_fp64_f_and_w_cycles_match_oracle_cycle_by_cycle(orc, mg, cycle):
     sm = mg.solve_scalar(pm, 1.0, cuda32(rho), fm, 1e-10)
     assert sm.converged
     assert relL2(fm.cpu().numpy(), ref.u) <= 1e-6
+
+
+def test_deposit_and_gather_read_pinned_host_memory_in_place(mg):
+    """Positions in page-locked host memory are read in place by the deposit and
+    the gather kernels, and forces written in place: the results are the device
+    path's, bit for bit (the same kernels, the same arithmetic)."""
+    N = 32
+    pos_h = inputs.zeldovich_positions(N, seed=52, sigma=1.2)
+    pos_d = cuda32(pos_h)
+    pos_p = torch.from_numpy(pos_h.astype(np.float32)).pin_memory()
+    rho_d = mg.deposit_cic(pos_d, N)
+    rho_p = mg.deposit_cic(pos_p, N)
+    assert torch.equal(rho_d, rho_p)
+    pg = mg.Params(model=0, n=1, fR0_abs=1e-5, box=64.0, precision=1, max_cycles=30)
+    field = torch.full((N, N, N), float("nan"), dtype=torch.float64, device="cuda")
+    mg.solve_scalar(pg, 1.0, rho_d, field, 1e-8)
+    f_d = mg.gather_force(pg, 1.0, field, pos_d, 0.5)
+    f_p = torch.empty((pos_h.shape[0], 3), dtype=torch.float32).pin_memory()
+    mg.gather_force(pg, 1.0, field, pos_p, 0.5, f_p)
+    torch.cuda.synchronize()
+    assert torch.equal(f_d.cpu(), f_p)
+    with pytest.raises(TypeError):
+        mg.deposit_cic(torch.from_numpy(pos_h.astype(np.float32)), N)  # pageable host memory: refused
+
+
+@pytest.mark.parametrize("chunks", [1, 3, 8])
+def test_host_io_pipelined_deposit_and_gather_match_device_path(mg, chunks):
+    """mgglam_deposit_cic_host / mgglam_gather_force_host (copies overlapped with
+    the kernels, in chunks that need not divide the particle count) give the
+    device path's mesh and forces bit for bit, and leave the positions in the
+    device staging buffer."""
+    N = 32
+    pos_h = inputs.zeldovich_positions(N, seed=53, sigma=1.2)[:-5]  # 32763 particles
+    pos_d = cuda32(pos_h)
+    pos_p = torch.from_numpy(pos_h.astype(np.float32)).pin_memory()
+    stage = torch.empty_like(pos_d)
+    rho_d = mg.deposit_cic(pos_d, N)
+    rho_h = mg.deposit_cic_host(pos_p, stage, N, chunks=chunks)
+    torch.cuda.synchronize()
+    assert torch.equal(rho_d, rho_h)
+    assert torch.equal(stage, pos_d)
+    pg = mg.Params(model=0, n=1, fR0_abs=1e-5, box=64.0, precision=1, max_cycles=30)
+    field = torch.full((N, N, N), float("nan"), dtype=torch.float64, device="cuda")
+    mg.solve_scalar(pg, 1.0, rho_d, field, 1e-8)
+    f_d = mg.gather_force(pg, 1.0, field, pos_d, 0.5)
+    f_host = torch.empty((pos_h.shape[0], 3), dtype=torch.float32).pin_memory()
+    f_stage = torch.empty_like(pos_d)
+    mg.gather_force_host(pg, 1.0, field, stage, f_stage, f_host, 0.5, chunks=chunks)
+    torch.cuda.synchronize()
+    assert torch.equal(f_d.cpu(), f_host)
