@@ -71,9 +71,12 @@ __global__ void __launch_bounds__(128) k_smooth32s(LevelF f, int n, float* __res
   int seg;
   bool act;
   split_lane(n, np, warp, lane, &r, &seg, &act);
-  int i = i0 + (int)(r / n);
+  const bool pow2 = (n & (n - 1)) == 0;
+  const int sh = __ffs(n) - 1;
+  int i = i0 + (int)(pow2 ? r >> sh : r / n);
   if (i >= n) i -= n;
-  smooth_split<K>(f, n, e, ub, rho, S, i, (int)(r % n), seg, act, colour, lane);
+  const int j = (int)(pow2 ? r & (n - 1) : r % n);
+  smooth_split<K>(f, n, e, ub, rho, S, i, j, seg, act, colour, lane);
 }
 
 // Quad version (levels with n % 4 == 0) on the planes i0 .. i0+np-1 (mod n):

@@ -110,8 +110,9 @@ __device__ __forceinline__ float fr_root_scaled_fast(float p) {
       return frcp(A * A + p3 + B * B);
     }
     // three real roots: the largest lies in [sqrt(3) r, 2 r), r = sqrt(-p/3);
-    // Newton from 2r converges monotonically (P convex there)
-    float y = 2.f * fsqrt(-p3);
+    // Newton from 2r converges monotonically (P convex there).  Three steps
+    // (error <= 15% -> ~1e-6): with two, the solves to 1e-11 stall.
+    float y = 2.f * fsqrt_nn(-p3);
 #pragma unroll
     for (int it = 0; it < 3; ++it) y -= fdiv((y * y + p) * y - 1.f, 3.f * y * y + p);
     return y;
@@ -147,7 +148,7 @@ __device__ __forceinline__ float sym_root_fast(float p, float q, float u_old) {
     x = fdiv(hq + hq, A * A + p3 + B * B);
   } else {
     const float aq = -2.f * hq;  // q of the positive-side problem
-    x = 2.f * fsqrt(-p3);
+    x = 2.f * fsqrt_nn(-p3);
 #pragma unroll
     for (int it = 0; it < 3; ++it) x -= fdiv((x * x + p) * x + aq, 3.f * x * x + p);
   }
@@ -351,7 +352,9 @@ __device__ __forceinline__ void split_lane(int n, int np, long long warp, int la
   const int nq = n >> 3;
   const long long rows = (long long)np * n;
   if (nq <= 32) {
-    const int per = 32 / nq, sub = lane / nq;
+    const bool pow2 = (nq & (nq - 1)) == 0;  // shifts instead of divisions (the usual meshes)
+    const int sh = __ffs(nq) - 1;
+    const int per = pow2 ? 32 >> sh : 32 / nq, sub = pow2 ? lane >> sh : lane / nq;
     *r = warp * per + sub;
     *seg = lane - sub * nq;
     *act = sub < per;
