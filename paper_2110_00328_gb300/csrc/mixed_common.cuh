@@ -183,6 +183,65 @@ __device__ __forceinline__ void restrict_quad(const LevelF& f, int nf, const flo
 }
 
 // ---------------------------------------------------------------------------
+// FAS source of a coarse level, four cells per lane (side % 4 == 0)
+// ---------------------------------------------------------------------------
+//
+// S <- M(Re) - S at the four cells k0 .. k0+3 of row (i, j) (S holds R d on
+// entry; Eq. general_pde_numerical_coarse), with the neighbour quantities of
+// Re read as 16-byte quads from the row and the four rows around it and the
+// two k-neighbours outside the quad from the adjacent lanes.  All 32 lanes of a
+// warp take part; lanes past the row end work on a clamped quad and store
+// nothing.
+template <int K>
+__device__ __forceinline__ void fas_quad(const LevelF& f, int n, const float* __restrict__ Re,
+                                         const float* __restrict__ ub, const float* __restrict__ rho,
+                                         float* __restrict__ S, int i, int j, int tq, int lane) {
+  constexpr bool FR = is_fr(K);
+  constexpr bool RHO = (K == KSYM) || (K == KCQ);
+  const int nq = n >> 2;
+  const bool act = tq < nq;
+  const int k0 = 4 * (act ? tq : nq - 1);
+  const long long nn = (long long)n * n;
+  const long long c0 = (long long)i * nn + (long long)j * n + k0;
+  const long long djp = (j + 1 < n) ? (long long)n : -(long long)(n - 1) * n;
+  const long long djm = (j > 0) ? -(long long)n : (long long)(n - 1) * n;
+  const long long dip = (i + 1 < n) ? nn : -(long long)(n - 1) * nn;
+  const long long dim = (i > 0) ? -nn : (long long)(n - 1) * nn;
+  auto q4 = [&](long long c) {
+    const float4 E = ld4(Re + c);
+    if constexpr (FR) {
+      const float4 U = ld4(ub + c);
+      return make_float4(dw<K>(U.x, E.x), dw<K>(U.y, E.y), dw<K>(U.z, E.z), dw<K>(U.w, E.w));
+    } else {
+      return E;
+    }
+  };
+  const float4 E = ld4(Re + c0), U = ld4(ub + c0), Sv = ld4(S + c0);
+  const float4 q = FR ? make_float4(dw<K>(U.x, E.x), dw<K>(U.y, E.y), dw<K>(U.z, E.z), dw<K>(U.w, E.w)) : E;
+  const float4 P = q4(c0 + djp), M = q4(c0 + djm), A = q4(c0 + dip), B = q4(c0 + dim);
+  float4 R = make_float4(1.f, 1.f, 1.f, 1.f);
+  if constexpr (RHO) {
+    if (rho) R = ld4(rho + c0);
+  }
+  float qm = __shfl_up_sync(0xffffffffu, q.w, 1);
+  float qp = __shfl_down_sync(0xffffffffu, q.x, 1);
+  if (lane == 0) {
+    const long long c = c0 + (k0 == 0 ? n - 1 : -1);
+    qm = nbq<K>(FR ? ub[c] : 0.f, Re[c]);
+  }
+  if (lane == 31 || tq + 1 >= nq) {
+    const long long c = c0 + (k0 + 4 == n ? 4 - n : 4);
+    qp = nbq<K>(FR ? ub[c] : 0.f, Re[c]);
+  }
+  float4 out;
+  out.x = local_M<K>(f, U.x, E.x, R.x, (qm + q.y) + (P.x + M.x) + (A.x + B.x)) - Sv.x;
+  out.y = local_M<K>(f, U.y, E.y, R.y, (q.x + q.z) + (P.y + M.y) + (A.y + B.y)) - Sv.y;
+  out.z = local_M<K>(f, U.z, E.z, R.z, (q.y + q.w) + (P.z + M.z) + (A.z + B.z)) - Sv.z;
+  out.w = local_M<K>(f, U.w, E.w, R.w, (q.z + qp) + (P.w + M.w) + (A.w + B.w)) - Sv.w;
+  if (act) *reinterpret_cast<float4*>(S + c0) = out;
+}
+
+// ---------------------------------------------------------------------------
 // Prolongation-correction, four fine cells per lane (fine side % 4 == 0)
 // ---------------------------------------------------------------------------
 //

@@ -171,6 +171,15 @@ __global__ void __launch_bounds__(128) k_prolong_correct32q(int nc, const float*
                    threadIdx.x);
 }
 
+// FAS source, four cells per lane (n % 4 == 0, n >= 8): grid (ceil(n/128), n, n/4).
+template <int K>
+__global__ void __launch_bounds__(128) k_fas_source32q(LevelF f, int n, const float* __restrict__ Re,
+                                                       const float* __restrict__ ub, const float* __restrict__ rho,
+                                                       float* __restrict__ S) {
+  fas_quad<K>(f, n, Re, ub, rho, S, blockIdx.z * 4 + threadIdx.y, blockIdx.y, blockIdx.x * 32 + threadIdx.x,
+              threadIdx.x);
+}
+
 // In place: S <- M^H(Re) - S (S holds R d on entry).
 template <int K>
 __global__ void __launch_bounds__(128) k_fas_source32(LevelF f, int n, const float* __restrict__ Re,
@@ -361,16 +370,28 @@ static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
 
 static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode);
 
+// The FAS source on level l (natural layout).
+static int fas_source(const MixedCtx& C, int l, cudaStream_t st) {
+  Level& H = C.ws->lev[l];
+  const float* rhoH = C.need_rho ? H.rho32 : nullptr;
+  if (H.n % 4 == 0 && H.n >= 8) {
+    const dim3 g((H.n / 4 + 31) / 32, H.n, H.n / 4);
+    MG_DISPATCH32(C.m.kind, (k_fas_source32q<KK><<<g, dim3(32, 4), 0, st>>>(C.lf[l], H.n, H.Re, H.ub, rhoH, H.S32)));
+  } else {
+    const int bh = bx_for(H.n);
+    MG_DISPATCH32(C.m.kind, (k_fas_source32<KK><<<grid3(H.n, H.n, H.n, bh), bh, 0, st>>>(C.lf[l], H.n, H.Re, H.ub,
+                                                                                        rhoH, H.S32)));
+  }
+  return MGGLAM_OK;
+}
+
 // Coarse-grid correction seen from the finest level: the FAS source on level 1
 // and the cycle(s) on levels >= 1 (V: one; W: two W; F: F then V), enqueued directly.
 static int coarse_part_direct(const MixedCtx& C, cudaStream_t st) {
-  Level& H = C.ws->lev[1];
-  const float* rhoH = C.need_rho ? H.rho32 : nullptr;
-  const int bh = bx_for(H.n);
-  MG_DISPATCH32(C.m.kind, (k_fas_source32<KK><<<grid3(H.n, H.n, H.n, bh), bh, 0, st>>>(C.lf[1], H.n, H.Re, H.ub,
-                                                                                      rhoH, H.S32)));
+  int rc = fas_source(C, 1, st);
+  if (rc) return rc;
   const int mode = C.prm->cycle;
-  int rc = vcycle32(C, 1, st, mode);
+  rc = vcycle32(C, 1, st, mode);
   if (rc || mode == 0) return rc;
   return vcycle32(C, 1, st, mode == 2 ? 2 : 0);
 }
@@ -495,7 +516,6 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode) {
   if ((rc = smooth32(C, l, C.prm->nu1, st))) return rc;
   if (l == 0) prof_end(st);
   Level& H = ws->lev[l + 1];
-  const float* rhoH = C.need_rho ? H.rho32 : nullptr;
   const int bh = bx_for(H.n);
   if (l == 0) prof_begin(PC_RESTRICT32_FINE, st, 14.0 * L.n3);
   if (l == 0 && C.split) {
@@ -515,8 +535,7 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode) {
     prof_begin(PC_COARSE_LEVELS, st, 0.0);
     if ((rc = coarse_part(C, st))) return rc;
   } else {
-    MG_DISPATCH32(C.m.kind, (k_fas_source32<KK><<<grid3(H.n, H.n, H.n, bh), bh, 0, st>>>(C.lf[l + 1], H.n, H.Re,
-                                                                                        H.ub, rhoH, H.S32)));
+    if ((rc = fas_source(C, l + 1, st))) return rc;
     if ((rc = vcycle32(C, l + 1, st, mode))) return rc;
     if (mode != 0 && (rc = vcycle32(C, l + 1, st, mode == 2 ? 2 : 0))) return rc;
   }
