@@ -360,3 +360,38 @@ def test_host_io_pipelined_deposit_and_gather_match_device_path(mg, chunks):
     mg.gather_force_host(pg, 1.0, field, stage, f_stage, f_host, 0.5, chunks=chunks)
     torch.cuda.synchronize()
     assert torch.equal(f_d.cpu(), f_host)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("key", ["fr1", "sym", "cq"])
+def test_uniform_density_is_solved_by_the_background(orc, mg, key, precision):
+    """Degenerate input: a uniform density has delta = 0, and the background
+    field solves the discrete equations (f(R) ubar, symmetron ubar, CQ 0) up to
+    rounding, so the solve starting from the background stops after zero cycles
+    and returns the background value everywhere.  (With delta = 0 the relative
+    residual's normaliser falls back to 1, so the symmetron's rounding floor is
+    ~a^2/(2 xi^2) x 1e-16 ~ 5e-10: tol 1e-6.)"""
+    N = 32
+    po, pg = both_params(orc, mg, key, box=64.0, precision=precision, max_cycles=5)
+    rho = torch.full((N, N, N), 3.25, dtype=torch.float32, device="cuda")  # any constant: normalised to mean 1
+    field = torch.full((N, N, N), float("nan"), dtype=torch.float64, device="cuda")
+    st = mg.solve_scalar(pg, 1.0, rho, field, 1e-6)
+    ubar = orc.background(po, N)["ubar"] if key != "cq" else 0.0
+    assert st.converged and st.cycles == 0
+    got = field.cpu().numpy()
+    assert np.abs(got - ubar).max() <= 1e-15 * max(1.0, abs(ubar))
+
+
+def test_largest_mesh_argument_and_small_particle_counts(mg):
+    """Boundaries of the deposit's arguments: N above 2048 is rejected before
+    any work, and a single particle deposits its full mass N^3 over its eight
+    cells."""
+    import ctypes
+    lib = mg.load()
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: the check fails first
+    assert lib.mgglam_deposit_cic(fake, 1, 2049, fake, None) == -2
+    N = 8
+    pos = torch.tensor([[3.3, 4.6, 0.2]], dtype=torch.float32, device="cuda")
+    rho = mg.deposit_cic(pos, N).cpu().numpy().astype(np.float64)
+    assert np.count_nonzero(rho) == 8
+    assert rho.sum() == pytest.approx(N ** 3, rel=1e-6)
