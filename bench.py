@@ -559,7 +559,7 @@ def run_ours(args) -> None:
                    "parallelism": f"independent realisation per GPU x{world}"},
         "time_to_tol_ms": round(sol / args.steps, 3), "deposit_ms": round(dep / args.steps, 3),
         "gather_ms": round(gat / args.steps, 3), "cycles": cycles, "outer_steps": recs[-1][0].outer,
-        "final_resid": recs[-1][0].resid, "solved_Mcells_per_s": round(N_MESH ** 3 * args.steps * world / (sol * 1e-3) / 1e6, 1),
+        "final_resid": recs[-1][0].resid, "resid_per_outer_step": recs[-1][0].hist, "solved_Mcells_per_s": round(N_MESH ** 3 * args.steps * world / (sol * 1e-3) / 1e6, 1),
         "roofline": roof, "kernels": kernels, "timed_kernel_ms": round(timed_total, 3),
         "gpu_launches": int(launches),
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(pos_host.numel() * 4),

@@ -101,7 +101,8 @@ typedef struct {
 /* Per-solve statistics.  resid values are the relative global residual:
  * RMS of the fine-level local residual divided by the RMS of the model's
  * linear source term (f(R): Om delta/a; symmetron: a^2/(2xi^2)(a_star/a)^3 ubar delta;
- * CQ: 3 beta Om e^{beta phibar} delta / a), or by 1 when that is zero. */
+ * CQ: 3 beta Om e^{beta phibar} delta / a), or by 1 when that is zero (below
+ * 1e-12 of the term's coefficient: a uniform density, up to rounding). */
 typedef struct {
   int cycles;               /* multigrid cycles run (MIXED: inner FP32 V-cycles) */
   int outer;                /* MIXED: FP64 defect-correction steps */

@@ -652,7 +652,7 @@ int solve_adjoint(const mgglam_params* prm, double a, const double* field, const
   // inner FP32 cycles per FP64/float-float step: fixed, or (inner_cycles = 0)
   // enough for tol at the observed contraction, capped where one single-
   // precision correction stops gaining (~1e-6), as in the forward solve
-  double rho_est = 0.1;
+  double rho_est = kInitialContraction;
   int status = MGGLAM_OK;
   while (!(eps <= tol) && cyc < prm->max_cycles) {
     if (!isfinite(eps)) { status = MGGLAM_ERR_NONFINITE; break; }
@@ -660,7 +660,7 @@ int solve_adjoint(const mgglam_params* prm, double a, const double* field, const
     if (inner <= 0) {
       const double lr = log(rho_est);
       const int need = (int)ceil(log(fmax(tol, 1e-300) / eps) / lr - 1e-9);
-      const int cap = (int)ceil(log(1e-6) / lr);
+      const int cap = (int)ceil(log(kFp32StepGain) / lr - 1e-9);
       inner = need < 1 ? 1 : (need > cap ? cap : need);
     }
     const double eps_before = eps;
@@ -673,7 +673,7 @@ int solve_adjoint(const mgglam_params* prm, double a, const double* field, const
     if ((rc = residual())) return rc;
     eps = sqrt(w->h_scal[0] / (double)n3) / snorm;
     if (nh < 64) S->resid_hist[nh++] = eps;
-    if (done > 0 && eps > 0.0 && eps < eps_before && eps / eps_before > 1e-5)
+    if (done > 0 && eps > 0.0 && eps < eps_before && eps / eps_before > kFp32StepGain)
       rho_est = fmin(0.5, fmax(0.01, pow(eps / eps_before, 1.0 / done)));
   }
   const int go = grid_for(n3);

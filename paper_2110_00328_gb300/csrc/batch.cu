@@ -785,7 +785,7 @@ int solve_batch(int count, const mgglam_params* prm, const double* a, const floa
   for (int s = 0; s < count; ++s) {
     const double n3 = (double)B->sv[s].N * B->sv[s].N * B->sv[s].N;
     const double src = sqrt(B->h_sums[count + s] / n3);
-    snorm[s] = src > 0.0 ? src : 1.0;
+    snorm[s] = source_norm(models[s], src);
     eps[s] = sqrt(B->h_sums[s] / n3) / snorm[s];
     memset(&lst[s], 0, sizeof(mgglam_stats));
     lst[s].resid0 = eps[s];
@@ -823,7 +823,7 @@ int solve_batch(int count, const mgglam_params* prm, const double* a, const floa
     B->vsig = sig;
   }
   int cyc = 0, outer = 0, status = MGGLAM_OK;
-  double rho_est = 0.1;
+  double rho_est = kInitialContraction;
   const int maxc = prm[0].max_cycles;
   auto worst = [&]() {
     double w = 0.0;
@@ -849,7 +849,7 @@ int solve_batch(int count, const mgglam_params* prm, const double* a, const floa
     if (inner <= 0) {
       const double lr = log(rho_est);
       const int need = (int)ceil(log(1.0 / worst()) / lr - 1e-9);
-      const int cap = (int)ceil(log(1e-6) / lr);
+      const int cap = (int)ceil(log(kFp32StepGain) / lr - 1e-9);
       inner = need < 1 ? 1 : (need > cap ? cap : need);
     }
     double worst_before = worst();
@@ -874,7 +874,7 @@ int solve_batch(int count, const mgglam_params* prm, const double* a, const floa
       if (lst[s].outer < 64) lst[s].resid_hist[lst[s].outer] = eps[s];
     }
     const double worst_after = worst();
-    if (done > 0 && worst_after > 0.0 && worst_after < worst_before && worst_after / worst_before > 1e-5)
+    if (done > 0 && worst_after > 0.0 && worst_after < worst_before && worst_after / worst_before > kFp32StepGain)
       rho_est = fmin(0.5, fmax(0.01, pow(worst_after / worst_before, 1.0 / done)));
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

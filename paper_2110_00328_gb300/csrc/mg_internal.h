@@ -12,6 +12,22 @@ namespace mg {
 
 constexpr int kMaxLevels = 16;
 
+// Inner-cycle schedule of the mixed-precision solvers (host side).
+// Residual reduction one FP32 inner solve can deliver before its own rounding
+// limits it (measured: a step stalls at a few 1e-7 of its starting residual).
+// The inner-cycle count of an outer step is capped at what reaches it: more
+// cycles gain nothing until the next float-float/FP64 residual.
+constexpr double kFp32StepGain = 1e-5;
+
+// Per-cycle residual contraction assumed before one has been measured.  A
+// V(2,1) cycle contracts the f(R) residual by ~0.08 on the 256^3 workload; the
+// estimate errs on the slow side, because planning too few cycles costs a
+// whole extra outer step (a float-float residual and a host synchronisation),
+// while planning one too many costs one cycle.  Convergence is always decided
+// on the outer residual, and a measured contraction replaces this estimate as
+// soon as an outer step is not limited by single precision.
+constexpr double kInitialContraction = 0.1;
+
 // One multigrid level.  FP64 arrays serve the FP64 path (and the FP64 fine
 // level of the mixed path); FP32 arrays serve the mixed path's inner cycles.
 struct Level {
@@ -61,6 +77,12 @@ struct Workspace {
 enum Scalar { SC_MEAN = 0, SC_SUMSQ = 1, SC_SRC = 2, SC_FLAG = 3, SC_FFC = 8, SC_COUNT = 16 };
 
 int count_levels(int N, int levels);
+
+// Normaliser of the relative residual: the RMS of the model's linear source
+// term (coefficient x RMS(delta)), or 1 where the density is uniform.  A
+// source below 1e-12 of its coefficient counts as uniform: that is rounding in
+// delta = rho/mean - 1, not structure.
+double source_norm(const ModelDev& m, double src_rms);
 
 // Build the device model constants for level-independent use (c~ from N_fine).
 int make_model(const mgglam_params* prm, double a, int Nfine, ModelDev* m);

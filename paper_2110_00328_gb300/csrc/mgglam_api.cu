@@ -15,6 +15,15 @@ namespace mg {
 // c / H0 in Mpc/h: the speed of light over 100 km/s/Mpc.
 static const double kCOverH0 = 299792.458 / 100.0;
 
+double source_norm(const ModelDev& m, double src_rms) {
+  double coef;
+  if (is_fr(m.kind)) coef = m.om_a;
+  else if (m.kind == KSYM) coef = m.msym * m.rat3 * m.ubar;
+  else coef = m.cq_src;
+  coef = fabs(coef);
+  return src_rms > 1e-12 * coef && src_rms > 0.0 ? src_rms : 1.0;
+}
+
 int count_levels(int N, int levels) {
   int nl = 1, n = N;
   if (levels > 0) {

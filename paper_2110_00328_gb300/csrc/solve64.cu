@@ -460,7 +460,7 @@ int solve_fp64(const mgglam_params* prm, double a, const float* rho, int N, doub
   MG_CUDA_TRY(cudaMemcpyAsync(ws->h_scalars, ws->scalars, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
   MG_CUDA_TRY(cudaStreamSynchronize(st));
   const double src = sqrt(ws->h_scalars[SC_SRC] / (double)n3);
-  const double snorm = src > 0.0 ? src : 1.0;
+  const double snorm = source_norm(m, src);
   double eps = sqrt(ws->h_scalars[SC_SUMSQ] / (double)n3) / snorm;
   mgglam_stats local;
   mgglam_stats* S = stats ? stats : &local;

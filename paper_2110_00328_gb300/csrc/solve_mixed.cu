@@ -702,7 +702,7 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
   MG_CUDA_TRY(cudaStreamSynchronize(st));
   MG_CUDA_TRY(cudaGetLastError());
   const double src = sqrt(ws->h_scalars[SC_SRC] / (double)n3);
-  const double snorm = src > 0.0 ? src : 1.0;
+  const double snorm = source_norm(C.m, src);
   double eps = sqrt(ws->h_scalars[SC_SUMSQ] / (double)n3) / snorm;
   mgglam_stats local;
   mgglam_stats* S = stats ? stats : &local;
@@ -712,10 +712,8 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
   int cyc = 0, outer = 0, nh = 1;
   // Inner cycles per outer step: fixed (prm->inner_cycles > 0), or adaptive:
   // enough cycles to reach tol at the contraction rho observed so far, but no
-  // more than single precision can use in one step (a correction is accurate to
-  // ~1e-6 of itself, so rho^k below 1e-6 gains nothing before the next FP64
-  // residual).
-  double rho_est = 0.1;
+  // more than single precision can use in one step (kFp32StepGain).
+  double rho_est = kInitialContraction;
   int status = MGGLAM_OK;
   while (!(eps <= tol) && cyc < prm->max_cycles) {
     if (!isfinite(eps)) { status = MGGLAM_ERR_NONFINITE; break; }
@@ -723,7 +721,7 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
     if (inner <= 0) {
       const double lr = log(rho_est);
       const int need = (int)ceil(log(fmax(tol, 1e-300) / eps) / lr - 1e-9);
-      const int cap = (int)ceil(log(1e-6) / lr);
+      const int cap = (int)ceil(log(kFp32StepGain) / lr - 1e-9);
       inner = need < 1 ? 1 : (need > cap ? cap : need);
     }
     const double eps_before = eps;
@@ -747,7 +745,7 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
     if (done > 0 && eps > 0.0 && eps < eps_before) {
       // per-cycle contraction of this step, when it was not limited by single precision
       const double r = pow(eps / eps_before, 1.0 / done);
-      if (eps / eps_before > 1e-5) rho_est = fmin(0.5, fmax(0.01, r));
+      if (eps / eps_before > kFp32StepGain) rho_est = fmin(0.5, fmax(0.01, r));
     }
   }
   if (status == MGGLAM_OK && !isfinite(eps)) status = MGGLAM_ERR_NONFINITE;
