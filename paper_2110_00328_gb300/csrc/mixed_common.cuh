@@ -251,10 +251,14 @@ __device__ __forceinline__ void fas_quad(const LevelF& f, int n, const float* __
 // (2tq, 2tq+1), takes the combinations at 2tq-1 and 2tq+2 from the adjacent
 // lanes, and weights (3, 1) along k.  f(R): where u + e would not be positive
 // the total field is halved instead (e <- (e_old - u)/2).
-template <bool FR, class FL = NatLayout>
+// QK >= 0 (split layout, f(R) n = QK): also writes the second colour's stored
+// neighbour quantity q = Delta w(u, e) into qf (smooth_split with QS), so that
+// the next first-colour pass sees the corrected values.
+template <bool FR, class FL = NatLayout, int QK = -1>
 __device__ __forceinline__ void prolong_quad(int nc, const float* __restrict__ eH, const float* __restrict__ Re,
                                              const float* __restrict__ ub, float* __restrict__ ef, int i, int j,
-                                             int tq, int lane) {
+                                             int tq, int lane, float* __restrict__ qf = nullptr) {
+  static_assert(QK < 0 || (FR && QK != KFR0), "stored q: f(R) n = 1, 2");
   const int nf = nc << 1, nq = nf >> 2;
   const bool act = tq < nq;
   const int t = act ? tq : nq - 1;
@@ -287,14 +291,25 @@ __device__ __forceinline__ void prolong_quad(int nc, const float* __restrict__ e
   const float4 old = FL::q(ef, nf, i, j, k0);
   float4 v = make_float4(old.x + (3.f * Rx + Rm) * w, old.y + (3.f * Rx + Ry) * w, old.z + (3.f * Ry + Rx) * w,
                          old.w + (3.f * Ry + Rp) * w);
+  float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
   if constexpr (FR) {
-    const float4 u = FL::q(ub, nf, i, j, k0);
+    u = FL::q(ub, nf, i, j, k0);
     if (!(u.x + v.x > 0.f)) v.x = 0.5f * (old.x - u.x);
     if (!(u.y + v.y > 0.f)) v.y = 0.5f * (old.y - u.y);
     if (!(u.z + v.z > 0.f)) v.z = 0.5f * (old.z - u.z);
     if (!(u.w + v.w > 0.f)) v.w = 0.5f * (old.w - u.w);
   }
   if (act) FL::st(ef, nf, i, j, k0, v);
+  if constexpr (QK >= 0) {
+    // second-colour cells of the quad: k odd where i + j is even, else k even
+    if (act) {
+      const int h = nf >> 1;
+      const long long H = (long long)nf * nf * h, r = ((long long)i * nf + j) * h + (k0 >> 1);
+      *reinterpret_cast<float2*>(qf + H + r) = ((i + j) & 1)
+                                                   ? make_float2(dw<QK>(u.x, v.x), dw<QK>(u.z, v.z))
+                                                   : make_float2(dw<QK>(u.y, v.y), dw<QK>(u.w, v.w));
+    }
+  }
 }
 
 // 1/x in FP64 by one Newton-Raphson refinement y1 = y0 (2 - x y0) of a

@@ -61,10 +61,12 @@ __global__ void __launch_bounds__(64) k_smooth32(LevelF f, int n, float* __restr
 // i0 .. i0+np-1 (mod n): rows of n/8 lanes packed into warps (several short rows
 // per warp, a long row over several warps), four cells per lane; block (32, 4),
 // 1D grid over warps.
-template <int K>
+// QS: f(R) n = 1, 2 with the neighbour quantity q stored beside e (smooth_split).
+template <int K, bool QS = false>
 __global__ void __launch_bounds__(128) k_smooth32s(LevelF f, int n, float* __restrict__ e,
                                                    const float* __restrict__ ub, const float* __restrict__ rho,
-                                                   const float* __restrict__ S, int colour, int i0, int np) {
+                                                   const float* __restrict__ S, int colour, int i0, int np,
+                                                   float* __restrict__ q) {
   const int lane = threadIdx.x;
   const long long warp = (long long)blockIdx.x * 4 + threadIdx.y;
   long long r;
@@ -76,7 +78,7 @@ __global__ void __launch_bounds__(128) k_smooth32s(LevelF f, int n, float* __res
   int i = i0 + (int)(pow2 ? r >> sh : r / n);
   if (i >= n) i -= n;
   const int j = (int)(pow2 ? r & (n - 1) : r % n);
-  smooth_split<K>(f, n, e, ub, rho, S, i, j, seg, act, colour, lane);
+  smooth_split<K, QS>(f, n, e, ub, rho, S, i, j, seg, act, colour, lane, q);
 }
 
 // Quad version (levels with n % 4 == 0) on the planes i0 .. i0+np-1 (mod n):
@@ -163,12 +165,13 @@ __global__ void __launch_bounds__(128) k_residual_restrict32q(LevelF f, int nf, 
 }
 
 // Prolongation: grid (ceil(nf/128), nf [j], nf/4 [i]).
-template <bool FR, class FL = NatLayout>
+template <bool FR, class FL = NatLayout, int QK = -1>
 __global__ void __launch_bounds__(128) k_prolong_correct32q(int nc, const float* __restrict__ eH,
                                                             const float* __restrict__ Re,
-                                                            const float* __restrict__ ub, float* __restrict__ ef) {
-  prolong_quad<FR, FL>(nc, eH, Re, ub, ef, blockIdx.z * 4 + threadIdx.y, blockIdx.y, blockIdx.x * 32 + threadIdx.x,
-                   threadIdx.x);
+                                                            const float* __restrict__ ub, float* __restrict__ ef,
+                                                            float* __restrict__ qf = nullptr) {
+  prolong_quad<FR, FL, QK>(nc, eH, Re, ub, ef, blockIdx.z * 4 + threadIdx.y, blockIdx.y,
+                           blockIdx.x * 32 + threadIdx.x, threadIdx.x, qf);
 }
 
 // FAS source, four cells per lane (n % 4 == 0, n >= 8): grid (ceil(n/128), n, n/4).
@@ -271,6 +274,7 @@ struct MixedCtx {
   bool split;         // the finest level in the red-black split layout
   bool ff_resid;      // fine residual in float-float (f(R), symmetron) rather than FP64 (CQ)
   int tail_level;     // first level (>= 1) run by the one-block tail kernel, or -1
+  float* qs;          // split f(R) n = 1, 2: the finest level's stored neighbour quantity, else nullptr
 };
 
 static FFC* ffc_of(Workspace* ws) { return reinterpret_cast<FFC*>(ws->scalars + SC_FFC); }
@@ -335,8 +339,18 @@ static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
         if (np <= 0) return MGGLAM_OK;
         if (split) {
           const unsigned blocks = (unsigned)((split_warps(L.n, np) + 3) / 4);
+          if (C.qs) {
+            if (C.m.kind == KFR1)
+              k_smooth32s<KFR1, true><<<blocks, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, nullptr, L.S32, parity,
+                                                                      i0, np, C.qs);
+            else
+              k_smooth32s<KFR2, true><<<blocks, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, nullptr, L.S32, parity,
+                                                                      i0, np, C.qs);
+            note_launch(1);
+            return MGGLAM_OK;
+          }
           MG_DISPATCH32(C.m.kind, (k_smooth32s<KK><<<blocks, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, rho,
-                                                                                   L.S32, parity, i0, np)));
+                                                                                   L.S32, parity, i0, np, nullptr)));
           return MGGLAM_OK;
         }
         const dim3 g((L.n / 4 + 31) / 32, L.n, (np + 3) / 4);
@@ -543,7 +557,12 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode) {
   const int bf = bx_for(L.n);
   if (l == 0 && C.split) {
     const dim3 g((L.n / 4 + 31) / 32, L.n, L.n / 4);
-    if (is_fr(C.m.kind)) k_prolong_correct32q<true, SplitLayout><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
+    if (C.qs && C.m.kind == KFR1)
+      k_prolong_correct32q<true, SplitLayout, KFR1><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.qs);
+    else if (C.qs)
+      k_prolong_correct32q<true, SplitLayout, KFR2><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.qs);
+    else if (is_fr(C.m.kind))
+      k_prolong_correct32q<true, SplitLayout><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
     else k_prolong_correct32q<false, SplitLayout><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
   } else if (L.n % 4 == 0 && L.n >= 8) {
     const dim3 g((L.n / 4 + 31) / 32, L.n, L.n / 4);
@@ -655,6 +674,8 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
   C.ff_resid = C.m.kind != KCQ;
   // red-black split fine level: float-float residual with its 8 x 32 tiles, per-colour smoothing
   C.split = C.ff_resid && prm->sweep_chunk <= 0 && C.ws->lev[0].n % 32 == 0;
+  // the split level never runs the fused sweep, so its second buffer holds q
+  C.qs = C.split && (C.m.kind == KFR1 || C.m.kind == KFR2) ? C.ws->lev[0].e_alt : nullptr;
   C.tail_level = -1;  // the one-block tail runs V-cycles only
   const long long tail_cells = prm->tail_cells == 0 ? 512 : (prm->tail_cells > kTailMaxCells ? kTailMaxCells : prm->tail_cells);
   for (int l = 1; l < C.ws->nlev && tail_cells > 0 && prm->cycle == 0; ++l)
@@ -727,6 +748,7 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
     const double eps_before = eps;
     int done = 0;
     MG_CUDA_TRY(cudaMemsetAsync(F.e, 0, F.n3 * sizeof(float), st));
+    if (C.qs) MG_CUDA_TRY(cudaMemsetAsync(C.qs, 0, F.n3 * sizeof(float), st));  // Delta w(u, 0) = 0
     for (int c = 0; c < inner && cyc < prm->max_cycles; ++c, ++cyc, ++done)
       if ((rc = vcycle32(C, 0, st, C.prm->cycle))) return rc;
     prof_begin(PC_APPLY_CORR, st, 20.0 * n3);

@@ -416,12 +416,22 @@ struct SplitLayout {
 // colour's e and u at m0 .. m0+3 of the same row and of the rows (i, j+-1),
 // (i+-1, j); the one k-neighbour outside that window comes from the adjacent
 // lane (p = 0: m0 - 1; p = 1: m0 + 4), or a load at a row end.
-template <int K>
+//
+// Stored neighbour quantity (QS, f(R) n = 1, 2): the level also keeps
+// q = Delta w(u, e) of every cell in the same layout, written with e by the
+// pass that updates the cell (and by the prolongation for the second colour).
+// A pass then reads the other colour's q instead of its e and u -- five rows
+// of loads and five Delta w evaluations fewer per cell, the same DRAM bytes
+// (q written beside e).  q is formed by the same expression from the same
+// values, so the sweep computes what it computes without it, up to where the
+// compiler fuses a product into the neighbouring sum.
+template <int K, bool QS = false>
 __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __restrict__ e,
                                              const float* __restrict__ ub, const float* __restrict__ rho,
                                              const float* __restrict__ S, int i, int j, int seg, bool act,
-                                             int colour, int lane) {
+                                             int colour, int lane, float* __restrict__ q = nullptr) {
   constexpr bool FR = is_fr(K);
+  static_assert(!QS || K == KFR1 || K == KFR2, "the stored neighbour quantity differs from e for f(R) n = 1, 2 only");
   constexpr bool RHO = (K == KSYM) || (K == KCQ);
   const int h = n >> 1, nq = h >> 2;
   const int m0 = 4 * seg;
@@ -437,6 +447,35 @@ __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __re
   const float* e1 = e + (long long)(colour ^ 1) * H + r0;   // other colour
   const float* uo = ub + (long long)colour * H + r0;
   const float* u1 = ub + (long long)(colour ^ 1) * H + r0;
+  if constexpr (QS) {
+    const float* q1 = q + (long long)(colour ^ 1) * H + r0;  // other colour's q
+    const float4 U = ld4(uo), Sv = ld4(S + (long long)colour * H + r0);
+    const float4 Q = ld4(q1);
+    const float4 Qjp = ld4(q1 + djp), Qjm = ld4(q1 + djm), Qip = ld4(q1 + dip), Qim = ld4(q1 + dim);
+    float qm = __shfl_up_sync(0xffffffffu, Q.w, 1);
+    float qp = __shfl_down_sync(0xffffffffu, Q.x, 1);
+    if (p == 0 && (seg == 0 || lane == 0)) qm = q1[m0 == 0 ? h - 1 : -1];
+    if (p == 1 && (seg == nq - 1 || lane == 31)) qp = q1[m0 + 4 == h ? 4 - h : 4];
+    const float k0s = p ? Q.x + Q.y : qm + Q.x;
+    const float k1s = p ? Q.y + Q.z : Q.x + Q.y;
+    const float k2s = p ? Q.z + Q.w : Q.y + Q.z;
+    const float k3s = p ? Q.w + qp : Q.z + Q.w;
+    const float L0 = k0s + (Qjp.x + Qjm.x) + (Qip.x + Qim.x);
+    const float L1 = k1s + (Qjp.y + Qjm.y) + (Qip.y + Qim.y);
+    const float L2 = k2s + (Qjp.z + Qjm.z) + (Qip.z + Qim.z);
+    const float L3 = k3s + (Qjp.w + Qjm.w) + (Qip.w + Qim.w);
+    float4 out;
+    out.x = update_e_fast<K>(f, U.x, 0.f, 1.f, Sv.x, L0);
+    out.y = update_e_fast<K>(f, U.y, 0.f, 1.f, Sv.y, L1);
+    out.z = update_e_fast<K>(f, U.z, 0.f, 1.f, Sv.z, L2);
+    out.w = update_e_fast<K>(f, U.w, 0.f, 1.f, Sv.w, L3);
+    if (act) {
+      *reinterpret_cast<float4*>(eo) = out;
+      *reinterpret_cast<float4*>(q + (long long)colour * H + r0) =
+          make_float4(nbq<K>(U.x, out.x), nbq<K>(U.y, out.y), nbq<K>(U.z, out.z), nbq<K>(U.w, out.w));
+    }
+    return;
+  }
   const float4 U = ld4(uo), Sv = ld4(S + (long long)colour * H + r0);
   float4 E = make_float4(0.f, 0.f, 0.f, 0.f);
   if constexpr (!FR) E = ld4(eo);
