@@ -616,8 +616,7 @@ int solve_adjoint(const mgglam_params* prm, double a, const double* field, const
   const int bt = N >= 256 ? 256 : (N <= 32 ? 32 : ((N + 31) / 32) * 32);
   // the fine residual in float-float on meshes its 8 x 32 tiles divide, else FP64
   const bool ffr = N % 32 == 0;
-  int chunk = N >= 64 ? 64 : N;
-  while ((long long)(N / 32) * (N / 8) * ((N + chunk - 1) / chunk) > kMaxReduceBlocks) chunk *= 2;
+  const int chunk = ffr ? march_chunk(N, (long long)(N / 32) * (N / 8), (const void*)k_adj_residual_ff<8, 32>, 256) : N;
   const dim3 gff((N / 32) * (N / 8), (N + chunk - 1) / chunk);
   const ff kappa_ff = {(float)kappa, (float)(kappa - (double)(float)kappa)};
   if (ffr) {

@@ -68,17 +68,44 @@ __device__ __forceinline__ ff ff_sqr(ff x) {
   return fast_two_sum(p.hi, __fmaf_rn(__fadd_rn(x.hi, x.hi), x.lo, p.lo));
 }
 
-// 1/x: the single-precision reciprocal refined by one Newton step carried in
-// float-float (the residual 1 - x r is formed exactly to first order).
-__device__ __forceinline__ ff ff_rcp(ff x) {
+__device__ __forceinline__ float ff_to_float(ff x) { return __fadd_rn(x.hi, x.lo); }
+
+// x / y: the quotient's leading float q1 from the approximate reciprocal, then
+// one correction q2 = (x - q1 y) / y with the remainder formed exactly to first
+// order (q1 y.hi by two-product; x.hi - (q1 y.hi).hi is exact since the two
+// agree to a few ulp).  Unnormalised: |q2| <= ~2^-22 |q1|.
+__device__ __forceinline__ ff ff_div(ff x, ff y) {
   float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x.hi));  // within 1 ulp; the step squares its error
-  const ff xr = ff_mul_f(x, r);               // ~ 1
-  const ff t = ff_sub(ff{1.f, 0.f}, xr);      // 1 - x r, tiny
-  return fast_two_sum(r, __fmul_rn(r, t.hi));  // r + r (1 - x r)
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y.hi));
+  const float q1 = __fmul_rn(x.hi, r);
+  const ff p = two_prod(q1, y.hi);
+  const float rem = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(x.hi, p.hi), p.lo), x.lo), __fmul_rn(q1, y.lo));
+  return ff{q1, __fmul_rn(rem, r)};
 }
 
-__device__ __forceinline__ float ff_to_float(ff x) { return __fadd_rn(x.hi, x.lo); }
+// Unnormalised float-float accumulator: the value is s + e, where s is the
+// running float sum of the leading parts and e collects, in single precision,
+// the exact rounding errors of those sums together with the low parts.  One
+// two-sum per term and no renormalisation: after m terms the error is at most
+// ~m^2 2^-48 of the largest partial sum.
+struct ffacc {
+  float s, e;
+};
+
+__device__ __forceinline__ ffacc acc_of(ff x) { return ffacc{x.hi, x.lo}; }
+
+// a += hi + lo
+__device__ __forceinline__ void acc_add(ffacc& a, float hi, float lo) {
+  const ff t = two_sum(a.s, hi);
+  a.s = t.hi;
+  a.e = __fadd_rn(a.e, __fadd_rn(t.lo, lo));
+}
+
+__device__ __forceinline__ void acc_add(ffacc& a, ff x) { acc_add(a, x.hi, x.lo); }
+
+__device__ __forceinline__ ff acc_ff(const ffacc& a) { return two_sum(a.s, a.e); }
+
+__device__ __forceinline__ float acc_float(const ffacc& a) { return __fadd_rn(a.s, a.e); }
 
 // Exact split of a double into hi + lo by integer operations on its bits (no
 // double-precision instruction): hi keeps the leading 24 bits of the

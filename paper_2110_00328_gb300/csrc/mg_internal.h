@@ -78,6 +78,10 @@ enum Scalar { SC_MEAN = 0, SC_SUMSQ = 1, SC_SRC = 2, SC_FLAG = 3, SC_FFC = 8, SC
 
 int count_levels(int N, int levels);
 
+// Planes per CTA of a z-marching kernel 'kern' (threads per CTA) over 'tiles'
+// (j,k) tiles of a level of side n, sized to whole waves of resident CTAs.
+int march_chunk(int n, long long tiles, const void* kern, int threads);
+
 // Normaliser of the relative residual: the RMS of the model's linear source
 // term (coefficient x RMS(delta)), or 1 where the density is uniform.  A
 // source below 1e-12 of its coefficient counts as uniform: that is rounding in

@@ -15,6 +15,35 @@ namespace mg {
 // c / H0 in Mpc/h: the speed of light over 100 km/s/Mpc.
 static const double kCOverH0 = 299792.458 / 100.0;
 
+// Planes per CTA of a z-marching kernel over 'tiles' (j,k) tiles of a level of
+// side n.  Each CTA marches its whole chunk, so a last wave holding a few CTAs
+// costs as much as a full one: the chunk minimises waves x (chunk + 4: the two
+// prologue planes and about as much again for the CTA's start and reduction),
+// with the resident CTAs per SM from the occupancy calculator, at least 8
+// planes (halo re-reads <= 25%), and the CTA count within the partial-sum array.
+int march_chunk(int n, long long tiles, const void* kern, int threads) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const long long R = (long long)(sms > 0 ? sms : 1) * per_sm;
+  int best = n;
+  long long best_cost = -1;
+  for (int c = n < 8 ? n : 8; c <= n; ++c) {
+    const long long ctas = tiles * ((n + c - 1) / c);
+    if (ctas > kMaxReduceBlocks) continue;
+    const long long cost = ((ctas + R - 1) / R) * (c + 4);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = c;
+    }
+  }
+  return best;
+}
+
 double source_norm(const ModelDev& m, double src_rms) {
   double coef;
   if (is_fr(m.kind)) coef = m.om_a;

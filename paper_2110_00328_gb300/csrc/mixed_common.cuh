@@ -508,23 +508,36 @@ __device__ __forceinline__ double outer_residual_tile_ff(const FFC& C, int n, in
     const float r = rho[g];
     const ff uc = ff{s_uh[sl][cc], s_ul[sl][cc]};
     const ff wc = W(sl, cc);
-    ff L = ff_add(W(sm, cc), W(sp, cc));
-    L = ff_add(L, ff_add(W(sl, cc - PK), W(sl, cc + PK)));
-    L = ff_add(L, ff_add(W(sl, cc - 1), W(sl, cc + 1)));
-    L = ff_sub(L, ff_mul_f(wc, 6.f));  // sum of the six neighbours - 6 w
-    ff v;
+    // sum of the six neighbours - 6 w, accumulated unnormalised
+    ffacc La = acc_of(W(sm, cc));
+    acc_add(La, W(sp, cc));
+    acc_add(La, W(sl, cc - PK));
+    acc_add(La, W(sl, cc + PK));
+    acc_add(La, W(sl, cc - 1));
+    acc_add(La, W(sl, cc + 1));
+    {
+      const ff w6 = two_prod(wc.hi, -6.f);
+      acc_add(La, w6.hi, __fmaf_rn(wc.lo, -6.f, w6.lo));
+    }
+    const ff L = acc_ff(La);
+    float tv;
     if constexpr (is_fr(K)) {
-      // c1 rho + c0 - c2 (L - 6w) - K/u
-      v = ff_add(ff_mul_f(C.c1, r), C.c0);
-      v = ff_sub(v, ff_mul(C.c2, L));
-      v = ff_sub(v, ff_mul(C.K, ff_rcp(uc)));
+      // c1 rho + c0 - c2 (L - 6w) - K/u, each product kept as an exact leading
+      // product plus its first-order low part
+      ffacc v = acc_of(C.c0);
+      const ff p1 = two_prod(C.c1.hi, r);
+      acc_add(v, p1.hi, __fmaf_rn(C.c1.lo, r, p1.lo));
+      const ff p2 = two_prod(C.c2.hi, L.hi);
+      acc_add(v, -p2.hi, -__fmaf_rn(C.c2.hi, L.lo, __fmaf_rn(C.c2.lo, L.hi, p2.lo)));
+      const ff q = ff_div(C.K, uc);
+      acc_add(v, -q.hi, -q.lo);
+      tv = -acc_float(v);
     } else {
       // c2 (L - 6u) - msym ((rho/mean rat3 - 1) u + u^3)
       const ff a = ff_sub(ff_mul(ff_mul_f(C.c1, r), C.rat3), ff{1.f, 0.f});
       const ff b = ff_add(ff_mul(a, uc), ff_mul(ff_sqr(uc), uc));
-      v = ff_sub(ff_mul(C.c2, L), ff_mul(C.msym, b));
+      tv = -ff_to_float(ff_sub(ff_mul(C.c2, L), ff_mul(C.msym, b)));
     }
-    const float tv = -ff_to_float(v);
     const long long o = SPLIT ? split_idx(n, i, jg, kg) : (long long)g;  // the level's layout
     ub[o] = ff_to_float(uc);
     tau[o] = tv;

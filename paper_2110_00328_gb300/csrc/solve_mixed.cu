@@ -589,8 +589,9 @@ static int launch_outer_residual_ff(const MixedCtx& C, double* field, int* block
   Level& F = ws->lev[0];
   const FFC* ffc = ffc_of(ws);
   if (F.n % kRTK == 0 && F.n % kRTJ == 0) {
-    int chunk = F.n >= 64 ? 64 : F.n;
-    while ((long long)(F.n / kRTK) * (F.n / kRTJ) * ((F.n + chunk - 1) / chunk) > kMaxReduceBlocks) chunk *= 2;
+    const long long tiles = (long long)(F.n / kRTK) * (F.n / kRTJ);
+    const int chunk = C.split ? march_chunk(F.n, tiles, (const void*)k_outer_residual_ff<K, kRTJ, kRTK, true>, kRTJ * kRTK)
+                              : march_chunk(F.n, tiles, (const void*)k_outer_residual_ff<K, kRTJ, kRTK>, kRTJ * kRTK);
     dim3 grid((F.n / kRTK) * (F.n / kRTJ), (F.n + chunk - 1) / chunk);
     *blocks = grid.x * grid.y;
     if (*blocks > kMaxReduceBlocks) return MGGLAM_ERR_SHAPE;
@@ -623,8 +624,8 @@ static int launch_outer_residual_t(const MixedCtx& C, double* field, int* blocks
     if (C.ff_resid) return launch_outer_residual_ff<K>(C, field, blocks, st);
   }
   if (F.n % kRTK == 0 && F.n % kRTJ == 0) {
-    int chunk = F.n >= 64 ? 64 : F.n;
-    while ((long long)(F.n / kRTK) * (F.n / kRTJ) * ((F.n + chunk - 1) / chunk) > kMaxReduceBlocks) chunk *= 2;
+    const int chunk = march_chunk(F.n, (long long)(F.n / kRTK) * (F.n / kRTJ),
+                                  (const void*)k_outer_residual<K, kRTJ, kRTK>, kRTJ * kRTK);
     dim3 grid((F.n / kRTK) * (F.n / kRTJ), (F.n + chunk - 1) / chunk);
     *blocks = grid.x * grid.y;
     if (*blocks > kMaxReduceBlocks) return MGGLAM_ERR_SHAPE;
