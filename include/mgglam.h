@@ -354,6 +354,62 @@ int mgglam_cq_background(double alpha, double beta, double omega_m, double h, do
  * (photons at 2.7255 K, 3.046 massless neutrinos; Sec. 3.2.3). */
 double mgglam_radiation_density(double h);
 
+/* ---- Particle-mesh time step (Sec. 3.1 and the particle equations of
+ * Secs. 3.2.3-3.2.5) ------------------------------------------------------ */
+
+/*
+ * Periodic Poisson equation by FFT, the PM gravity solver of Sec. 3.1 (Eq.
+ * GR_poisson_codeunit with the discrete Green's function of the 7-point
+ * Laplacian): phi solves grad_h^2 phi = coef (rho/mean(rho) - 1) on the N^3
+ * mesh (h = 1), with mean(phi) = 0.  Single-precision FFTs of power-of-two
+ * length, twiddles from double precision: phi carries ~1e-6 relative error.
+ *   rho  device, N^3 float32 density (row-major [x][y][z]); any positive mean.
+ *   N    power of two, 8 <= N <= 1024.
+ *   coef for the Newtonian potential (3/2) Om / a.
+ *   phi  device, N^3 float32 output (may not alias rho).
+ * The library keeps an N^3 complex work array per (device, N), freed by
+ * mgglam_release.  Errors: MGGLAM_ERR_ARG, MGGLAM_ERR_SHAPE, MGGLAM_ERR_OOM,
+ * MGGLAM_ERR_CUDA.
+ */
+int mgglam_poisson_fft(const float* rho, int N, double coef, float* phi, void* stream);
+
+/* Scalars of one PM step from a to a + da. */
+typedef struct {
+  double a;           /* scale factor of the positions (the force time a_n) */
+  double da;          /* step in a (> 0) */
+  double E_a;         /* H(a)/H0 */
+  double E_half;      /* H(a + da/2)/H0 */
+  double dphibar_da;  /* CQ: d phibar / da at a (the momentum drag); unused otherwise */
+  int scalar;         /* 1: the model's scalar field and fifth force; 0: LCDM (Newtonian only) */
+} mgglam_pm_step_desc;
+
+/*
+ * One leapfrog step of the PM N-body code, positions at a, momenta at
+ * a - da/2 (code units of Eq. code_units: x in cells, p~):
+ *   rho = CIC deposit of pos; grad^2 Phi_N = (3/2) Om/a delta (FFT);
+ *   scalar: the model's field solved at a from 'field' (the previous step's
+ *           solution, or NaN in its first element for the background), as
+ *           mgglam_solve_scalar;
+ *   p += da (H0/adot) grad Psi - gamma p da (drag at the midpoint),
+ *     Psi = -sN Phi_N + (the fifth-force potential of mgglam_gather_force),
+ *     sN = e^{beta phibar} for CQ (Sec. 3.2.3), else 1; H0/adot = 1/(a E_a);
+ *     gamma = beta dphibar/da (CQ, Eq. csf_particle_geodesic_code2),
+ *     9 Om beta*^2 xi^2 sqrt(1 - (a_star/a)^3) a^-4 u(x) (symmetron, a > a_star,
+ *     Eq. F_x_codeunit), 0 otherwise;
+ *   pos += da p / ((a + da/2)^3 E_half), wrapped into [0, N).
+ *   pos, mom  device, [np][3] float32, updated in place.
+ *   field     device, N^3 float64 (desc->scalar), in/out; else may be NULL.
+ *   rho_work, psi_work  device, N^3 float32 scratch each (rho_work holds the
+ *             density on return, psi_work the total potential Psi).
+ *   N         power of two, 8 <= N <= 1024.
+ * Returns the scalar solve's status (MGGLAM_ERR_NOT_CONVERGED still moves the
+ * particles with the last iterate), or an argument/CUDA/allocation error
+ * before anything moves.
+ */
+int mgglam_pm_step(const mgglam_params* prm, const mgglam_pm_step_desc* desc, int N, float* pos, float* mom,
+                   long long np, double* field, double tol, float* rho_work, float* psi_work, mgglam_stats* stats,
+                   void* stream);
+
 /* ---- tracing (not part of the paper's method: measurement support) ---- */
 
 /* Accumulated CUDA-event timing of one class of kernel launches. */

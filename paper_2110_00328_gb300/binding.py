@@ -103,7 +103,7 @@ EXPORTS = ["mgglam_version", "mgglam_status_string", "mgglam_default_params", "m
            "mgglam_restrict", "mgglam_prolong_correct", "mgglam_release", "mgglam_profile_start",
            "mgglam_profile_stop", "mgglam_launch_count", "mgglam_deposit_cic_static",
            "mgglam_solve_adjoint", "mgglam_solve_batch", "mgglam_cq_background", "mgglam_radiation_density",
-           "mgglam_deposit_cic_host", "mgglam_gather_force_host"]
+           "mgglam_deposit_cic_host", "mgglam_gather_force_host", "mgglam_poisson_fft", "mgglam_pm_step"]
 
 
 class CKernelProfile(ctypes.Structure):
@@ -370,6 +370,60 @@ def radiation_density(h: float = 0.6774) -> float:
     lib = load()
     lib.mgglam_radiation_density.restype = ctypes.c_double
     return lib.mgglam_radiation_density(ctypes.c_double(h))
+
+
+def poisson_fft(rho, coef: float, phi=None, stream=None):
+    """phi with grad_h^2 phi = coef (rho/mean - 1), mean(phi) = 0 (mgglam_poisson_fft)."""
+    import torch
+    N = rho.shape[0]
+    if phi is None:
+        phi = torch.empty_like(rho)
+    lib = load()
+    lib.mgglam_poisson_fft.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                       ctypes.c_void_p]
+    _check("mgglam_poisson_fft", lib.mgglam_poisson_fft(_ptr(rho, torch.float32), N, coef,
+                                                        _ptr(phi, torch.float32), _stream(stream)))
+    return phi
+
+
+class CPmStepDesc(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("da", ctypes.c_double), ("E_a", ctypes.c_double),
+                ("E_half", ctypes.c_double), ("dphibar_da", ctypes.c_double), ("scalar", ctypes.c_int)]
+
+
+def lcdm_E(a: float, omega_m: float = 0.3, omega_l: float = 0.7) -> float:
+    """H(a)/H0 of the flat LCDM background (matter and Lambda)."""
+    return (omega_m / a ** 3 + omega_l) ** 0.5
+
+
+def pm_step(prm: Params, a: float, da: float, pos, mom, rho_work, psi_work, field=None, tol: float = 1e-8,
+            E_a: float | None = None, E_half: float | None = None, dphibar_da: float = 0.0, stream=None,
+            allow_unconverged=False) -> Stats | None:
+    """One PM leapfrog step in place on pos/mom (mgglam_pm_step); field=None is a
+    LCDM step.  E_a, E_half default to the LCDM H/H0 of prm's Om, OL."""
+    import torch
+    N = rho_work.shape[0]
+    if E_a is None:
+        E_a = lcdm_E(a, prm.omega_m, prm.omega_l)
+    if E_half is None:
+        E_half = lcdm_E(a + 0.5 * da, prm.omega_m, prm.omega_l)
+    d = CPmStepDesc(a, da, E_a, E_half, dphibar_da, 1 if field is not None else 0)
+    st = CStats()
+    lib = load()
+    lib.mgglam_pm_step.argtypes = [ctypes.POINTER(CParams), ctypes.POINTER(CPmStepDesc), ctypes.c_int,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
+                                   ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(CStats),
+                                   ctypes.c_void_p]
+    rc = lib.mgglam_pm_step(ctypes.byref(prm.c()), ctypes.byref(d), N, _ptr(pos, torch.float32),
+                            _ptr(mom, torch.float32), pos.shape[0],
+                            _ptr(field, torch.float64) if field is not None else None, tol,
+                            _ptr(rho_work, torch.float32), _ptr(psi_work, torch.float32), ctypes.byref(st),
+                            _stream(stream))
+    _check("mgglam_pm_step", rc, (0, -4) if allow_unconverged else (0,))
+    if field is None:
+        return None
+    nh = min(64, (st.outer if prm.precision == MIXED else st.cycles) + 1)
+    return Stats(st.cycles, st.outer, bool(st.converged), st.resid0, st.resid, st.seconds, list(st.resid_hist[:nh]))
 
 
 def solve_batch(prms, a_list, rhos, fields, tol: float, stream=None, allow_unconverged=False):

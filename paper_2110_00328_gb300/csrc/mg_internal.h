@@ -123,7 +123,8 @@ int launch_init_background(const ModelDev& m, double* field, size_t n3, cudaStre
 enum ProfClass {
   PC_SMOOTH32_FINE = 0, PC_RESTRICT32_FINE, PC_PROLONG32_FINE, PC_OUTER_RESID, PC_APPLY_CORR,
   PC_SMOOTH64_FINE, PC_RESTRICT64_FINE, PC_PROLONG64_FINE, PC_RESID64_FINE, PC_COARSE_LEVELS,
-  PC_DEPOSIT, PC_DEPOSIT_FINISH, PC_TRANSFORM, PC_GATHER, PC_COUNT
+  PC_DEPOSIT, PC_DEPOSIT_FINISH, PC_TRANSFORM, PC_GATHER, PC_POISSON_FFT, PC_PM_POTENTIAL, PC_PM_KICK_DRIFT,
+  PC_COUNT
 };
 void note_launch(int n);
 long long launch_count();
@@ -135,6 +136,12 @@ int solve_fp64(const mgglam_params* prm, double a, const float* rho, int N, doub
                double tol, mgglam_stats* stats, cudaStream_t st);
 int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, double* field,
                 double tol, mgglam_stats* stats, cudaStream_t st);
+
+// ---- PM step (fft.cu, pm.cu) ----
+int poisson_fft(const float* rho, int N, double coef, float* phi, cudaStream_t st);
+void release_fft_plans();
+int pm_step(const mgglam_params* prm, const mgglam_pm_step_desc* d, int N, float* pos, float* mom, long long np,
+            double* field, double tol, float* rho_work, float* psi_work, mgglam_stats* stats, cudaStream_t st);
 
 // ---- adjoint (adjoint.cu), batch (batch.cu) ----
 void release_adjoint_work();

@@ -392,9 +392,28 @@ int mgglam_prolong_correct(const mgglam_params* prm, int n, const double* uH, co
   return launch_prolong_correct64(m, n / 2, uH, RuH, u_fine, (cudaStream_t)stream);
 }
 
+int mgglam_poisson_fft(const float* rho, int N, double coef, float* phi, void* stream) {
+  if (!rho || !phi || rho == phi || !(coef == coef)) return MGGLAM_ERR_ARG;
+  return poisson_fft(rho, N, coef, phi, (cudaStream_t)stream);
+}
+
+int mgglam_pm_step(const mgglam_params* prm, const mgglam_pm_step_desc* d, int N, float* pos, float* mom,
+                   long long np, double* field, double tol, float* rho_work, float* psi_work, mgglam_stats* stats,
+                   void* stream) {
+  int rc = check_params(prm);
+  if (rc) return rc;
+  if (!d || !pos || !mom || np < 1 || !rho_work || !psi_work || rho_work == psi_work) return MGGLAM_ERR_ARG;
+  if (d->scalar && (!field || !(tol >= 0.0))) return MGGLAM_ERR_ARG;
+  if (!(d->a > 0.0) || !(d->da > 0.0) || !(d->E_a > 0.0) || !(d->E_half > 0.0) || !(d->dphibar_da == d->dphibar_da))
+    return MGGLAM_ERR_ARG;
+  if (N < 8 || N > 1024 || (N & (N - 1))) return MGGLAM_ERR_SHAPE;
+  return pm_step(prm, d, N, pos, mom, np, field, tol, rho_work, psi_work, stats, (cudaStream_t)stream);
+}
+
 int mgglam_release(void) {
   cudaError_t e = cudaDeviceSynchronize();
   release_workspaces();
+  release_fft_plans();
   release_adjoint_work();
   release_batches();
   return e == cudaSuccess ? MGGLAM_OK : MGGLAM_ERR_CUDA;

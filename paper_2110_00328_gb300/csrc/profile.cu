@@ -15,7 +15,8 @@ static const char* kProfNames[PC_COUNT] = {
     "smooth32_fine",     "residual_restrict32_fine", "prolong_correct32_fine", "outer_residual64",
     "apply_correction64", "smooth64_fine",           "residual_restrict64_fine", "prolong_correct64_fine",
     "residual64_fine",   "coarse_levels",            "deposit_cic",            "deposit_finish",
-    "field_transform",   "gather_force"};
+    "field_transform",   "gather_force",             "poisson_fft",            "pm_potential",
+    "pm_kick_drift"};
 
 static std::atomic<long long> g_launches{0};
 static std::mutex g_pmu;
