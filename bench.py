@@ -330,6 +330,66 @@ def run_models_extra(mg, torch, dev, tol=TOL) -> dict:
     return out
 
 
+def run_pm_extra(mg, torch, dev) -> dict:
+    """One particle-mesh time step at 256^3 (the headline workload's 256^3 Zel'dovich
+    particles and mesh, box 256 Mpc/h, a = 0.9, da = 0.01, momenta from rest):
+    LCDM (deposit, FFT Poisson, gather-kick-drift) against f(R) n=1, |fR0| = 1e-6
+    (the same plus the mixed scalar solve to 1e-8, warm-started from the previous
+    step's field as in a simulation, or from the background), and the FFT Poisson
+    solve alone (algorithmic 72 B/cell: density in, five complex passes, potential out).
+    The paper reports an MG-GLAM run at 3-5x the time of the LCDM GLAM run (Sec. 1)."""
+    from paper_2110_00328_gb300 import inputs
+    N = N_MESH
+    pos0 = torch.from_numpy(inputs.zeldovich_positions(N, seed=1, sigma=SIGMA)).to(dev)
+    rho_w = torch.empty((N,) * 3, dtype=torch.float32, device=dev)
+    psi_w = torch.empty_like(rho_w)
+    prm = mg.Params(model=0, n=1, fR0_abs=FR0, box=BOX, precision=mg.MIXED, max_cycles=80, nu2=1, coarse_sweeps=4)
+    a0, da, steps = 0.9, 0.01, 6
+
+    def run(scalar: bool, warm: bool):
+        pos, mom = pos0.clone(), torch.zeros_like(pos0)
+        field = torch.full((N,) * 3, float("nan"), dtype=torch.float64, device=dev) if scalar else None
+        times, cycles = [], []
+        for s in range(steps):
+            if scalar and not warm:
+                field.fill_(float("nan"))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = mg.pm_step(prm, a0 + s * da, da, pos, mom, rho_w, psi_w, field=field, tol=TOL)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            if st is not None:
+                cycles.append(st.cycles)
+        return times, cycles
+
+    t_l, _ = run(False, True)
+    t_w, c_w = run(True, True)
+    t_c, c_c = run(True, False)
+    ms = lambda t: round(float(np.median(t[1:])), 3)
+    fft = []
+    for _ in range(8):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mg.poisson_fft(rho_w, 1.5 * 0.3 / a0, psi_w)
+        e1.record()
+        torch.cuda.synchronize()
+        fft.append(e0.elapsed_time(e1))
+    fft_ms = float(np.median(fft[2:]))
+    peak, _ = measured_peaks()
+    gbs = 72.0 * N ** 3 / (fft_ms * 1e-3) / 1e9
+    return {"workload": "256^3 mesh, 256^3 Zel'dovich particles (pixel sigma 1.5, seed 1), box 256, a = 0.9, "
+                        "da = 0.01, 6 steps (median of steps 2-6)",
+            "lcdm_step_ms": ms(t_l), "fr_step_warm_ms": ms(t_w), "fr_cycles_warm": c_w,
+            "fr_step_cold_ms": ms(t_c), "fr_cycles_cold": c_c,
+            "mg_over_lcdm_warm": round(ms(t_w) / ms(t_l), 2), "mg_over_lcdm_cold": round(ms(t_c) / ms(t_l), 2),
+            "paper_mg_over_lcdm": "3-5 (whole runs, Sec. 1)",
+            "poisson_fft_ms": round(fft_ms, 4), "poisson_fft_GBps": round(gbs, 1),
+            "poisson_fft_frac_hbm": round(gbs / peak, 4)}
+
+
 def run_adjoint_extra(mg, torch, dev) -> dict:
     """Gradient of sum_b log P_F(k_b) (fifth-force power, 32 log bins) w.r.t. the
     density and ln|fR0| at 512^3 (f(R) n=1, |fR0| = 1e-5, box 512 Mpc/h, lognormal
@@ -570,7 +630,7 @@ def run_ours(args) -> None:
                                     "d2h_bytes_per_step": int(force_host.numel() * 4)}},
         "clocks": clk,
     }
-    extras = {"all": ("batch", "adjoint", "models"), "none": ()}.get(args.extras, (args.extras,))
+    extras = {"all": ("batch", "adjoint", "models", "pm"), "none": ()}.get(args.extras, (args.extras,))
     if args.no_extras:
         extras = ()
     if "batch" in extras:
@@ -579,6 +639,8 @@ def run_ours(args) -> None:
         line["adjoint"] = run_adjoint_extra(mg, torch, dev)
     if "models" in extras:
         line["models"] = run_models_extra(mg, torch, dev)
+    if "pm" in extras:
+        line["pm"] = run_pm_extra(mg, torch, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = run_oracle_baseline(pos_h)
     print(json.dumps(line), flush=True)
@@ -603,7 +665,7 @@ def main():
     ap.add_argument("--tail-cells", type=int, default=0, help="largest level run by the one-block tail (0 = default)")
     ap.add_argument("--cycle", choices=["V", "F", "W"], default="V", help="multigrid cycle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", choices=["all", "none", "batch", "adjoint", "models"], default="all",
+    ap.add_argument("--extras", choices=["all", "none", "batch", "adjoint", "models", "pm"], default="all",
                     help="extra measurements after the main step: the 48-solve batch, the 512^3 adjoint, "
                          "the symmetron and CQ solves at 256^3")
     ap.add_argument("--no-extras", action="store_true", help="same as --extras none")

@@ -6,9 +6,13 @@
 //   K_h^2 = sum_d 4 sin^2(pi k_d / N)   (the 7-point Laplacian's eigenvalues),
 //   Phi_0 = 0 (the mean of Phi is not fixed by the equation).
 //
-// Single-precision complex FFTs of power-of-two length, radix-2 Stockham
-// (self-sorting) stages in shared memory; twiddles formed in double on the host.
-// Five passes over the mesh, each one read and one write:
+// Single-precision complex FFTs of power-of-two length N = R1 R2 (R1, R2 <= 32)
+// by one Cooley-Tukey split: with n = R2 n1 + n2 and k = k1 + R1 k2,
+//   X[k1 + R1 k2] = sum_n2 W_R2^{n2 k2} [ W_N^{n2 k1} sum_n1 x[R2 n1 + n2] W_R1^{n1 k1} ],
+// so a thread computes an R1-point DFT in registers, applies the twiddle
+// W_N^{n2 k1} (table formed in double on the host), exchanges through shared
+// memory once, and computes an R2-point DFT in registers.  Five passes over the
+// mesh, each one read and one write:
 //   z forward (real density in) -> y forward -> x forward, times the Green's
 //   function, x inverse (one kernel) -> y inverse -> z inverse (real Phi out).
 // z is the contiguous axis: a CTA transforms whole rows.  For y and x a CTA
@@ -24,113 +28,193 @@
 namespace mg {
 
 constexpr int kFftThreads = 256;
-constexpr int kFftRowElems = 2048;   // complex values per buffer, contiguous-axis kernel (2 x 16 KB)
-constexpr int kFftTileElems = 4096;  // complex values per buffer, strided-axis kernel (2 x 32 KB)
+
+// exp(-2 pi i m / 32), m = 0..15: the twiddles of the register DFTs (R <= 32)
+__constant__ float2 c_w32[16] = {
+    {1.0f, 0.0f}, {0.980785251f, -0.195090324f}, {0.923879504f, -0.382683426f}, {0.831469595f, -0.555570245f},
+    {0.707106769f, -0.707106769f}, {0.555570245f, -0.831469595f}, {0.382683426f, -0.923879504f},
+    {0.195090324f, -0.980785251f}, {0.0f, -1.0f}, {-0.195090324f, -0.980785251f}, {-0.382683426f, -0.923879504f},
+    {-0.555570245f, -0.831469595f}, {-0.707106769f, -0.707106769f}, {-0.831469595f, -0.555570245f},
+    {-0.923879504f, -0.382683426f}, {-0.980785251f, -0.195090324f}};
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// log2(N) radix-2 Stockham stages on L lines of length N in shared memory,
-// ping-ponging between a and b; returns the buffer holding the transform
-// (natural order).  LINE_MAJOR: element m of line l at l N + m, else at m L + l
-// (threads are mapped so that consecutive threads touch consecutive words).
-// Stage with span Ns: for j < N/2, k = j mod Ns,
-//   x0 = in[j], x1 = in[j + N/2] w^k  (w = exp(-+2 pi i / (2 Ns)))
-//   out[2(j - k) + k] = x0 + x1,  out[2(j - k) + k + Ns] = x0 - x1.
-template <bool INV, bool LINE_MAJOR>
-__device__ __forceinline__ float2* stockham(float2* a, float2* b, int N, int L, const float2* __restrict__ tw) {
-  const int half = N >> 1;
-  for (int Ns = 1; Ns < N; Ns <<= 1) {
-    const int step = N / (2 * Ns);
-    for (int t = threadIdx.x; t < L * half; t += blockDim.x) {
-      const int l = LINE_MAJOR ? t / half : t % L;
-      const int j = LINE_MAJOR ? t - l * half : t / L;
-      const int k = j & (Ns - 1);
-      float2 w = __ldg(&tw[k * step]);
-      if (INV) w.y = -w.y;
-      const int o = ((j - k) << 1) + k;
-      const float2 x0 = LINE_MAJOR ? a[l * N + j] : a[j * L + l];
-      const float2 x1 = cmul(LINE_MAJOR ? a[l * N + j + half] : a[(j + half) * L + l], w);
-      const float2 s = make_float2(x0.x + x1.x, x0.y + x1.y), d = make_float2(x0.x - x1.x, x0.y - x1.y);
-      if (LINE_MAJOR) {
-        b[l * N + o] = s;
-        b[l * N + o + Ns] = d;
-      } else {
-        b[o * L + l] = s;
-        b[(o + Ns) * L + l] = d;
+__host__ __device__ constexpr int bitrev(int k, int R) {
+  int r = 0;
+  for (int b = 1; b < R; b <<= 1) {
+    r = (r << 1) | (k & 1);
+    k >>= 1;
+  }
+  return r;
+}
+
+// R-point DFT in registers (R a power of two <= 32): radix-2 decimation in
+// frequency, natural input, bit-reversed output (X[k] in v[bitrev(k, R)]).
+template <int R, bool INV>
+__device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
+#pragma unroll
+  for (int span = R / 2; span >= 1; span >>= 1) {
+#pragma unroll
+    for (int s = 0; s < R; s += 2 * span) {
+#pragma unroll
+      for (int j = 0; j < span; ++j) {
+        const float2 a = v[s + j], b = v[s + j + span];
+        v[s + j] = make_float2(a.x + b.x, a.y + b.y);
+        float2 d = make_float2(a.x - b.x, a.y - b.y);
+        if (j != 0) {  // W_{2 span}^j = W_32^{j 32 / (2 span)}
+          float2 w = c_w32[j * (32 / (2 * span))];
+          if (INV) w.y = -w.y;
+          d = cmul(d, w);
+        }
+        v[s + j + span] = d;
       }
     }
-    __syncthreads();
-    float2* tmp = a;
-    a = b;
-    b = tmp;
   }
-  return a;
 }
 
-// Contiguous axis (z), L whole rows per CTA.  MODE 1: forward, the real density
-// in (times N^3 / sum rho, i.e. rho / mean); MODE 2: inverse, the real part out
-// times 'scale'; MODE 0: complex in and out.
-template <bool INV, int MODE>
-__global__ void __launch_bounds__(kFftThreads) k_fft_rows(const float* __restrict__ rin, float2* __restrict__ data,
-                                                          float* __restrict__ rout, int N, int L, float scale,
-                                                          const double* __restrict__ rho_sum, long long n3,
-                                                          const float2* __restrict__ tw) {
+template <int R1, int R2>
+__host__ __device__ constexpr int fft_threads_per_line() {
+  return R1 > R2 ? R1 : R2;
+}
+
+// Resident CTAs per SM the register allocation is bounded for: four (64
+// registers a thread) while a thread's DFT holds at most 16 complex values,
+// two for the 32-point factors, whose 64 values would otherwise spill.
+template <int R1, int R2>
+__host__ __device__ constexpr int fft_min_ctas() {
+  return (R1 > 16 || R2 > 16) ? 2 : 4;
+}
+
+// Phase 1 of a transform of length N = R1 R2 for the thread owning n2 (< R2):
+// v holds x[R2 n1 + n2], n1 = 0..R1-1 (natural order); writes the twiddled
+// R1-point DFT, W_N^{n2 k1} X1[k1], to ex(k1).
+template <int R1, int R2, bool INV, class EX>
+__device__ __forceinline__ void fft_phase1(float2 (&v)[R1], int n2, const float2* __restrict__ twN, EX ex) {
+  dft_reg<R1, INV>(v);
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    float2 w = __ldg(&twN[n2 * k1]);
+    if (INV) w.y = -w.y;
+    ex(k1) = cmul(v[bitrev(k1, R1)], w);
+  }
+}
+
+// Phase 3 for the thread owning k1 (< R1): u holds the twiddled values of all
+// n2 (< R2); on return u[k2] = X[k1 + R1 k2] in natural order of k2.
+template <int R2, bool INV>
+__device__ __forceinline__ void fft_phase3(float2 (&u)[R2]) {
+  dft_reg<R2, INV>(u);
+  float2 t[R2];
+#pragma unroll
+  for (int k2 = 0; k2 < R2; ++k2) t[k2] = u[bitrev(k2, R2)];
+#pragma unroll
+  for (int k2 = 0; k2 < R2; ++k2) u[k2] = t[k2];
+}
+
+// Contiguous axis (z), L whole rows per CTA, T = max(R1, R2) threads per row:
+// thread (l, r) loads x[R2 n1 + r] of its row straight into registers (runs of
+// R2 consecutive values across the threads), exchanges once through shared
+// memory (Y[n2][k1] at l R1 (R2+1) + k1 (R2+1) + n2: the padding keeps a
+// half-warp's column reads on distinct banks) and stores X[r + R1 k2].
+// MODE 1: forward, the real density in (times N^3 / sum rho, i.e. rho / mean);
+// MODE 2: inverse, the real part out times 'scale'; MODE 0: complex in and out.
+template <int R1, int R2, bool INV, int MODE>
+__global__ void __launch_bounds__(kFftThreads, fft_min_ctas<R1, R2>()) k_fft_rows(const float* __restrict__ rin, float2* __restrict__ data,
+                                                             float* __restrict__ rout, int L, float scale,
+                                                             const double* __restrict__ rho_sum, long long n3,
+                                                             const float2* __restrict__ twN) {
+  constexpr int N = R1 * R2;
+  constexpr int T = fft_threads_per_line<R1, R2>();
   extern __shared__ float2 fft_sm[];
-  float2* A = fft_sm;
-  float2* B = fft_sm + L * N;
-  const long long base = (long long)blockIdx.x * L * N;
+  const int l = threadIdx.x / T, r = threadIdx.x - l * T;
+  const long long lb = ((long long)blockIdx.x * L + l) * N;
+  float2* Y = fft_sm + l * (R1 * (R2 + 1));
   float s = scale;
   if constexpr (MODE == 1) s = (float)((double)n3 / *rho_sum);
-  for (int e = threadIdx.x; e < L * N; e += blockDim.x) {
-    if constexpr (MODE == 1) A[e] = make_float2(rin[base + e] * s, 0.f);
-    else A[e] = data[base + e];
+  if (r < R2) {
+    float2 v[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+      if constexpr (MODE == 1) v[n1] = make_float2(rin[lb + R2 * n1 + r] * s, 0.f);
+      else v[n1] = data[lb + R2 * n1 + r];
+    }
+    fft_phase1<R1, R2, INV>(v, r, twN, [&](int k1) -> float2& { return Y[k1 * (R2 + 1) + r]; });
   }
   __syncthreads();
-  const float2* r = stockham<INV, true>(A, B, N, L, tw);
-  for (int e = threadIdx.x; e < L * N; e += blockDim.x) {
-    if constexpr (MODE == 2) rout[base + e] = r[e].x * s;
-    else data[base + e] = r[e];
+  if (r < R1) {
+    float2 u[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) u[n2] = Y[r * (R2 + 1) + n2];
+    fft_phase3<R2, INV>(u);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      if constexpr (MODE == 2) rout[lb + r + R1 * k2] = u[k2].x * s;
+      else data[lb + r + R1 * k2] = u[k2];
+    }
   }
 }
 
-// Strided axis: element m of column t at base + m * stride_axis + t, with
-// base = blockIdx.y * stride_other + z0, z0 = blockIdx.x * TC.  GREEN: forward
-// transform, multiplication by -coef / K_h^2 (k_axis = m, k_other = blockIdx.y,
-// k_z = z0 + t; the x pass), inverse transform.
-template <bool INV, bool GREEN>
-__global__ void __launch_bounds__(kFftThreads) k_fft_cols(float2* __restrict__ data, int N, int TC,
-                                                          long long stride_axis, long long stride_other,
-                                                          const float2* __restrict__ tw, const float* __restrict__ s2,
-                                                          float coef) {
+// Strided axis: element m of column c at base + m * stride_axis + c with
+// base = blockIdx.y * stride_other + z0, z0 = blockIdx.x * TC; thread (c, r) =
+// (t % TC, t / TC), so a warp's global accesses are runs of TC consecutive
+// values.  Exchange buffer Y[n2][k1] at (k1 R2 + n2) TC + c.
+// GREEN (the x pass): the forward result X[k1 + R1 k2] stays in the registers
+// of thread k1, is multiplied by -coef / K_h^2 (k_x = k1 + R1 k2, k_y =
+// blockIdx.y, k_z = z0 + c) and transformed back with the two factors' roles
+// swapped (input index R1 k2 + k1: phase 1 of length R2 over k2 by the thread
+// owning k1, phase 3 of length R1), so the inverse starts from the registers;
+// its output index is j1 + R2 j2.
+template <int R1, int R2, bool INV, bool GREEN>
+__global__ void __launch_bounds__(kFftThreads, fft_min_ctas<R1, R2>()) k_fft_cols(float2* __restrict__ data, int TC, long long stride_axis,
+                                                             long long stride_other, const float2* __restrict__ twN,
+                                                             const float* __restrict__ s2, float coef) {
   extern __shared__ float2 fft_sm[];
-  float2* A = fft_sm;
-  float2* B = fft_sm + N * TC;
+  const int c = threadIdx.x % TC, r = threadIdx.x / TC;
   const int z0 = blockIdx.x * TC;
   const int o = blockIdx.y;
-  const long long base = (long long)o * stride_other + z0;
-  for (int e = threadIdx.x; e < N * TC; e += blockDim.x) {
-    const int m = e / TC, t = e - m * TC;
-    A[e] = data[base + (long long)m * stride_axis + t];
+  float2* col = data + (long long)o * stride_other + z0 + c;
+  if (r < R2) {
+    float2 v[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = col[(long long)(R2 * n1 + r) * stride_axis];
+    fft_phase1<R1, R2, INV>(v, r, twN, [&](int k1) -> float2& { return fft_sm[(k1 * R2 + r) * TC + c]; });
   }
   __syncthreads();
-  float2* r = stockham<INV, false>(A, B, N, TC, tw);
+  float2 u[R2];
+  if (r < R1) {
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) u[n2] = fft_sm[(r * R2 + n2) * TC + c];
+    fft_phase3<R2, INV>(u);
+    if constexpr (!GREEN) {
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) col[(long long)(r + R1 * k2) * stride_axis] = u[k2];
+    }
+  }
   if constexpr (GREEN) {
-    const float so = s2[o];
-    for (int e = threadIdx.x; e < N * TC; e += blockDim.x) {
-      const int m = e / TC, t = e - m * TC;
-      const float K2 = s2[m] + so + s2[z0 + t];
-      const float g = K2 > 0.f ? -coef / K2 : 0.f;
-      r[e] = make_float2(r[e].x * g, r[e].y * g);
+    __syncthreads();  // every phase-3 read of the exchange buffer is done
+    if (r < R1) {
+      const float sc = s2[o] + s2[z0 + c];
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) {
+        const float K2 = s2[r + R1 * k2] + sc;
+        // fast division (a few ulp): far below the transforms' own rounding
+        const float g = K2 > 0.f ? __fdividef(-coef, K2) : 0.f;
+        u[k2] = make_float2(u[k2].x * g, u[k2].y * g);
+      }
+      // inverse, roles swapped: length-R2 DFTs over k2, twiddle W_N^{-r j1}
+      fft_phase1<R2, R1, true>(u, r, twN, [&](int j1) -> float2& { return fft_sm[(j1 * R1 + r) * TC + c]; });
     }
     __syncthreads();
-    float2* other = r == A ? B : A;
-    r = stockham<true, false>(r, other, N, TC, tw);
-  }
-  for (int e = threadIdx.x; e < N * TC; e += blockDim.x) {
-    const int m = e / TC, t = e - m * TC;
-    data[base + (long long)m * stride_axis + t] = r[e];
+    if (r < R2) {
+      float2 w[R1];
+#pragma unroll
+      for (int n2 = 0; n2 < R1; ++n2) w[n2] = fft_sm[(r * R1 + n2) * TC + c];
+      fft_phase3<R1, true>(w);
+#pragma unroll
+      for (int j2 = 0; j2 < R1; ++j2) col[(long long)(r + R2 * j2) * stride_axis] = w[j2];
+    }
   }
 }
 
@@ -165,20 +249,14 @@ static int fft_plan(int N, FftPlan** out) {
   p->N = N;
   const size_t n3 = (size_t)N * N * N;
   bool ok = cudaMalloc(&p->buf, n3 * sizeof(float2)) == cudaSuccess &&
-            cudaMalloc(&p->tw, (size_t)(N / 2) * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc(&p->tw, (size_t)N * sizeof(float2)) == cudaSuccess &&
             cudaMalloc(&p->s2, (size_t)N * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&p->partials, kMaxReduceBlocks * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&p->sum, sizeof(double)) == cudaSuccess;
-  // the shared-memory opt-in of the strided kernels (2 x 32 KB)
-  const int bytes = 2 * kFftTileElems * (int)sizeof(float2);
-  ok = ok && cudaFuncSetAttribute(k_fft_cols<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ==
-                 cudaSuccess &&
-       cudaFuncSetAttribute(k_fft_cols<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
-       cudaFuncSetAttribute(k_fft_cols<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
   if (ok) {
-    float2* tw = new float2[N / 2];
+    float2* tw = new float2[N];
     float* s2 = new float[N];
-    for (int m = 0; m < N / 2; ++m) {
+    for (int m = 0; m < N; ++m) {
       const double ang = -2.0 * M_PI * (double)m / (double)N;
       tw[m] = make_float2((float)cos(ang), (float)sin(ang));
     }
@@ -186,7 +264,7 @@ static int fft_plan(int N, FftPlan** out) {
       const double s = sin(M_PI * (double)k / (double)N);
       s2[k] = (float)(4.0 * s * s);
     }
-    ok = cudaMemcpy(p->tw, tw, (size_t)(N / 2) * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
+    ok = cudaMemcpy(p->tw, tw, (size_t)N * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(p->s2, s2, (size_t)N * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
     delete[] tw;
     delete[] s2;
@@ -229,31 +307,63 @@ void release_fft_plans() {
 
 static bool pow2_mesh(int N) { return N >= 8 && N <= 1024 && (N & (N - 1)) == 0; }
 
+// The five passes for N = R1 R2.  Rows kernel: L = 256/T rows per CTA (at most
+// N^2); columns kernel: TC = 256/T z columns per tile (at most N).  Dynamic
+// shared memory: the exchange buffer (about 33 KB at N = 256, 66 KB at 1024).
+template <int R1, int R2>
+static int poisson_passes(const float* rho, float* phi, double coef, const FftPlan* p, cudaStream_t st) {
+  constexpr int N = R1 * R2;
+  constexpr int T = fft_threads_per_line<R1, R2>();
+  const long long NN = (long long)N * N, n3 = NN * N;
+  const int L = (int)(kFftThreads / T < NN ? kFftThreads / T : NN);
+  const int TC = kFftThreads / T < N ? kFftThreads / T : N;
+  const size_t rows_smem = (size_t)L * R1 * (R2 + 1) * sizeof(float2);
+  const size_t cols_smem = (size_t)N * TC * sizeof(float2);
+  static bool attr_set[64] = {};  // per device: the opt-in above 48 KB, once
+  if (p->device < 64 && !attr_set[p->device]) {
+    MG_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows<R1, R2, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)rows_smem));
+    MG_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows<R1, R2, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)rows_smem));
+    MG_CUDA_TRY(cudaFuncSetAttribute(k_fft_cols<R1, R2, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)cols_smem));
+    MG_CUDA_TRY(cudaFuncSetAttribute(k_fft_cols<R1, R2, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)cols_smem));
+    MG_CUDA_TRY(cudaFuncSetAttribute(k_fft_cols<R1, R2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)cols_smem));
+    attr_set[p->device] = true;
+  }
+  const unsigned rows_grid = (unsigned)(NN / L);
+  const dim3 cols_grid(N / TC, N);
+  prof_begin(PC_POISSON_FFT, st, 72.0 * n3);
+  k_fft_rows<R1, R2, false, 1><<<rows_grid, L * T, rows_smem, st>>>(rho, p->buf, nullptr, L, 1.f, p->sum, n3, p->tw);
+  k_fft_cols<R1, R2, false, false><<<cols_grid, TC * T, cols_smem, st>>>(p->buf, TC, N, NN, p->tw, p->s2, 0.f);
+  k_fft_cols<R1, R2, false, true><<<cols_grid, TC * T, cols_smem, st>>>(p->buf, TC, NN, N, p->tw, p->s2, (float)coef);
+  k_fft_cols<R1, R2, true, false><<<cols_grid, TC * T, cols_smem, st>>>(p->buf, TC, N, NN, p->tw, p->s2, 0.f);
+  k_fft_rows<R1, R2, true, 2><<<rows_grid, L * T, rows_smem, st>>>(nullptr, p->buf, phi, L, (float)(1.0 / (double)n3),
+                                                                    nullptr, n3, p->tw);
+  prof_end(st);
+  note_launch(5);
+  MG_CUDA_TRY(cudaGetLastError());
+  return MGGLAM_OK;
+}
+
 int poisson_fft(const float* rho, int N, double coef, float* phi, cudaStream_t st) {
   if (!pow2_mesh(N)) return MGGLAM_ERR_SHAPE;
   FftPlan* p = nullptr;
   int rc = fft_plan(N, &p);
   if (rc) return rc;
-  const long long n3 = (long long)N * N * N;
-  if ((rc = launch_density_mean(rho, (size_t)n3, p->partials, p->sum, st))) return rc;
-  const long long NN = (long long)N * N;
-  const int L = kFftRowElems / N < NN ? kFftRowElems / N : (int)NN;  // rows per CTA (N <= 1024: >= 2)
-  const int TC = kFftTileElems / N < N ? kFftTileElems / N : N;       // z columns per tile (>= 4)
-  const unsigned rows_grid = (unsigned)(NN / L);
-  const size_t rows_smem = 2 * (size_t)L * N * sizeof(float2);
-  const size_t cols_smem = 2 * (size_t)N * TC * sizeof(float2);
-  const dim3 cols_grid(N / TC, N);
-  prof_begin(PC_POISSON_FFT, st, 72.0 * n3);
-  k_fft_rows<false, 1><<<rows_grid, kFftThreads, rows_smem, st>>>(rho, p->buf, nullptr, N, L, 1.f, p->sum, n3, p->tw);
-  k_fft_cols<false, false><<<cols_grid, kFftThreads, cols_smem, st>>>(p->buf, N, TC, N, NN, p->tw, p->s2, 0.f);
-  k_fft_cols<false, true><<<cols_grid, kFftThreads, cols_smem, st>>>(p->buf, N, TC, NN, N, p->tw, p->s2, (float)coef);
-  k_fft_cols<true, false><<<cols_grid, kFftThreads, cols_smem, st>>>(p->buf, N, TC, N, NN, p->tw, p->s2, 0.f);
-  k_fft_rows<true, 2><<<rows_grid, kFftThreads, rows_smem, st>>>(nullptr, p->buf, phi, N, L, (float)(1.0 / (double)n3),
-                                                                 nullptr, n3, p->tw);
-  prof_end(st);
-  note_launch(5);
-  MG_CUDA_TRY(cudaGetLastError());
-  return MGGLAM_OK;
+  if ((rc = launch_density_mean(rho, (size_t)N * N * N, p->partials, p->sum, st))) return rc;
+  switch (N) {
+    case 8: return poisson_passes<4, 2>(rho, phi, coef, p, st);
+    case 16: return poisson_passes<4, 4>(rho, phi, coef, p, st);
+    case 32: return poisson_passes<8, 4>(rho, phi, coef, p, st);
+    case 64: return poisson_passes<8, 8>(rho, phi, coef, p, st);
+    case 128: return poisson_passes<16, 8>(rho, phi, coef, p, st);
+    case 256: return poisson_passes<16, 16>(rho, phi, coef, p, st);
+    case 512: return poisson_passes<32, 16>(rho, phi, coef, p, st);
+    default: return poisson_passes<32, 32>(rho, phi, coef, p, st);
+  }
 }
 
 }  // namespace mg

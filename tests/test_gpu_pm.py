@@ -2,7 +2,7 @@
 
 Tolerances:
 * FFT Poisson: single-precision FFTs of length N carry ~log2(N) x 6e-8 relative
-  rounding per transform; 2e-5 of max|phi| covers the five passes up to N = 128.
+  rounding per transform; 2e-5 of max|phi| covers the five passes up to N = 1024.
 * One PM step: positions and momenta are float32 (rounding 6e-8 relative, i.e.
   ~2e-6 cells at x ~ 32); the mixed scalar solve agrees with the FP64 oracle to
   ~1e-6 of the field, the FP32 potential and gradient to ~1e-5 of the force.
@@ -34,13 +34,35 @@ def pm(orc):
     return pm_mod
 
 
-@pytest.mark.parametrize("N", [8, 32, 128])
+@pytest.mark.parametrize("N", [8, 16, 32, 64, 128, 256])
 def test_poisson_fft_matches_oracle(mg, pm, N):
     rho = inputs.lognormal_density(N, 1.0, seed=60 + N).astype(np.float32) * 2.5
     coef = 1.5 * 0.3 / 0.7
     phi = mg.poisson_fft(torch.from_numpy(rho).cuda(), coef).cpu().numpy().astype(np.float64)
     ref = pm.poisson_fft(rho.astype(np.float64), coef)
     assert np.abs(phi - ref).max() <= 2e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("N", [512, 1024])
+def test_poisson_fft_single_mode_closed_form(mg, N):
+    """The largest transforms (32 x 16 and 32 x 32 splits): rho = 1 + A cos(2 pi m x / N)
+    along each axis in turn gives phi = -coef A cos(...) / (4 sin^2(pi m / N))."""
+    coef, A, m = 0.9, 0.4, 3
+    x = (torch.arange(N, device="cuda", dtype=torch.float64) + 0.5) * (2 * np.pi * m / N)
+    expect_line = (-coef * A * torch.cos(x) / (4 * np.sin(np.pi * m / N) ** 2)).cpu().numpy()
+    for axis in range(3):
+        shape = [1, 1, 1]
+        shape[axis] = N
+        rho = (1 + A * torch.cos(x)).to(torch.float32).reshape(shape).expand(N, N, N).contiguous()
+        phi = mg.poisson_fft(rho, coef)
+        idx = [slice(0, 1)] * 3
+        idx[axis] = slice(None)
+        got = phi[tuple(idx)].reshape(-1).double().cpu().numpy()
+        assert np.abs(got - expect_line).max() <= 2e-5 * np.abs(expect_line).max()
+        # every line along the other axes is the same
+        assert float((phi - phi[tuple(idx)]).abs().max()) <= 2e-5 * np.abs(expect_line).max()
+        del rho, phi
+    torch.cuda.empty_cache()
 
 
 def test_poisson_fft_rejects_unsupported_meshes(mg):
