@@ -413,3 +413,24 @@ def test_tophat_matches_oracle_and_radial_ode(orc, mg, key, precision):
     assert relL2(got, ref.u) <= (1e-9 if precision == 0 else 1e-6)
     inside, edge, far, _ = tophat_errors(got, r, rr, uu, N)
     assert inside <= 1e-2 and edge <= 4e-2 and far <= 5e-3
+
+
+@pytest.mark.parametrize("key", ["fr1", "fr2", "sym"])
+def test_mixed_solve_at_the_headline_tolerance(orc, mg, key):
+    """A mixed solve to 1e-8 (the tolerance of the 256^3 workload) on a split finest
+    level: the oracle's FP64 residual of the GPU solution meets the tolerance, and the
+    field agrees with the oracle's 1e-11 solution to the accuracy a 1e-8 residual implies."""
+    N = 64
+    rho = inputs.lognormal_density(N, 1.2, seed=70)
+    box = {"sym": float(N)}.get(key, 64.0)
+    po, pg = both_params(orc, mg, key, box=box, precision=1, max_cycles=40)
+    rho32 = rho.astype(np.float32)
+    ref = orc.solve(po, rho32.astype(np.float64), tol=1e-11, max_cycles=60)
+    field = torch.full((N, N, N), float("nan"), dtype=torch.float64, device="cuda")
+    st = mg.solve_scalar(pg, 1.0, cuda32(rho32), field, 1e-8)
+    assert st.converged
+    got = field.cpu().numpy()
+    rho_n = rho32.astype(np.float64) / rho32.astype(np.float64).mean()
+    eps = np.sqrt((orc.residual(po, got, rho_n) ** 2).mean()) / orc.source_rms(po, rho_n)
+    assert eps <= 1e-8
+    assert relL2(got, ref.u) <= 1e-5
