@@ -254,11 +254,18 @@ __device__ __forceinline__ void fas_quad(const LevelF& f, int n, const float* __
 // QK >= 0 (split layout, f(R) n = QK): also writes the second colour's stored
 // neighbour quantity q = Delta w(u, e) into qf (smooth_split with QS), so that
 // the next first-colour pass sees the corrected values.
-template <bool FR, class FL = NatLayout, int QK = -1>
+// SECOND_ONLY (with QK >= 0, when post-smoothing follows): corrects the second
+// colour only.  The f(R) local solve of the first-colour pass that comes next
+// does not read a cell's old value (the closed-form root from u, S and the
+// neighbours, then the polish), so the first colour's corrected values would be
+// overwritten unread; skipping them leaves the iterates unchanged and moves
+// 8 instead of 14 bytes per fine cell.
+template <bool FR, class FL = NatLayout, int QK = -1, bool SECOND_ONLY = false>
 __device__ __forceinline__ void prolong_quad(int nc, const float* __restrict__ eH, const float* __restrict__ Re,
                                              const float* __restrict__ ub, float* __restrict__ ef, int i, int j,
                                              int tq, int lane, float* __restrict__ qf = nullptr) {
   static_assert(QK < 0 || (FR && QK != KFR0), "stored q: f(R) n = 1, 2");
+  static_assert(!SECOND_ONLY || QK >= 0, "second-colour-only prolongation: split layout with stored q");
   const int nf = nc << 1, nq = nf >> 2;
   const bool act = tq < nq;
   const int t = act ? tq : nq - 1;
@@ -288,6 +295,24 @@ __device__ __forceinline__ void prolong_quad(int nc, const float* __restrict__ e
     Rp = 9.f * d1(rA, Kp) + 3.f * (d1(rB, Kp) + d1(rC, Kp)) + d1(rD, Kp);
   }
   constexpr float w = 1.f / 64.f;
+  if constexpr (SECOND_ONLY) {
+    // the second colour's two cells of the quad: k0 and k0+2 where i + j is odd, else k0+1 and k0+3;
+    // they are consecutive in the second colour's half-row
+    const bool odd = (i + j) & 1;
+    const float cA = odd ? (3.f * Rx + Rm) * w : (3.f * Rx + Ry) * w;
+    const float cB = odd ? (3.f * Ry + Rx) * w : (3.f * Ry + Rp) * w;
+    const int h = nf >> 1;
+    const long long o1 = (long long)nf * nf * h + ((long long)i * nf + j) * h + (k0 >> 1);
+    const float2 old = ld2(ef + o1), u = ld2(ub + o1);
+    float vA = old.x + cA, vB = old.y + cB;
+    if (!(u.x + vA > 0.f)) vA = 0.5f * (old.x - u.x);
+    if (!(u.y + vB > 0.f)) vB = 0.5f * (old.y - u.y);
+    if (act) {
+      *reinterpret_cast<float2*>(ef + o1) = make_float2(vA, vB);
+      *reinterpret_cast<float2*>(qf + o1) = make_float2(dw<QK>(u.x, vA), dw<QK>(u.y, vB));
+    }
+    return;
+  }
   const float4 old = FL::q(ef, nf, i, j, k0);
   float4 v = make_float4(old.x + (3.f * Rx + Rm) * w, old.y + (3.f * Rx + Ry) * w, old.z + (3.f * Ry + Rx) * w,
                          old.w + (3.f * Ry + Rp) * w);

@@ -165,13 +165,13 @@ __global__ void __launch_bounds__(128) k_residual_restrict32q(LevelF f, int nf, 
 }
 
 // Prolongation: grid (ceil(nf/128), nf [j], nf/4 [i]).
-template <bool FR, class FL = NatLayout, int QK = -1>
+template <bool FR, class FL = NatLayout, int QK = -1, bool SECOND_ONLY = false>
 __global__ void __launch_bounds__(128) k_prolong_correct32q(int nc, const float* __restrict__ eH,
                                                             const float* __restrict__ Re,
                                                             const float* __restrict__ ub, float* __restrict__ ef,
                                                             float* __restrict__ qf = nullptr) {
-  prolong_quad<FR, FL, QK>(nc, eH, Re, ub, ef, blockIdx.z * 4 + threadIdx.y, blockIdx.y,
-                           blockIdx.x * 32 + threadIdx.x, threadIdx.x, qf);
+  prolong_quad<FR, FL, QK, SECOND_ONLY>(nc, eH, Re, ub, ef, blockIdx.z * 4 + threadIdx.y, blockIdx.y,
+                                        blockIdx.x * 32 + threadIdx.x, threadIdx.x, qf);
 }
 
 // FAS source, four cells per lane (n % 4 == 0, n >= 8): grid (ceil(n/128), n, n/4).
@@ -553,12 +553,20 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode) {
     if ((rc = vcycle32(C, l + 1, st, mode))) return rc;
     if (mode != 0 && (rc = vcycle32(C, l + 1, st, mode == 2 ? 2 : 0))) return rc;
   }
-  if (l == 0) { prof_end(st); prof_begin(PC_PROLONG32_FINE, st, 13.0 * L.n3); }
+  // algorithmic bytes per fine cell: e, u read and e written (12), the coarse pair (1); the
+  // second-colour-only form reads and writes half of e and u and writes half of q (9)
+  if (l == 0) { prof_end(st); prof_begin(PC_PROLONG32_FINE, st, (C.qs && C.prm->nu2 >= 1 ? 9.0 : 13.0) * L.n3); }
   const int bf = bx_for(L.n);
   if (l == 0 && C.split) {
     const dim3 g((L.n / 4 + 31) / 32, L.n, L.n / 4);
-    if (C.qs && C.m.kind == KFR1)
+    // with post-smoothing the first colour's corrections would be overwritten unread (prolong_quad)
+    const bool second_only = C.prm->nu2 >= 1;
+    if (C.qs && C.m.kind == KFR1 && second_only)
+      k_prolong_correct32q<true, SplitLayout, KFR1, true><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.qs);
+    else if (C.qs && C.m.kind == KFR1)
       k_prolong_correct32q<true, SplitLayout, KFR1><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.qs);
+    else if (C.qs && second_only)
+      k_prolong_correct32q<true, SplitLayout, KFR2, true><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.qs);
     else if (C.qs)
       k_prolong_correct32q<true, SplitLayout, KFR2><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.qs);
     else if (is_fr(C.m.kind))
