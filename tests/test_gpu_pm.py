@@ -146,3 +146,26 @@ def test_pm_plane_wave_grows_like_the_discrete_linear_mode(mg):
     # float32 positions near 32 resolve ~2e-6 cells: 1e-4 of the 0.025-cell amplitude
     assert np.abs(disp[:, 0] - A_final * psi).max() / A_final < 2e-3
     assert np.abs(disp[:, 1:]).max() < 1e-5
+
+
+@pytest.mark.parametrize("N,steps", [(32, 5), (256, 1)])
+def test_pm_step_conserves_momentum(mg, N, steps):
+    """CIC deposit and interpolation with a symmetric Green's function and an
+    antisymmetric difference exert no net force (test_pm.py pins this for the
+    oracle); it holds at any size, so it checks the GPU step at the headline size
+    (256^3 mesh, 256^3 Zel'dovich particles): a LCDM step changes the total momentum
+    by float32 rounding only, far below the sum of the kicks."""
+    pos = torch.from_numpy(inputs.zeldovich_positions(N, seed=1, sigma=1.5)).cuda()
+    mom = torch.zeros_like(pos)
+    rho_w = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+    psi_w = torch.empty_like(rho_w)
+    prm = mg.Params(model=0, n=1, fR0_abs=1e-6, box=float(N))
+    a, da = 0.5, 0.01
+    for s in range(steps):
+        before = mom.double().sum(0)
+        prev = mom.clone()
+        mg.pm_step(prm, a + s * da, da, pos, mom, rho_w, psi_w)
+        kick = (mom - prev).double()
+        total = float(kick.abs().sum())
+        assert total > 0
+        assert float((mom.double().sum(0) - before).abs().max()) <= 1e-5 * total
