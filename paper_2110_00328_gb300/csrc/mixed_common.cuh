@@ -90,12 +90,15 @@ __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast
 // k-neighbours outside the quad come from the adjacent lanes by shuffles.  All
 // 32 lanes of a warp take part (same I, J); lanes past the row end work on a
 // clamped quad and store nothing.
-template <int K, class FL = NatLayout>
+// QH (f(R) n = 1, 2 on a split level with stored q, in qf): the halo rows'
+// neighbour quantities are read from qf instead of formed from e and u.
+template <int K, class FL = NatLayout, bool QH = false>
 __device__ __forceinline__ void restrict_quad(const LevelF& f, int nf, const float* __restrict__ e,
                                               const float* __restrict__ ub, const float* __restrict__ rho,
                                               const float* __restrict__ S, float* __restrict__ Re,
                                               float* __restrict__ eH, float* __restrict__ ubH,
-                                              float* __restrict__ SH, int I, int J, int tq, int lane) {
+                                              float* __restrict__ SH, int I, int J, int tq, int lane,
+                                              const float* __restrict__ qf = nullptr) {
   constexpr bool FR = is_fr(K);
   constexpr bool RHO = (K == KSYM) || (K == KCQ);
   const int nc = nf >> 1, nq = nf >> 2;
@@ -105,6 +108,10 @@ __device__ __forceinline__ void restrict_quad(const LevelF& f, int nf, const flo
   const int iA = i0 == 0 ? nf - 1 : i0 - 1, iB = i0 + 2 == nf ? 0 : i0 + 2;
   const int jA = j0 == 0 ? nf - 1 : j0 - 1, jB = j0 + 2 == nf ? 0 : j0 + 2;
   auto q4 = [&](int i, int j) {
+    if constexpr (QH) {
+      static_assert(K == KFR1 || K == KFR2, "stored q: f(R) n = 1, 2");
+      return FL::q(qf, nf, i, j, k0);
+    }
     const float4 E = FL::q(e, nf, i, j, k0);
     if constexpr (FR) {
       const float4 U = FL::q(ub, nf, i, j, k0);
