@@ -434,3 +434,23 @@ def test_mixed_solve_at_the_headline_tolerance(orc, mg, key):
     eps = np.sqrt((orc.residual(po, got, rho_n) ** 2).mean()) / orc.source_rms(po, rho_n)
     assert eps <= 1e-8
     assert relL2(got, ref.u) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_point_mass_matches_oracle_and_decays_at_m_eff(orc, mg, precision):
+    """The Sec. 4.2 point mass at 64^3 (f(R) n = 1, |fR0| = 1e-5, box 96 Mpc/h): the GPU
+    solution equals the oracle's and its far field decays at the paper's m~_eff
+    (test_point_mass_far_field_is_the_yukawa_solution)."""
+    from test_oracle_pins import point_mass_case, point_mass_decay, paper_m_eff
+    N = 64
+    p, b, delta, _, R = point_mass_case(orc, 1, N)
+    rho32 = (1 + delta).astype(np.float32)
+    ref = orc.solve(p, rho32.astype(np.float64), tol=1e-12, max_cycles=80)
+    pg = mg.Params(model=0, n=1, fR0_abs=1e-5, box=p.box, precision=precision, max_cycles=60)
+    field = torch.full((N, N, N), float("nan"), dtype=torch.float64, device="cuda")
+    st = mg.solve_scalar(pg, 1.0, cuda32(rho32), field, 1e-10)
+    assert st.converged
+    u = field.cpu().numpy()
+    assert relL2(u, ref.u) <= (1e-9 if precision == 0 else 1e-6)
+    dfR = -(u ** 2) - b["fRbar"]
+    assert point_mass_decay(dfR, N, diagonal=True) == pytest.approx(paper_m_eff(p, b), rel=0.01)
