@@ -34,6 +34,7 @@ struct BDesc {
   int split;  // this level (the finest) in the red-black split layout
   LevelF lf;  // constants of this level
   float *e, *ub, *S, *rho, *Re;      // this level
+  float* q;                          // split f(R) n = 1, 2: the stored neighbour quantity, else nullptr
   float *eH, *ubH, *SH, *ReH;        // next coarser level (if any)
 };
 
@@ -46,6 +47,7 @@ struct BFine {
   const FFC* ffc;      // f(R), symmetron: float-float residual constants
   const float* rho;    // f(R), symmetron: the caller's density
   float *ub, *tau, *e;
+  float* q;            // the finest level's stored neighbour quantity (zeroed with e), or nullptr
 };
 
 // Level layouts of the batched kernels: the quad kernels take levels whose side
@@ -80,6 +82,13 @@ __global__ void __launch_bounds__(32 * ROWS) kb_smooth(const BDesc* __restrict__
     int seg;
     bool act;
     split_lane(n, n, (long long)b * ROWS + threadIdx.y, threadIdx.x, &r, &seg, &act);
+    if constexpr (K == KFR1 || K == KFR2) {
+      if (d.q) {
+        smooth_split<K, true>(d.lf, n, d.e, d.ub, d.rho, d.S, (int)(r / n), (int)(r % n), seg, act, parity,
+                              threadIdx.x, d.q);
+        return;
+      }
+    }
     smooth_split<K>(d.lf, n, d.e, d.ub, d.rho, d.S, (int)(r / n), (int)(r % n), seg, act, parity, threadIdx.x);
     return;
   }
@@ -121,6 +130,13 @@ __global__ void __launch_bounds__(128) kb_restrict(const BDesc* __restrict__ D, 
     const int nbx = ((nf >> 2) + 31) / 32;
     const int xb = b % nbx, r = b / nbx, J = r % nc, I = (r / nc) * 4 + threadIdx.y;
     if (I >= nc) return;  // whole warps
+    if constexpr (K == KFR1 || K == KFR2) {
+      if (d.split && d.q) {
+        restrict_quad<K, SplitLayout, true>(d.lf, nf, d.e, d.ub, d.rho, d.S, d.ReH, d.eH, d.ubH, d.SH, I, J,
+                                            xb * 32 + threadIdx.x, threadIdx.x, d.q);
+        return;
+      }
+    }
     if (d.split)
       restrict_quad<K, SplitLayout>(d.lf, nf, d.e, d.ub, d.rho, d.S, d.ReH, d.eH, d.ubH, d.SH, I, J,
                                     xb * 32 + threadIdx.x, threadIdx.x);
@@ -175,7 +191,9 @@ __global__ void __launch_bounds__(64) kb_fas(const BDesc* __restrict__ D, const 
 // Prolongation-correction of level l from l+1; block (32, 4).  Quad levels:
 // ceil(nf/128) x nf x ceil(nf/4) blocks per solve; others: one fine cell per
 // thread, flat.
-template <bool FR>
+// QK >= 0 (f(R) n = QK): levels with a stored q get it written (prolong_quad),
+// only for the second colour when SO (post-smoothing follows).
+template <bool FR, int QK = -1, bool SO = false>
 __global__ void __launch_bounds__(128) kb_prolong(const BDesc* __restrict__ D, const int* __restrict__ prefix, int cnt,
                                                   const int* __restrict__ active) {
   const int s = find_slot(prefix, cnt, blockIdx.x);
@@ -187,6 +205,13 @@ __global__ void __launch_bounds__(128) kb_prolong(const BDesc* __restrict__ D, c
     const int nbx = ((nf >> 2) + 31) / 32;
     const int xb = b % nbx, r = b / nbx, j = r % nf, i = (r / nf) * 4 + threadIdx.y;
     if (i >= nf) return;  // whole warps
+    if constexpr (QK >= 0) {
+      if (d.split && d.q) {
+        prolong_quad<FR, SplitLayout, QK, SO>(nc, d.eH, d.ReH, d.ub, d.e, i, j, xb * 32 + threadIdx.x, threadIdx.x,
+                                              d.q);
+        return;
+      }
+    }
     if (d.split) prolong_quad<FR, SplitLayout>(nc, d.eH, d.ReH, d.ub, d.e, i, j, xb * 32 + threadIdx.x, threadIdx.x);
     else prolong_quad<FR>(nc, d.eH, d.ReH, d.ub, d.e, i, j, xb * 32 + threadIdx.x, threadIdx.x);
     return;
@@ -265,7 +290,7 @@ __global__ void kb_finalize(const BFine* __restrict__ F, const int* __restrict__
   if (threadIdx.x == 0) out[F[s].solve] = a;
 }
 
-// u64 += e and e <- 0 for every active solve (fine-cell grid).
+// u64 += e and e <- 0 (and the stored q <- 0) for every active solve (fine-cell grid).
 __global__ void __launch_bounds__(256) kb_apply(const BFine* __restrict__ F, const int* __restrict__ prefix, int cnt,
                                                 const int* __restrict__ active, int clear_only) {
   const int s = find_slot(prefix, cnt, blockIdx.x);
@@ -280,6 +305,7 @@ __global__ void __launch_bounds__(256) kb_apply(const BFine* __restrict__ F, con
                                                   (int)(t % f.n));
   if (!clear_only) f.u[t] += (double)f.e[c];
   f.e[c] = 0.f;
+  if (f.q) f.q[c] = 0.f;  // Delta w(u, 0)
 }
 
 // ---------------------------------------------------------------------------
@@ -303,6 +329,7 @@ struct Batch {
     int N, nlev, kind;
     double* src64;
     float *e[kMaxLevels], *ub[kMaxLevels], *S32[kMaxLevels], *Re[kMaxLevels], *rho32[kMaxLevels];
+    float* q0;  // the finest level's stored neighbour quantity (used for f(R) n = 1, 2)
   };
   std::vector<S> sv;
   double* partials = nullptr;  // outer-residual partials
@@ -365,7 +392,7 @@ static int get_batch(int count, const int* N, const mgglam_params* prm, Batch** 
   b->count = count;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
-  struct O { size_t src, e[kMaxLevels], ub[kMaxLevels], S[kMaxLevels], Re[kMaxLevels], rho[kMaxLevels]; };
+  struct O { size_t src, q0, e[kMaxLevels], ub[kMaxLevels], S[kMaxLevels], Re[kMaxLevels], rho[kMaxLevels]; };
   std::vector<O> o(count);
   size_t total_blocks = 0;
   b->sv.resize(count);
@@ -374,6 +401,7 @@ static int get_batch(int count, const int* N, const mgglam_params* prm, Batch** 
     v.N = N[s];
     v.nlev = count_levels(N[s], prm[s].levels);
     o[s].src = take((size_t)N[s] * N[s] * N[s] * 8);
+    o[s].q0 = take((size_t)N[s] * N[s] * N[s] * 4);  // the plan is cached per mesh set, the models may change
     for (int l = 0, n = N[s]; l < v.nlev; ++l, n /= 2) {
       const size_t c = (size_t)n * n * n * 4;
       o[s].e[l] = take(c);
@@ -403,6 +431,7 @@ static int get_batch(int count, const int* N, const mgglam_params* prm, Batch** 
   for (int s = 0; s < count; ++s) {
     Batch::S& v = b->sv[s];
     v.src64 = (double*)(base + o[s].src);
+    v.q0 = (float*)(base + o[s].q0);
     for (int l = 0; l < v.nlev; ++l) {
       v.e[l] = (float*)(base + o[s].e[l]);
       v.ub[l] = (float*)(base + o[s].ub[l]);
@@ -480,6 +509,7 @@ static int build_plan(Batch* B, const std::vector<ModelDev>& models, const std::
     d.n = v.N >> l;
     d.solve = s;
     d.split = (l == 0 && models[s].kind != KCQ) ? 1 : 0;  // split finest level (float-float residual)
+    d.q = (l == 0 && (models[s].kind == KFR1 || models[s].kind == KFR2)) ? v.q0 : nullptr;
     d.lf = lfs[s][l];
     d.e = v.e[l];
     d.ub = v.ub[l];
@@ -588,6 +618,7 @@ static int build_plan(Batch* B, const std::vector<ModelDev>& models, const std::
       f.ub = v.ub[0];
       f.tau = v.S32[0];
       f.e = v.e[0];
+      f.q = (models[s].kind == KFR1 || models[s].kind == KFR2) ? v.q0 : nullptr;
       fk[g].push_back(f);
       bo.push_back((v.N / 32) * (v.N / 8) * ((v.N + 63) / 64));
       ba.push_back((int)(((size_t)v.N * v.N * v.N + 255) / 256));
@@ -670,8 +701,14 @@ static void batch_vcycle(const Plan& P, const int* active, const mgglam_params& 
     const auto& L = P.lv[l];
     for (size_t g = 0; g < L.prolong.size(); ++g) {
       const Phase& p = L.prolong[g];
-      if (is_fr(p.kind)) kb_prolong<true><<<p.blocks, dim3(32, 4), 0, st>>>(p.d, p.prefix, p.cnt, active);
-      else kb_prolong<false><<<p.blocks, dim3(32, 4), 0, st>>>(p.d, p.prefix, p.cnt, active);
+      const bool so = prm.nu2 >= 1;  // the same for every solve of the batch
+      const dim3 b4(32, 4);
+      if (p.kind == KFR1 && so) kb_prolong<true, KFR1, true><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active);
+      else if (p.kind == KFR1) kb_prolong<true, KFR1><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active);
+      else if (p.kind == KFR2 && so) kb_prolong<true, KFR2, true><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active);
+      else if (p.kind == KFR2) kb_prolong<true, KFR2><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active);
+      else if (is_fr(p.kind)) kb_prolong<true><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active);
+      else kb_prolong<false><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active);
       note_launch(1);
       for (int s = 0; s < prm.nu2; ++s)
         for (int par = 0; par < 2; ++par) launch_smooth_phase(L.smooth[g], rows, active, par, st);
@@ -719,6 +756,7 @@ int solve_batch(int count, const mgglam_params* prm, const double* a, const floa
                                      models[s], rho[s], n3, B->rmean + s, B->partials)));
     k_finalize_sum32<<<1, 1024, 0, st>>>(B->partials, stream_grid(n3), B->ssum + s);
     MG_CUDA_TRY(cudaMemsetAsync(v.e[0], 0, (size_t)n3 * 4, st));
+    MG_CUDA_TRY(cudaMemsetAsync(v.q0, 0, (size_t)n3 * 4, st));  // Delta w(u, 0) = 0
     note_launch(5 + v.nlev);
   }
   Plan P;
@@ -774,8 +812,11 @@ int solve_batch(int count, const mgglam_params* prm, const double* a, const floa
     }
     B->rows = best;
     // the timing sweeps changed e on the fine levels: start again from zero
-    for (int s = 0; s < count; ++s)
-      MG_CUDA_TRY(cudaMemsetAsync(B->sv[s].e[0], 0, (size_t)B->sv[s].N * B->sv[s].N * B->sv[s].N * 4, st));
+    for (int s = 0; s < count; ++s) {
+      const size_t bytes = (size_t)B->sv[s].N * B->sv[s].N * B->sv[s].N * 4;
+      MG_CUDA_TRY(cudaMemsetAsync(B->sv[s].e[0], 0, bytes, st));
+      MG_CUDA_TRY(cudaMemsetAsync(B->sv[s].q0, 0, bytes, st));
+    }
     if ((rc = build_plan(B, models, lfs, std::vector<const float*>(rho, rho + count), field, prm, false, B->rows, &P,
                          st)))
       return rc;
