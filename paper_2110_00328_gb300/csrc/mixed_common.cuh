@@ -579,15 +579,78 @@ __device__ __forceinline__ double outer_residual_tile_ff(const FFC& C, int n, in
   return block_sum((double)acc);
 }
 
+// skip (may be nullptr): set when k_background_residual_ff has already formed
+// this residual (the solve started from the background field).
 template <int K, int TJ, int TK, bool SPLIT = false>
 __global__ void __launch_bounds__(TJ* TK) k_outer_residual_ff(const FFC* __restrict__ C, int n, int chunk,
                                                               const double* __restrict__ u,
                                                               const float* __restrict__ rho,
                                                               float* __restrict__ ub, float* __restrict__ tau,
-                                                              double* __restrict__ partials) {
+                                                              double* __restrict__ partials,
+                                                              const int* __restrict__ skip = nullptr) {
+  if (skip && *skip) return;
   const FFC c = *C;
   const double a = outer_residual_tile_ff<K, TJ, TK, SPLIT>(c, n, chunk, u, rho, ub, tau, blockIdx.x, blockIdx.y);
   if (threadIdx.x == 0) partials[blockIdx.x + blockIdx.y * gridDim.x] = a;
+}
+
+// The start from the background field (its first element NaN on entry): the
+// field is set to ubar everywhere but at cell 0 (k_background_first writes that
+// one, and the flag, after every CTA has read it) and the residual at the
+// uniform field is formed in the same pass.  There the six-neighbour sum of w
+// equals 6w exactly, so r = N(ubar) is the source term alone, which the
+// float-float operations of outer_residual_tile_ff give to the same accuracy:
+//   f(R): c1 rho + c0 - K/ubar;  symmetron: -msym ((rho/mean rat3 - 1) ubar + ubar^3).
+// Writes ub = float(ubar), tau = -float(r) in the level's layout and one
+// partial sum of tau^2 per CTA, for a grid of the general kernel's shape.
+// When the field is not NaN-marked it returns at once (the general kernel runs).
+template <int K, bool SPLIT>
+__global__ void __launch_bounds__(256) k_background_residual_ff(const FFC* __restrict__ C, int n,
+                                                                double* __restrict__ u, double ubar,
+                                                                const float* __restrict__ rho,
+                                                                float* __restrict__ ub, float* __restrict__ tau,
+                                                                double* __restrict__ partials) {
+  static_assert(K != KCQ, "CQ keeps the FP64 residual");
+  if (!isnan(u[0])) return;
+  const FFC c = *C;
+  const ff uc = ff_from_double(ubar);
+  const float ubf = ff_to_float(uc);
+  const long long n3 = (long long)n * n * n;
+  const long long nb = (long long)gridDim.x * gridDim.y;
+  const long long b = blockIdx.x + (long long)blockIdx.y * gridDim.x;
+  float acc = 0.f;
+  for (long long t = b * blockDim.x + threadIdx.x; t < n3; t += nb * blockDim.x) {
+    if (t != 0) u[t] = ubar;
+    const float r = rho[t];
+    float tv;
+    if constexpr (is_fr(K)) {
+      ffacc v = acc_of(c.c0);
+      const ff p1 = two_prod(c.c1.hi, r);
+      acc_add(v, p1.hi, __fmaf_rn(c.c1.lo, r, p1.lo));
+      const ff q = ff_div(c.K, uc);
+      acc_add(v, -q.hi, -q.lo);
+      tv = -acc_float(v);
+    } else {
+      const ff a = ff_sub(ff_mul(ff_mul_f(c.c1, r), c.rat3), ff{1.f, 0.f});
+      const ff bb = ff_add(ff_mul(a, uc), ff_mul(ff_sqr(uc), uc));
+      tv = ff_to_float(ff_mul(c.msym, bb));
+    }
+    const int k = (int)(t % n), j = (int)((t / n) % n), i = (int)(t / ((long long)n * n));
+    const long long o = SPLIT ? split_idx(n, i, j, k) : t;
+    ub[o] = ubf;
+    tau[o] = tv;
+    acc += tv * tv;
+  }
+  const double a = block_sum((double)acc);
+  if (threadIdx.x == 0) partials[b] = a;
+}
+
+// Cell 0 of the background start, and the flag that tells the general residual
+// kernel its work is done (flag = 0 when the caller gave an initial field).
+static __global__ void k_background_first(double* __restrict__ u, double ubar, int* __restrict__ flag) {
+  const bool bg = isnan(u[0]);
+  if (bg) u[0] = ubar;
+  *flag = bg ? 1 : 0;
 }
 
 template <int K, int TJ, int TK>

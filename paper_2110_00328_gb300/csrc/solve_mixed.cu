@@ -602,24 +602,41 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode) {
 // Tile of the FP64 outer-residual kernel.
 constexpr int kRTJ = 8, kRTK = 32;
 
+// bg_first: the first residual of the solve, with the background start fused
+// into it (k_background_residual_ff); the tiled meshes only.
+static bool bg_residual_tiled(int n) { return n % kRTK == 0 && n % kRTJ == 0; }
+
 template <int K>
-static int launch_outer_residual_ff(const MixedCtx& C, double* field, int* blocks, cudaStream_t st) {
+static int launch_outer_residual_ff(const MixedCtx& C, double* field, int* blocks, cudaStream_t st, bool bg_first) {
   Workspace* ws = C.ws;
   Level& F = ws->lev[0];
   const FFC* ffc = ffc_of(ws);
-  if (F.n % kRTK == 0 && F.n % kRTJ == 0) {
+  if (bg_residual_tiled(F.n)) {
     const long long tiles = (long long)(F.n / kRTK) * (F.n / kRTJ);
     const int chunk = C.split ? march_chunk(F.n, tiles, (const void*)k_outer_residual_ff<K, kRTJ, kRTK, true>, kRTJ * kRTK)
                               : march_chunk(F.n, tiles, (const void*)k_outer_residual_ff<K, kRTJ, kRTK>, kRTJ * kRTK);
     dim3 grid((F.n / kRTK) * (F.n / kRTJ), (F.n + chunk - 1) / chunk);
     *blocks = grid.x * grid.y;
     if (*blocks > kMaxReduceBlocks) return MGGLAM_ERR_SHAPE;
+    const int* skip = nullptr;
+    if (bg_first) {
+      int* flag = reinterpret_cast<int*>(ws->scalars + SC_FLAG);
+      if (C.split)
+        k_background_residual_ff<K, true><<<grid, 256, 0, st>>>(ffc, F.n, field, C.m.ubar, C.rho, F.ub, F.S32,
+                                                                 ws->partials);
+      else
+        k_background_residual_ff<K, false><<<grid, 256, 0, st>>>(ffc, F.n, field, C.m.ubar, C.rho, F.ub, F.S32,
+                                                                  ws->partials);
+      k_background_first<<<1, 1, 0, st>>>(field, C.m.ubar, flag);
+      note_launch(2);
+      skip = flag;
+    }
     if (C.split)
       k_outer_residual_ff<K, kRTJ, kRTK, true><<<grid, kRTJ * kRTK, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub,
-                                                                             F.S32, ws->partials);
+                                                                             F.S32, ws->partials, skip);
     else
       k_outer_residual_ff<K, kRTJ, kRTK><<<grid, kRTJ * kRTK, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub, F.S32,
-                                                                       ws->partials);
+                                                                       ws->partials, skip);
     return MGGLAM_OK;
   }
   const int tk = (F.n % 16 == 0) ? 16 : ((F.n % 8 == 0) ? 8 : ((F.n % 4 == 0) ? 4 : 2));
@@ -636,11 +653,11 @@ static int launch_outer_residual_ff(const MixedCtx& C, double* field, int* block
 }
 
 template <int K>
-static int launch_outer_residual_t(const MixedCtx& C, double* field, int* blocks, cudaStream_t st) {
+static int launch_outer_residual_t(const MixedCtx& C, double* field, int* blocks, cudaStream_t st, bool bg_first) {
   Workspace* ws = C.ws;
   Level& F = ws->lev[0];
   if constexpr (K != KCQ) {
-    if (C.ff_resid) return launch_outer_residual_ff<K>(C, field, blocks, st);
+    if (C.ff_resid) return launch_outer_residual_ff<K>(C, field, blocks, st, bg_first);
   }
   if (F.n % kRTK == 0 && F.n % kRTJ == 0) {
     const int chunk = march_chunk(F.n, (long long)(F.n / kRTK) * (F.n / kRTJ),
@@ -666,13 +683,17 @@ static int launch_outer_residual_t(const MixedCtx& C, double* field, int* blocks
   return MGGLAM_OK;
 }
 
-static int outer_residual(const MixedCtx& C, double* field, cudaStream_t st) {
+// bg_first: the solve's first residual, on a mesh where the background start is
+// fused into it (fused_background_start); the field's background fill happens there.
+static bool fused_background_start(const MixedCtx& C) { return C.ff_resid && bg_residual_tiled(C.ws->lev[0].n); }
+
+static int outer_residual(const MixedCtx& C, double* field, cudaStream_t st, bool bg_first = false) {
   Workspace* ws = C.ws;
   Level& F = ws->lev[0];
   // bytes per cell: u (8) and the source (float-float: the FP32 density, 4; FP64: src64, 8) in, ub and tau (4 + 4) out
   prof_begin(PC_OUTER_RESID, st, (C.ff_resid ? 20.0 : 24.0) * F.n3);
   int g = 0, rc = MGGLAM_OK;
-  MG_DISPATCH32(C.m.kind, (rc = launch_outer_residual_t<KK>(C, field, &g, st)));
+  MG_DISPATCH32(C.m.kind, (rc = launch_outer_residual_t<KK>(C, field, &g, st, bg_first)));
   if (rc) return rc;
   k_finalize_sum32<<<1, 1024, 0, st>>>(ws->partials, g, ws->scalars + SC_SUMSQ);
   note_launch(1);
@@ -733,12 +754,14 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
       note_launch(1);
     }
   }
-  if ((rc = launch_init_background(C.m, field, F.n3, st))) return rc;
+  // the background start (a NaN first element) is filled here, or inside the first residual
+  const bool fused_bg = fused_background_start(C);
+  if (!fused_bg && (rc = launch_init_background(C.m, field, F.n3, st))) return rc;
   MG_DISPATCH32(C.m.kind, (k_src_sumsq32<KK><<<g, kThreads, 0, st>>>(C.m, rho, n3, ws->scalars + SC_MEAN,
                                                                       ws->partials)));
   k_finalize_sum32<<<1, 1024, 0, st>>>(ws->partials, g, ws->scalars + SC_SRC);
   note_launch(1);
-  if ((rc = outer_residual(C, field, st))) return rc;
+  if ((rc = outer_residual(C, field, st, fused_bg))) return rc;
   MG_CUDA_TRY(cudaMemcpyAsync(ws->h_scalars, ws->scalars, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
   MG_CUDA_TRY(cudaStreamSynchronize(st));
   MG_CUDA_TRY(cudaGetLastError());
