@@ -615,31 +615,35 @@ __global__ void __launch_bounds__(256) k_background_residual_ff(const FFC* __res
   const FFC c = *C;
   const ff uc = ff_from_double(ubar);
   const float ubf = ff_to_float(uc);
-  const long long n3 = (long long)n * n * n;
-  const long long nb = (long long)gridDim.x * gridDim.y;
-  const long long b = blockIdx.x + (long long)blockIdx.y * gridDim.x;
+  const int nb = gridDim.x * gridDim.y;
+  const int b = blockIdx.x + blockIdx.y * gridDim.x;
+  const int rows = n * n;
+  const ff Kdu = ff_div(c.K, uc);              // f(R): K / ubar, the same in every cell
+  const ff ub3 = ff_mul(ff_sqr(uc), uc);       // symmetron: ubar^3
   float acc = 0.f;
-  for (long long t = b * blockDim.x + threadIdx.x; t < n3; t += nb * blockDim.x) {
-    if (t != 0) u[t] = ubar;
-    const float r = rho[t];
-    float tv;
-    if constexpr (is_fr(K)) {
-      ffacc v = acc_of(c.c0);
-      const ff p1 = two_prod(c.c1.hi, r);
-      acc_add(v, p1.hi, __fmaf_rn(c.c1.lo, r, p1.lo));
-      const ff q = ff_div(c.K, uc);
-      acc_add(v, -q.hi, -q.lo);
-      tv = -acc_float(v);
-    } else {
-      const ff a = ff_sub(ff_mul(ff_mul_f(c.c1, r), c.rat3), ff{1.f, 0.f});
-      const ff bb = ff_add(ff_mul(a, uc), ff_mul(ff_sqr(uc), uc));
-      tv = ff_to_float(ff_mul(c.msym, bb));
+  // rows (i, j) over the CTAs, k over the threads: one division per row
+  for (int row = b; row < rows; row += nb) {
+    const int i = row / n, j = row - i * n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const long long t = (long long)row * n + k;
+      if (t != 0) u[t] = ubar;
+      const float r = rho[t];
+      float tv;
+      if constexpr (is_fr(K)) {
+        ffacc v = acc_of(c.c0);
+        const ff p1 = two_prod(c.c1.hi, r);
+        acc_add(v, p1.hi, __fmaf_rn(c.c1.lo, r, p1.lo));
+        acc_add(v, -Kdu.hi, -Kdu.lo);
+        tv = -acc_float(v);
+      } else {
+        const ff a = ff_sub(ff_mul(ff_mul_f(c.c1, r), c.rat3), ff{1.f, 0.f});
+        tv = ff_to_float(ff_mul(c.msym, ff_add(ff_mul(a, uc), ub3)));
+      }
+      const long long o = SPLIT ? split_idx(n, i, j, k) : t;
+      ub[o] = ubf;
+      tau[o] = tv;
+      acc += tv * tv;
     }
-    const int k = (int)(t % n), j = (int)((t / n) % n), i = (int)(t / ((long long)n * n));
-    const long long o = SPLIT ? split_idx(n, i, j, k) : t;
-    ub[o] = ubf;
-    tau[o] = tv;
-    acc += tv * tv;
   }
   const double a = block_sum((double)acc);
   if (threadIdx.x == 0) partials[b] = a;
