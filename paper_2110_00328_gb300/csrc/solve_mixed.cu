@@ -228,12 +228,21 @@ __global__ void __launch_bounds__(128) k_prolong_correct32(int nc, const float* 
 // ---------------------------------------------------------------------------
 
 // u64 += e with e in the split layout.
+// Rows (i, j) over the CTAs; thread m adds the pair k = 2m, 2m+1, whose
+// corrections sit at the same index row h + m of the two colour halves.
 __global__ void k_apply_correction_split(double* __restrict__ u, const float* __restrict__ e, int n) {
-  const long long n3 = (long long)n * n * n;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(t % n), j = (int)((t / n) % n), i = (int)(t / ((long long)n * n));
-    u[t] += (double)e[split_idx(n, i, j, k)];
+  const int h = n >> 1, rows = n * n;
+  const long long H = (long long)n * n * h;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int i = row / n, j = row - i * n;
+    const long long c0 = ((i + j) & 1) ? H : 0;  // colour half of the even-k cells
+    double* ur = u + (long long)row * n;
+    const float* ev = e + c0 + (long long)row * h;
+    const float* od = e + (H - c0) + (long long)row * h;
+    for (int m = threadIdx.x; m < h; m += blockDim.x) {
+      ur[2 * m] += (double)ev[m];
+      ur[2 * m + 1] += (double)od[m];
+    }
   }
 }
 
@@ -795,7 +804,7 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
     for (int c = 0; c < inner && cyc < prm->max_cycles; ++c, ++cyc, ++done)
       if ((rc = vcycle32(C, 0, st, C.prm->cycle))) return rc;
     prof_begin(PC_APPLY_CORR, st, 20.0 * n3);
-    if (C.split) k_apply_correction_split<<<stream_grid(n3), kThreads, 0, st>>>(field, F.e, F.n);
+    if (C.split) k_apply_correction_split<<<kStreamBlocks, 128, 0, st>>>(field, F.e, F.n);
     else k_apply_correction<<<stream_grid(n3), kThreads, 0, st>>>(field, F.e, n3);
     note_launch(1);
     prof_end(st);
