@@ -18,6 +18,7 @@
 #include <mutex>
 
 #include "cic.cuh"
+#include "ff.cuh"
 #include "mg_common.cuh"
 #include "mg_internal.h"
 
@@ -158,20 +159,28 @@ int deposit_cic(const float* pos, long long np, int N, float* rho, cudaStream_t 
 // Gather
 // ---------------------------------------------------------------------------
 
-// T - Tbar per cell, formed in FP64 and stored in FP32.
+// T - Tbar per cell, stored in FP32.  f(R) and the symmetron form it in
+// float-float (FP32 instructions; the exact split of the FP64 field, v - ubar
+// exact to first order, ~48-bit products), which rounds to the same float as
+// FP64 would at 1/64 of FP32's rate; CQ (one product) stays in FP64.
 template <int K>
 __global__ void k_transform(const double* __restrict__ u, long long n3, double ubar, double beta,
                             float* __restrict__ T) {
+  const ff ub = ff_from_double(ubar);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
        t += (long long)gridDim.x * blockDim.x) {
-    const double v = u[t];
-    double d;
-    if constexpr (K == KFR0) d = -(v - ubar);
-    else if constexpr (K == KFR1) d = -(v - ubar) * (v + ubar);
-    else if constexpr (K == KFR2) d = -(v - ubar) * (v * v + v * ubar + ubar * ubar);
-    else if constexpr (K == KSYM) d = (v - ubar) * (v + ubar);
-    else d = beta * v;
-    T[t] = (float)d;
+    if constexpr (K == KCQ) {
+      T[t] = (float)(beta * u[t]);
+    } else {
+      const ff v = ff_from_double(u[t]);
+      const ff dv = ff_sub(v, ub);  // v - ubar
+      ff d;
+      if constexpr (K == KFR0) d = ff_neg(dv);
+      else if constexpr (K == KFR1) d = ff_neg(ff_mul(dv, ff_add(v, ub)));
+      else if constexpr (K == KFR2) d = ff_neg(ff_mul(dv, ff_add(ff_add(ff_sqr(v), ff_mul(v, ub)), ff_sqr(ub))));
+      else d = ff_mul(dv, ff_add(v, ub));  // symmetron: u^2 - ubar^2
+      T[t] = ff_to_float(d);
+    }
   }
 }
 

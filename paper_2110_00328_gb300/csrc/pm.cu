@@ -18,28 +18,37 @@
 #include <math.h>
 
 #include "cic.cuh"
+#include "ff.cuh"
 #include "mg_common.cuh"
 #include "mg_internal.h"
 
 namespace mg {
 
 // Psi = s5 (T - Tbar) - sN Phi_N in place over phi (FP64 field, FP32 Psi); the
-// transform T as in the gather (T - Tbar formed in FP64).
+// transform T as in the gather (k_transform: float-float for f(R) and the
+// symmetron, FP64 for CQ).
 template <int K, bool SCALAR>
 __global__ void k_pm_potential(const double* __restrict__ u, float* __restrict__ phi, long long n3, double ubar,
                                double beta, float s5, float sN) {
+  const ff ub = ff_from_double(ubar);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
        t += (long long)gridDim.x * blockDim.x) {
     float v = -sN * phi[t];
     if constexpr (SCALAR) {
-      const double w = u[t];
-      double d;
-      if constexpr (K == KFR0) d = -(w - ubar);
-      else if constexpr (K == KFR1) d = -(w - ubar) * (w + ubar);
-      else if constexpr (K == KFR2) d = -(w - ubar) * (w * w + w * ubar + ubar * ubar);
-      else if constexpr (K == KSYM) d = (w - ubar) * (w + ubar);
-      else d = beta * w;
-      v = fmaf(s5, (float)d, v);
+      float d;
+      if constexpr (K == KCQ) {
+        d = (float)(beta * u[t]);
+      } else {
+        const ff w = ff_from_double(u[t]);
+        const ff dw_ = ff_sub(w, ub);
+        ff T;
+        if constexpr (K == KFR0) T = ff_neg(dw_);
+        else if constexpr (K == KFR1) T = ff_neg(ff_mul(dw_, ff_add(w, ub)));
+        else if constexpr (K == KFR2) T = ff_neg(ff_mul(dw_, ff_add(ff_add(ff_sqr(w), ff_mul(w, ub)), ff_sqr(ub))));
+        else T = ff_mul(dw_, ff_add(w, ub));
+        d = ff_to_float(T);
+      }
+      v = fmaf(s5, d, v);
     }
     phi[t] = v;
   }
