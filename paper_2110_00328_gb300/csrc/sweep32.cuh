@@ -73,8 +73,9 @@ __device__ __forceinline__ float fsqrt_nn(float x) {
 // Newton polishing steps after the closed-form start of the local solve.  The
 // start inherits the single-precision cancellation in the polynomial's
 // coefficient p (-u^{n+1} + al K/u - B): in strongly screened cells its
-// relative error reaches ~1e-4, which two steps (error squared twice) remove;
-// with one step the mixed solve stalls near a 1e-10 relative residual.
+// relative error reaches ~1e-4, which two steps (error squared twice) remove.
+// With one step (or one Halley step) the mixed solve stalls: above 1e-8 on the
+// 256^3, |fR0| = 1e-6 workload, above 1e-11 on small meshes.
 constexpr int kPolishSteps = 2;
 
 // Delta w = (u+e)^{n+1} - u^{n+1}, factored so that small e loses nothing.
