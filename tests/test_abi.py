@@ -84,3 +84,41 @@ def test_binding_refuses_cpu_tensors(lib):
     field = torch.full((8, 8, 8), float("nan"), dtype=torch.float64)
     with pytest.raises(TypeError):
         binding.solve_scalar(binding.Params(), 1.0, rho, field, 1e-8)
+
+
+def test_pm_entry_points_reject_bad_arguments_before_device_work(lib):
+    """mgglam_poisson_fft and mgglam_pm_step check their arguments (NULL or aliased
+    buffers, mesh sides that are not powers of two in 8..1024, non-positive steps
+    or Hubble rates) and return before any device call."""
+    fake, fake2 = ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000)
+    lib.mgglam_poisson_fft.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                       ctypes.c_void_p]
+    assert lib.mgglam_poisson_fft(None, 32, 1.0, fake2, None) == -1
+    assert lib.mgglam_poisson_fft(fake, 32, 1.0, fake, None) == -1       # rho aliases phi
+    assert lib.mgglam_poisson_fft(fake, 32, float("nan"), fake2, None) == -1
+    for N in (4, 12, 96, 2048):
+        assert lib.mgglam_poisson_fft(fake, N, 1.0, fake2, None) == -2
+    lib.mgglam_pm_step.argtypes = [ctypes.POINTER(binding.CParams), ctypes.POINTER(binding.CPmStepDesc),
+                                   ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
+                                   ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.POINTER(binding.CStats), ctypes.c_void_p]
+    p = binding.Params().c()
+    st = binding.CStats()
+    ok = binding.CPmStepDesc(0.5, 0.01, 1.0, 1.0, 0.0, 1)
+
+    def call(desc=ok, N=32, pos=fake, mom=fake, np_=10, field=fake, tol=1e-8, rw=fake, pw=fake2, prm=p):
+        return lib.mgglam_pm_step(ctypes.byref(prm), ctypes.byref(desc) if desc is not None else None, N, pos, mom,
+                                  np_, field, tol, rw, pw, ctypes.byref(st), None)
+
+    assert call(desc=None) == -1
+    assert call(pos=None) == -1
+    assert call(np_=0) == -1
+    assert call(rw=fake2) == -1                    # rho_work aliases psi_work
+    assert call(field=None) == -1                  # a scalar step needs the field
+    assert call(tol=-1.0) == -1
+    assert call(desc=binding.CPmStepDesc(0.5, 0.0, 1.0, 1.0, 0.0, 1)) == -1     # da <= 0
+    assert call(desc=binding.CPmStepDesc(0.5, 0.01, -1.0, 1.0, 0.0, 1)) == -1   # E <= 0
+    assert call(desc=binding.CPmStepDesc(0.0, 0.01, 1.0, 1.0, 0.0, 1)) == -1    # a <= 0
+    for N in (4, 48, 2048):
+        assert call(N=N) == -2
+    assert call(prm=binding.Params(precision=9).c()) == -1
