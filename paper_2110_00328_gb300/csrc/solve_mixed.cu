@@ -66,7 +66,7 @@ template <int K, bool QS = false>
 __global__ void __launch_bounds__(128) k_smooth32s(LevelF f, int n, float* __restrict__ e,
                                                    const float* __restrict__ ub, const float* __restrict__ rho,
                                                    const float* __restrict__ S, int colour, int i0, int np,
-                                                   float* __restrict__ q) {
+                                                   float* __restrict__ q, int pdl) {
   const int lane = threadIdx.x;
   const long long warp = (long long)blockIdx.x * 4 + threadIdx.y;
   long long r;
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(128) k_smooth32s(LevelF f, int n, float* __res
   int i = i0 + (int)(pow2 ? r >> sh : r / n);
   if (i >= n) i -= n;
   const int j = (int)(pow2 ? r & (n - 1) : r % n);
-  smooth_split<K, QS>(f, n, e, ub, rho, S, i, j, seg, act, colour, lane, q);
+  smooth_split<K, QS>(f, n, e, ub, rho, S, i, j, seg, act, colour, lane, q, pdl);
 }
 
 // Quad version (levels with n % 4 == 0) on the planes i0 .. i0+np-1 (mod n):
@@ -332,6 +332,7 @@ static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
   const float* rho = C.need_rho ? L.rho32 : nullptr;
   const int tk = sweep_tile_k(L.n);
   const bool fused = use_fused(C, L.n);
+  int passes = 0;  // stored-q colour passes launched so far in this call
   for (int s = 0; s < sweeps; ++s) {
     if (fused && L.e_alt) {
       switch (tk) {
@@ -350,17 +351,30 @@ static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
         if (split) {
           const unsigned blocks = (unsigned)((split_warps(L.n, np) + 3) / 4);
           if (C.qs) {
+            // programmatic dependent launch: a pass overlaps its start with the
+            // previous pass's last wave (the first pass of the call waits first)
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(blocks);
+            cfg.blockDim = dim3(32, 4);
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            const int pdl = passes++ > 0 ? 1 : 2;
+            const float *ubc = L.ub, *Sc = L.S32, *no_rho = nullptr;
             if (C.m.kind == KFR1)
-              k_smooth32s<KFR1, true><<<blocks, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, nullptr, L.S32, parity,
-                                                                      i0, np, C.qs);
+              MG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_smooth32s<KFR1, true>, C.lf[l], L.n, L.e, ubc, no_rho, Sc, parity,
+                                             i0, np, C.qs, pdl));
             else
-              k_smooth32s<KFR2, true><<<blocks, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, nullptr, L.S32, parity,
-                                                                      i0, np, C.qs);
+              MG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_smooth32s<KFR2, true>, C.lf[l], L.n, L.e, ubc, no_rho, Sc, parity,
+                                             i0, np, C.qs, pdl));
             note_launch(1);
             return MGGLAM_OK;
           }
           MG_DISPATCH32(C.m.kind, (k_smooth32s<KK><<<blocks, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, rho,
-                                                                                   L.S32, parity, i0, np, nullptr)));
+                                                                                   L.S32, parity, i0, np, nullptr, 0)));
           return MGGLAM_OK;
         }
         const dim3 g((L.n / 4 + 31) / 32, L.n, (np + 3) / 4);

@@ -430,7 +430,7 @@ template <int K, bool QS = false>
 __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __restrict__ e,
                                              const float* __restrict__ ub, const float* __restrict__ rho,
                                              const float* __restrict__ S, int i, int j, int seg, bool act,
-                                             int colour, int lane, float* __restrict__ q = nullptr) {
+                                             int colour, int lane, float* __restrict__ q = nullptr, int pdl = 0) {
   constexpr bool FR = is_fr(K);
   static_assert(!QS || K == KFR1 || K == KFR2, "the stored neighbour quantity differs from e for f(R) n = 1, 2 only");
   constexpr bool RHO = (K == KSYM) || (K == KCQ);
@@ -449,8 +449,16 @@ __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __re
   const float* uo = ub + (long long)colour * H + r0;
   const float* u1 = ub + (long long)(colour ^ 1) * H + r0;
   if constexpr (QS) {
+    // pdl (programmatic dependent launch): 1 = the previous kernel is a colour
+    // pass, which writes only its own colour's e and q, so this colour's u and S
+    // (constant through the sweeps) are loaded before waiting for it; 2 = wait
+    // first.  The next pass may start only once every CTA here has waited, so
+    // when its own early loads run, every kernel before this one has finished.
     const float* q1 = q + (long long)(colour ^ 1) * H + r0;  // other colour's q
+    if (pdl == 2) asm volatile("griddepcontrol.wait;" ::: "memory");
     const float4 U = ld4(uo), Sv = ld4(S + (long long)colour * H + r0);
+    if (pdl == 1) asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (pdl) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const float4 Q = ld4(q1);
     const float4 Qjp = ld4(q1 + djp), Qjm = ld4(q1 + djm), Qip = ld4(q1 + dip), Qim = ld4(q1 + dim);
     float qm = __shfl_up_sync(0xffffffffu, Q.w, 1);
