@@ -57,8 +57,8 @@ def measured_peaks():
 # dram__bytes_write.sum of both colour launches from the ncu capture summarised
 # in profiles/k_smooth32s_fR256.md), valid while the kernel's sources hash to
 # the value recorded there.
-SMOOTHER_TRAFFIC = {"bytes_per_sweep": (100.944384 + 32.146432 + 100.946176 + 33.398528) * 1e6,
-                    "source_sha256_16": "e03e3f582b537012"}
+SMOOTHER_TRAFFIC = {"bytes_per_sweep": (100.953344 + 31.874560 + 100.946432 + 32.991488) * 1e6,
+                    "source_sha256_16": "b5f2d89a182fb1a7"}
 
 
 def smoother_traffic_per_sweep():

@@ -530,6 +530,30 @@ __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __re
   if (act) *reinterpret_cast<float4*>(eo) = out;
 }
 
+// Red-black split fine level (n % 8 == 0), one colour on the planes
+// i0 .. i0+np-1 (mod n): rows of n/8 lanes packed into warps (several short rows
+// per warp, a long row over several warps), four cells per lane; block (32, 4),
+// 1D grid over warps.
+// QS: f(R) n = 1, 2 with the neighbour quantity q stored beside e (smooth_split).
+template <int K, bool QS = false>
+__global__ void __launch_bounds__(128) k_smooth32s(LevelF f, int n, float* __restrict__ e,
+                                                   const float* __restrict__ ub, const float* __restrict__ rho,
+                                                   const float* __restrict__ S, int colour, int i0, int np,
+                                                   float* __restrict__ q, int pdl) {
+  const int lane = threadIdx.x;
+  const long long warp = (long long)blockIdx.x * 4 + threadIdx.y;
+  long long r;
+  int seg;
+  bool act;
+  split_lane(n, np, warp, lane, &r, &seg, &act);
+  const bool pow2 = (n & (n - 1)) == 0;
+  const int sh = __ffs(n) - 1;
+  int i = i0 + (int)(pow2 ? r >> sh : r / n);
+  if (i >= n) i -= n;
+  const int j = (int)(pow2 ? r & (n - 1) : r % n);
+  smooth_split<K, QS>(f, n, e, ub, rho, S, i, j, seg, act, colour, lane, q, pdl);
+}
+
 }  // namespace mg
 
 namespace mg {
