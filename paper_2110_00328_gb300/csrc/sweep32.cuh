@@ -215,6 +215,44 @@ __device__ __forceinline__ float update_e_fast(const LevelF& f, float u, float e
   }
 }
 
+// Largest Newton step, relative to the current total field u + e, from which
+// the warm-started update below finishes without the closed form.
+constexpr float kWarmStep = 1e-2f;
+
+// f(R) n = 1, 2 update started from the cell's current correction e.  The
+// local root is the zero of G(x) = Delta w(x) + al K x/(u(u+x)) - B, and
+// |G''| / (2 G') <= 1/(u+x) on the positive branch, so a Newton step from a
+// start that is eps (relative to u + x) from the root leaves at most eps^2.
+// When the first step of every lane of the warp is at most kWarmStep (u + e),
+// a second step leaves at most eps^4 <= 1e-8: an error of at most ~1e-6 of the
+// update itself, which shrinks with it as the iteration converges.  Otherwise
+// the warp takes the closed-form start and its polish (update_e_fast).  All 32
+// lanes of the warp call this together.
+template <int K>
+__device__ __forceinline__ float update_e_warm(const LevelF& f, float u, float e, float s, float Lnb) {
+  static_assert(K == KFR1 || K == KFR2, "warm start: f(R) n = 1, 2");
+  const float B = Lnb * (1.f / 6.f) + f.al * s;
+  const float ru = frcp(u);
+  auto newton = [&](float x, float* Ue_out) {
+    const float Ue = u + x;
+    const float rU = frcp(Ue);
+    const float G = dw<K>(u, x) + f.alK * x * ru * rU - B;
+    float dG = f.alK * rU * rU;
+    if constexpr (K == KFR1) dG += 2.f * Ue;
+    else dG += 3.f * Ue * Ue;
+    *Ue_out = Ue;
+    return fdiv(G, dG);
+  };
+  float Ue;
+  const float dx = newton(e, &Ue);
+  const bool near = Ue > 0.f && fabsf(dx) <= kWarmStep * Ue;
+  if (__all_sync(0xffffffffu, near)) {
+    const float x = e - dx;
+    return x - newton(x, &Ue);
+  }
+  return update_e_fast<K>(f, u, 0.f, 1.f, s, Lnb);
+}
+
 // ---------------------------------------------------------------------------
 // One colour of a red-black sweep, four consecutive cells per thread
 // ---------------------------------------------------------------------------
@@ -454,9 +492,11 @@ __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __re
     // (constant through the sweeps) are loaded before waiting for it; 2 = wait
     // first.  The next pass may start only once every CTA here has waited, so
     // when its own early loads run, every kernel before this one has finished.
+    // The colour's own e (the Newton start of update_e_warm) is written only by
+    // passes of this colour and by the prolongation, both finished by then.
     const float* q1 = q + (long long)(colour ^ 1) * H + r0;  // other colour's q
     if (pdl == 2) asm volatile("griddepcontrol.wait;" ::: "memory");
-    const float4 U = ld4(uo), Sv = ld4(S + (long long)colour * H + r0);
+    const float4 U = ld4(uo), Sv = ld4(S + (long long)colour * H + r0), E = ld4(eo);
     if (pdl == 1) asm volatile("griddepcontrol.wait;" ::: "memory");
     if (pdl) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const float4 Q = ld4(q1);
@@ -474,10 +514,10 @@ __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __re
     const float L2 = k2s + (Qjp.z + Qjm.z) + (Qip.z + Qim.z);
     const float L3 = k3s + (Qjp.w + Qjm.w) + (Qip.w + Qim.w);
     float4 out;
-    out.x = update_e_fast<K>(f, U.x, 0.f, 1.f, Sv.x, L0);
-    out.y = update_e_fast<K>(f, U.y, 0.f, 1.f, Sv.y, L1);
-    out.z = update_e_fast<K>(f, U.z, 0.f, 1.f, Sv.z, L2);
-    out.w = update_e_fast<K>(f, U.w, 0.f, 1.f, Sv.w, L3);
+    out.x = update_e_warm<K>(f, U.x, E.x, Sv.x, L0);
+    out.y = update_e_warm<K>(f, U.y, E.y, Sv.y, L1);
+    out.z = update_e_warm<K>(f, U.z, E.z, Sv.z, L2);
+    out.w = update_e_warm<K>(f, U.w, E.w, Sv.w, L3);
     if (act) {
       *reinterpret_cast<float4*>(eo) = out;
       *reinterpret_cast<float4*>(q + (long long)colour * H + r0) =
@@ -536,7 +576,7 @@ __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __re
 // 1D grid over warps.
 // QS: f(R) n = 1, 2 with the neighbour quantity q stored beside e (smooth_split).
 template <int K, bool QS = false>
-__global__ void __launch_bounds__(128) k_smooth32s(LevelF f, int n, float* __restrict__ e,
+__global__ void __launch_bounds__(128, QS ? 10 : 1) k_smooth32s(LevelF f, int n, float* __restrict__ e,
                                                    const float* __restrict__ ub, const float* __restrict__ rho,
                                                    const float* __restrict__ S, int colour, int i0, int np,
                                                    float* __restrict__ q, int pdl) {
