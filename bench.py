@@ -57,8 +57,8 @@ def measured_peaks():
 # dram__bytes_write.sum of both colour launches from the ncu capture summarised
 # in profiles/k_smooth32s_fR256.md), valid while the kernel's sources hash to
 # the value recorded there.
-SMOOTHER_TRAFFIC = {"bytes_per_sweep": (100.953344 + 31.874560 + 100.946432 + 32.991488) * 1e6,
-                    "source_sha256_16": "b5f2d89a182fb1a7"}
+SMOOTHER_TRAFFIC = {"bytes_per_sweep": (134.501632 + 31.328256 + 134.502656 + 32.583168) * 1e6,
+                    "source_sha256_16": "90d594f972119407"}
 
 
 def smoother_traffic_per_sweep():
