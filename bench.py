@@ -40,6 +40,12 @@ FR0 = 1e-6
 TOL = 1e-8
 SIGMA = 1.5
 WORKLOAD = "fR_HS_n1_fR0_1e-6_256cube_box256_zeldovich_sigma1.5_cic_tol1e-8"
+
+
+def workload_config() -> dict:
+    """The workload keys both arms' lines share."""
+    return {"workload": WORKLOAD, "N": N_MESH, "box_mpch": BOX, "fR0": FR0, "n": 1, "tol": TOL,
+            "particles": N_MESH ** 3}
 METRIC = "f(R) solve time-to-1e-8 residual at 256^3; Mcell-updates/s and % HBM peak"
 UNIT = "Mcell-updates/s"
 
@@ -214,7 +220,7 @@ def run_reference(args) -> None:
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "deposit + 1 V-cycle + gather"},
+            "data": "synthetic", "config": {**workload_config(), "sample": "deposit + 1 V-cycle + gather"},
             "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(),
                              "sample": "per step: CIC deposit, one FAS V-cycle, gather at 256^3", "value": value,
                              "unit": UNIT},
@@ -612,8 +618,7 @@ def run_ours(args) -> None:
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == mg.MIXED else "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N_MESH, "box_mpch": BOX, "fR0": FR0, "n": 1, "tol": TOL,
-                   "particles": npart, "precision": args.precision, "inner_cycles": args.inner_cycles, "sweep_chunk": args.chunk,
+        "config": {**workload_config(), "particles": npart, "precision": args.precision, "inner_cycles": args.inner_cycles, "sweep_chunk": args.chunk,
                    "nu1": prm.nu1, "nu2": prm.nu2, "coarse_sweeps": prm.coarse_sweeps, "tail_cells": prm.tail_cells, "cycle": args.cycle,
                    "levels": level_sizes(N_MESH),
                    "l2": "512 MB written between timed steps; positions (201 MB) exceed L2",
