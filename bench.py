@@ -59,10 +59,10 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-# DRAM bytes per fine-level sweep of the smoother (dram__bytes_read.sum +
-# dram__bytes_write.sum of both colour launches from the ncu capture summarised
-# in profiles/k_smooth32s_fR256.md), valid while the kernel's sources hash to
-# the value recorded there.
+# DRAM bytes per fine-level sweep of the smoother at 256^3: dram__bytes_read.sum +
+# dram__bytes_write.sum of both colour launches of a cycle-7 sweep (the warm
+# path), from one ncu capture; valid while the kernel's sources hash to the
+# value recorded with it.
 SMOOTHER_TRAFFIC = {"bytes_per_sweep": (134.501632 + 31.328256 + 134.502656 + 32.583168) * 1e6,
                     "source_sha256_16": "90d594f972119407"}
 

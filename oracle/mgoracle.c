@@ -36,7 +36,7 @@
  *  - CIC mass assignment and the three-point-difference force interpolated back
  *    to particles with the same CIC weights (Sec. 3.1).
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings taken where the paper leaves a point open:
  *  black cells are those with (i+j+k) even (0-based); the coarsest level is
  *  relaxed with a fixed number of sweeps; for f(R) a cell whose value is not
  *  positive after the coarse-grid correction is set to half its value before
