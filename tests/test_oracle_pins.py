@@ -5,24 +5,35 @@ sign, a wrong coefficient, a transposed index) with an independent reference:
 closed forms, the paper's manufactured solutions, FFT solutions of linear
 limits, library routines, brute force.
 """
+import json
+from pathlib import Path
+
 import numpy as np
 import pytest
 from scipy import ndimage
 
 from paper_2110_00328_gb300 import inputs
 
+# The parameters the paper prints for its code tests (Sec. 4.2), with citations.
+PAPER_TESTS = json.loads((Path(__file__).parent / "golden" / "paper_code_tests.json").read_text())
+UNIFORM = PAPER_TESTS["uniform_density_test"]
+SINE = PAPER_TESTS["sine_field_test"]
+
 C_OVER_H0 = 2997.92458  # c / (100 km/s/Mpc) in Mpc/h
 
 
 def fr_params(orc, **kw):
-    base = dict(model=orc.FR, n=1, fR0_abs=1e-5, omega_m=0.3, omega_l=0.7, box=64.0, a=1.0)
+    base = dict(model=orc.FR, n=UNIFORM["f(R)"]["n"], fR0_abs=abs(UNIFORM["f(R)"]["fR0"]), omega_m=0.3,
+                omega_l=0.7, box=64.0, a=1.0)
     base.update(kw)
     return orc.Params(**base)
 
 
 def sym_params(orc, **kw):
     # the homogeneous / sine tests of Sec. 4.2: a* = 0.5, xi = 1e-3, beta* = 0.1
-    base = dict(model=orc.SYMMETRON, a_star=0.5, xi=1e-3, beta_star=0.1, omega_m=0.3, box=256.0, a=1.0)
+    sp = UNIFORM["symmetron"]
+    base = dict(model=orc.SYMMETRON, a_star=sp["a_star"], xi=sp["xi"], beta_star=sp["beta_star"], omega_m=0.3,
+                box=256.0, a=1.0)
     base.update(kw)
     return orc.Params(**base)
 
@@ -161,17 +172,19 @@ def test_homogeneous_random_initial_guess_relaxes_to_background(orc, model):
         p = fr_params(orc, box=N * 0.5)
         ub = orc.background(p, N)["ubar"]
         # f_R / fbar_R uniform in [0, 2] -> u = ubar * ratio^{1/2} (n = 1); keep it positive
-        u0 = ub * np.sqrt(inputs.uniform_random_field(N, 0.01, 2.0, seed=5))
+        lo, hi = UNIFORM["f(R)"]["initial_guess_fR_over_fRbar"]
+        u0 = ub * np.sqrt(inputs.uniform_random_field(N, max(lo, 0.01), hi, seed=5))
         kind = orc.KIND_NONLINEAR
     elif model == "sym":
         p = sym_params(orc, box=float(N))
         ub = orc.background(p, N)["ubar"]
-        u0 = inputs.uniform_random_field(N, 0.01, 1.0, seed=6)
+        lo, hi = UNIFORM["symmetron"]["initial_guess_phi_over_phistar"]
+        u0 = inputs.uniform_random_field(N, max(lo, 0.01), hi, seed=6)
         kind = orc.KIND_NONLINEAR
     else:
         p = cq_params(orc, box=float(N))
         ub = 0.0
-        u0 = inputs.uniform_random_field(N, -0.5, 0.5, seed=7)
+        u0 = inputs.uniform_random_field(N, *UNIFORM["coupled_quintessence"]["initial_guess_c2_dphi"], seed=7)
         kind = orc.KIND_NEWTON
     r = orc.solve(p, rho, u0=u0, tol=0.0, max_cycles=60, kind=kind)
     if model == "cq":
@@ -181,19 +194,25 @@ def test_homogeneous_random_initial_guess_relaxes_to_background(orc, model):
         np.testing.assert_allclose(r.u, ub, rtol=1e-10)
 
 
+def test_golden_parameters_carry_their_citations():
+    for key in ("uniform_density_test", "sine_field_test"):
+        assert PAPER_TESTS[key]["citation"].startswith("Sec. 4.2")
+    assert 0 < SINE["A"] < 1  # |A| < 1 keeps f_R / fbar_R positive (Eq. sine_field_fR)
+
+
 # ---------------------------------------------------------------- 1D sine fields (Sec. 4.2.2)
 
 def _x_centres(N):
     return np.arange(N) + 0.5
 
 
-@pytest.mark.parametrize("n", [0, 1, 2])
+@pytest.mark.parametrize("n", SINE["f(R)"]["n"])
 def test_fr_sine_paper_density_gives_discretisation_residual(orc, n):
     """The paper's sine density (Eq. sine_field_fR and the delta printed below it)
     makes the discrete residual equal c^2 fbar_R A (k^2 - K_h^2) sin(kx), where
     K_h^2 = 4 sin^2(k/2) is the 7-point Laplacian's eigenvalue (exact identity)."""
-    N, A, a = 32, 0.5, 1.0
-    p = fr_params(orc, n=n, box=64.0)
+    N, A, a = 32, SINE["A"], 1.0
+    p = fr_params(orc, n=n, box=64.0, fR0_abs=abs(SINE["f(R)"]["fR0"]))
     b = orc.background(p, N)
     k = 2 * np.pi / N
     s = np.sin(k * _x_centres(N))[:, None, None] * np.ones((1, N, N))
@@ -206,8 +225,10 @@ def test_fr_sine_paper_density_gives_discretisation_residual(orc, n):
 
 
 def test_symmetron_sine_paper_density_gives_discretisation_residual(orc):
-    """Eq. sine_field_sym with the delta printed below it."""
-    N, A, a = 32, 0.25, 1.0
+    """Eq. sine_field_sym with the delta printed below it, at the paper's A = 0.5.
+    u = 1/2 + A sin(2 pi x/N) vanishes at x = 3N/4, between cell centres when
+    4 divides N, so the printed delta (which divides by u) is finite on the mesh."""
+    N, A, a = 32, SINE["A"], 1.0
     p = sym_params(orc, box=32.0)
     b = orc.background(p, N)
     k = 2 * np.pi / N
