@@ -39,7 +39,10 @@ def sym_params(orc, **kw):
 
 
 def cq_params(orc, **kw):
-    base = dict(model=orc.CQ, alpha=0.1, beta=-0.2, lam=1.0, phibar=0.5, omega_m=0.3, box=256.0, a=1.0)
+    # the homogeneous / sine / tophat tests of Sec. 4.2: alpha = 0.1, beta = -0.2
+    cp = UNIFORM["coupled_quintessence"]
+    base = dict(model=orc.CQ, alpha=cp["alpha"], beta=cp["beta"], lam=1.0, phibar=0.5, omega_m=0.3, box=256.0,
+                a=1.0)
     base.update(kw)
     return orc.Params(**base)
 
@@ -195,8 +198,12 @@ def test_homogeneous_random_initial_guess_relaxes_to_background(orc, model):
 
 
 def test_golden_parameters_carry_their_citations():
-    for key in ("uniform_density_test", "sine_field_test"):
+    for key in ("uniform_density_test", "sine_field_test", "tophat_test"):
         assert PAPER_TESTS[key]["citation"].startswith("Sec. 4.2")
+    # the CQ and symmetron parameters are the same in all three tests (Secs. 4.2.1-4.2.3)
+    for model in ("coupled_quintessence", "symmetron"):
+        for k, v in PAPER_TESTS["tophat_test"][model].items():
+            assert UNIFORM[model][k] == v
     assert 0 < SINE["A"] < 1  # |A| < 1 keeps f_R / fbar_R positive (Eq. sine_field_fR)
 
 
@@ -328,6 +335,58 @@ def test_cq_linear_regime_mass_from_potential(orc):
     r = orc.solve(p, rho, u0=np.zeros((N,) * 3), tol=1e-14, max_cycles=80, kind=orc.KIND_NEWTON)
     ref = fft_solve(lambda K2: -(K2 + m2), b["cq_src"] * A * g)
     assert np.abs(r.u - ref).max() < 1e-4 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------- branches the paper's tests leave out
+
+def test_cq_with_exp_factor_kept_recovers_manufactured_field(orc):
+    """Eq. csf_eom_code with exp(beta phi~/c~^2) kept in front of (1 + delta): the
+    density built from a chosen 3D field (tests/manufactured.py) is solved back by
+    Newton-Gauss-Seidel FAS cycles to 1e-10.  The same density solved with the
+    factor dropped (Sec. 3.2.3's simplification) lands ~1e-2 away, so a wrong sign
+    or a dropped factor in the kept branch cannot pass."""
+    import manufactured as mf
+    N = 16
+    kw, rho, phi = mf.cq_exp_kept(N, **{k: UNIFORM["coupled_quintessence"][k] for k in ("alpha", "beta")})
+    assert kw["keep_exp"] and abs(rho.mean() - 1) < 1e-14 and rho.min() > 0
+    p = cq_params(orc, **kw)
+    r = orc.solve(p, rho, u0=np.zeros((N,) * 3), tol=1e-14, max_cycles=60, kind=orc.KIND_NEWTON)
+    assert r.eps < 1e-13
+    assert np.abs(r.u - phi).max() < 1e-10 * np.abs(phi).max()
+    # the exact Jacobian (local_dN of the kept branch) gives textbook contraction
+    ratios = r.hist[2:6] / r.hist[1:5]
+    assert ratios.max() < 0.1
+    # dropping the factor changes the solution well above the tolerance
+    r0 = orc.solve(cq_params(orc, **{**kw, "keep_exp": False}), rho, u0=np.zeros((N,) * 3), tol=1e-14,
+                   max_cycles=60, kind=orc.KIND_NEWTON)
+    assert np.abs(r0.u - phi).max() > 1e-3 * np.abs(phi).max()
+
+
+def test_symmetron_domain_walls_recovered_from_their_sign_pattern(orc):
+    """A sign-changing symmetron field (two walls pinned by high density,
+    tests/manufactured.py) is an exact discrete solution and a strict local
+    minimum (m_eff > 0).  The oracle's root rule (the root with the sign opposite
+    to q, i.e. the sign of the neighbour sum on the finest level; reading C3)
+    keeps it: from a start with the walls' sign pattern (+-ubar) the FAS cycles
+    recover it to 1e-10, and the mirror -u likewise.  From the background (ubar
+    everywhere) the same density relaxes to a different exact solution, positive
+    everywhere: with both signs allowed the basin of the start decides."""
+    import manufactured as mf
+    N = 32
+    kw, rho, u, m_eff = mf.symmetron_domain_walls(N)
+    assert m_eff.min() > 0.05 and rho.min() > 0.2 and abs(rho.mean() - 1) < 1e-14
+    assert (u < 0).mean() == 0.5
+    p = orc.Params(model=orc.SYMMETRON, a=1.0, **kw)
+    ub = orc.background(p, N)["ubar"]
+    assert 0.3 < ub < 0.5  # a_* < a: the low-density regions are in the broken phase
+    for sgn in (1.0, -1.0):
+        r = orc.solve(p, rho, u0=sgn * np.sign(u) * ub, tol=1e-13, max_cycles=40)
+        assert r.eps < 1e-12
+        assert np.abs(r.u - sgn * u).max() < 1e-10 * np.abs(u).max()
+    rb = orc.solve(p, rho, tol=1e-13, max_cycles=40)
+    assert rb.eps < 1e-12 and rb.u.min() > 0
+    d = orc.residual(p, rb.u, rho)
+    assert np.abs(d).max() < 1e-6 * np.abs(orc.residual(p, np.full_like(u, ub), rho)).max()
 
 
 # ---------------------------------------------------------------- brute force
