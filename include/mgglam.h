@@ -162,25 +162,27 @@ int mgglam_deposit_cic_host(const float* pos_host, float* pos_dev, long long np,
  * for bit), for callers that must not trigger a device allocation.
  * mgglam_deposit_cic takes its accumulator from the library's scratch cache
  * and calls cudaMalloc the first time it sees a mesh size.  Some callers
- * cannot allow that: code that runs while a CUDA graph is being captured
- * (an allocation there fails or breaks the capture), applications that
- * hand all device memory to their own pool allocator and hold a fixed budget,
- * and loops that cannot absorb the implicit device synchronisation of
- * cudaMalloc.  This entry point allocates nothing.  Its accumulator is a fixed
- * device array compiled into the library, sized for meshes up to N = 128
- * (128^3 64-bit integers = 16 MiB); every GPU on which the library is used
- * holds that array until the process exits.
+ * cannot allow that: applications that hand all device memory to their own
+ * pool allocator and run inside a fixed budget (a foreign cudaMalloc can fail
+ * or push them over it), and time-stepping loops that cannot absorb the
+ * implicit device-wide synchronisation of cudaMalloc in the middle of a step.
+ * This entry point allocates nothing.  Its accumulator is a fixed device array
+ * compiled into the library, sized for meshes up to N = 128 (128^3 64-bit
+ * integers = 16 MiB); every GPU on which the library is loaded holds that
+ * array until the process exits.
  *   Arguments and layout as for mgglam_deposit_cic.
  *   N must satisfy 2 <= N <= 128; larger meshes return MGGLAM_ERR_SHAPE before
  *   any work is enqueued (use mgglam_deposit_cic for them).
  * The first call on each device looks up the array's device address (with
  * that device current) and caches it; make that first call before starting
- * any stream capture.  Each call clears the part of the array it uses before
- * accumulating, but all calls share the one array: calls that may run at the
- * same time on the GPU (different streams without ordering, or several host
- * threads) race and corrupt each other's results.
- * This entry point is an implementation convenience; the paper has no
- * counterpart.
+ * any stream capture.  mgglam_release() drops the cached address of the
+ * current device, so the next call looks it up again.  Each call clears the
+ * part of the array it uses before accumulating, but all calls share the one
+ * array: calls that may run at the same time on the GPU (different streams
+ * without ordering, or several host threads) race and corrupt each other's
+ * results.
+ * The paper has no counterpart to this entry point: it exists for callers
+ * that cannot allocate device memory.
  * Errors: MGGLAM_ERR_ARG (null pointer, np < 1), MGGLAM_ERR_SHAPE (N),
  * MGGLAM_ERR_CUDA.
  */
@@ -326,7 +328,8 @@ int mgglam_restrict(int n, const double* fine, double* coarse, void* stream);
 int mgglam_prolong_correct(const mgglam_params* prm, int n, const double* uH, const double* RuH,
                            double* u_fine, void* stream);
 
-/* Free every cached scratch allocation on the current device. */
+/* Free every cached scratch allocation on the current device (and forget the
+ * cached address of mgglam_deposit_cic_static's array there). */
 int mgglam_release(void);
 
 /* ---- Coupled-quintessence background (host code, once per parameter set) --

@@ -125,6 +125,7 @@ def load(path: str = LIB_PATH):
     lib.mgglam_status_string.argtypes = [i]
     lib.mgglam_default_params.argtypes = [P(CParams)]
     lib.mgglam_deposit_cic.argtypes = [vp, ll, i, vp, vp]
+    lib.mgglam_deposit_cic_static.argtypes = [vp, ll, i, vp, vp]
     lib.mgglam_solve_scalar.argtypes = [P(CParams), d, vp, i, vp, d, P(CStats), vp]
     lib.mgglam_gather_force.argtypes = [P(CParams), d, vp, i, vp, ll, vp, d, vp]
     lib.mgglam_smooth.argtypes = [P(CParams), d, i, d, vp, vp, vp, i, vp]
@@ -317,11 +318,6 @@ def deposit_cic_static(pos, N: int, rho=None, stream=None):
     """
     import torch
     lib = load()
-    if not hasattr(lib, "_static_bound"):
-        lib.mgglam_deposit_cic_static.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
-                                                  ctypes.c_void_p, ctypes.c_void_p]
-        lib.mgglam_deposit_cic_static.restype = ctypes.c_int
-        lib._static_bound = True
     if rho is None:
         rho = torch.empty((N, N, N), dtype=torch.float32, device=pos.device)
     _check("mgglam_deposit_cic_static", lib.mgglam_deposit_cic_static(_ptr(pos, torch.float32), pos.shape[0], N,

@@ -149,6 +149,7 @@ void release_batches();
 
 // ---- particles (particles.cu) ----
 int deposit_cic(const float* pos, long long np, int N, float* rho, cudaStream_t st);
+void forget_static_deposit_address();
 int gather_force(const ModelDev& m, int kind, int n_fr, const mgglam_params* prm,
                  const double* field, int N, const float* pos, long long np, float* force,
                  double prefactor, cudaStream_t st);

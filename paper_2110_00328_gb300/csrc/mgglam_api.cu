@@ -416,6 +416,7 @@ int mgglam_release(void) {
   release_fft_plans();
   release_adjoint_work();
   release_batches();
+  forget_static_deposit_address();
   return e == cudaSuccess ? MGGLAM_OK : MGGLAM_ERR_CUDA;
 }
 

@@ -358,7 +358,8 @@ int gather_force_host(const ModelDev& m, int kind, const mgglam_params* prm, con
 // scratch cache, so this entry point never calls cudaMalloc.  The array's name
 // is only a host-side stand-in in host code; the device address comes from
 // cudaGetSymbolAddress, looked up once per device (with that device current)
-// on the first call and cached.
+// on the first call and cached until mgglam_release runs on that device (a
+// reset device reloads the module, which may move the array).
 
 namespace mg {
 
@@ -390,6 +391,17 @@ static int static_deposit_scratch(unsigned long long** out) {
   }
   *out = g_static_acc_ptr[dev];
   return MGGLAM_OK;
+}
+
+void forget_static_deposit_address() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (dev < 0 || dev >= kStaticMaxDevices) return;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  g_static_acc_ptr[dev] = nullptr;
 }
 
 }  // namespace mg

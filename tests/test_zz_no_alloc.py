@@ -1,10 +1,10 @@
 """mgglam_deposit_cic_static: the CIC deposit that allocates no device memory.
 
-Some callers cannot let the library call cudaMalloc (code running during CUDA
-graph capture, applications whose device memory is owned by their own pool
-allocator, loops that cannot take cudaMalloc's implicit synchronisation).  For
-them the library offers a deposit whose accumulator is a fixed device array
-compiled into the library (meshes up to 128^3).  These tests call it through
+Some callers cannot let the library call cudaMalloc: applications whose
+device memory is owned by their own pool allocator under a fixed budget, and
+time-stepping loops that cannot take cudaMalloc's implicit device-wide
+synchronisation.  For them the library offers a deposit whose accumulator is a
+fixed device array compiled into the library (meshes up to 128^3).  These tests call it through
 the C-ABI and compare it with the regular mgglam_deposit_cic on two calls in a
 row: the second call must not see the first call's sums, since every call
 shares the one array.  This file is named so that pytest collects it last.
