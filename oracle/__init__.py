@@ -110,6 +110,8 @@ def lib():
         _lib.or_deposit_cic.argtypes = [fp, ll, i, dp]
         _lib.or_gather_force.argtypes = [P(CParams), i, dp, dp, fp, ll, d, dp]
         _lib.or_num_threads.restype = i
+        _lib.or_set_num_threads.argtypes = [i]
+        _lib.or_set_num_threads.restype = None
         _lib.or_local_root.argtypes = [i, i, d, d, d]
         _lib.or_local_root.restype = d
         _lib.or_cq_background.argtypes = [d, d, d, d, d, d, d, d, i, dp, dp, dp, dp]
@@ -265,6 +267,11 @@ def cq_background(alpha: float, beta: float, omega_m: float, omega_r: float, a: 
 
 def num_threads() -> int:
     return lib().or_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on (OpenMP)."""
+    lib().or_set_num_threads(int(n))
 
 
 # ---------------------------------------------------------------------------

@@ -619,6 +619,15 @@ int or_num_threads(void) {
 #endif
 }
 
+/* Set the number of threads of later parallel loops (no effect without OpenMP). */
+void or_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* Test export: the nonlinear Gauss-Seidel local root for given p, q. */
 double or_local_root(int model, int n, double pp, double qq, double u_old) {
   or_params p;
