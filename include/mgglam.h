@@ -259,11 +259,16 @@ int mgglam_gather_force_host(const mgglam_params* prm, double a, const double* f
  * transfers; the coarse-level coefficients are rebuilt from u* on each call, no
  * forward iterate is stored).  Then
  *   grad_rho[i] = dl/d delta_i = -(dN_i/d delta_i) lambda_i   (delta = rho/mean - 1)
+ *   grad_rho_raw[j] = dl/d rho_j for the rho passed in, through the solver's
+ *                mean-1 normalisation (Eq. code_units2's convention):
+ *                (grad_rho[j] - sum_i grad_rho[i] rho_i / sum_i rho_i) / mean(rho)
  *   *grad_logfR0 = dl/d ln|f_R0| = sum_i lambda_i K/((n+1) u_i)   (f(R); 0 otherwise)
  *   prm, a, rho, N   as passed to mgglam_solve_scalar (rho device float32)
  *   field            device, N^3 float64, the converged u*
  *   grad_field       device, N^3 float64, g = dl/du*
  *   grad_rho         device, N^3 float64 output
+ *   grad_rho_raw     device, N^3 float64 output, or NULL (not formed); must
+ *                    not alias grad_rho
  *   grad_logfR0      host, may be NULL
  *   tol              relative residual of the adjoint equation
  * Returns as mgglam_solve_scalar; MGGLAM_ERR_ARG for the CQ model (not supported).
@@ -271,8 +276,8 @@ int mgglam_gather_force_host(const mgglam_params* prm, double a, const double* f
  * through the solver (the paper's emulator motivation, Sec. 6).
  */
 int mgglam_solve_adjoint(const mgglam_params* prm, double a, const double* field, const float* rho, int N,
-                         const double* grad_field, double* grad_rho, double* grad_logfR0, double tol,
-                         mgglam_stats* stats, void* stream);
+                         const double* grad_field, double* grad_rho, double* grad_rho_raw, double* grad_logfR0,
+                         double tol, mgglam_stats* stats, void* stream);
 
 /*
  * Many independent solves at once (an emulator's parameter grid, several

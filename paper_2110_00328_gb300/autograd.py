@@ -2,10 +2,10 @@
 
 ``ScalarSolve.apply(rho, log_fR0, prm, a, tol)`` returns the converged field u*
 (mgglam_solve_scalar).  Its backward runs mgglam_solve_adjoint: the adjoint
-field lambda of J^T lambda = dl/du*, from which the gradients with respect to
-the density and ln|f_R0| follow; the mean-1 normalisation the solver applies to
-rho is differentiated here as well.  Only u* (and the density) is kept between
-forward and backward; the adjoint rebuilds its coarse levels from u*.
+field lambda of J^T lambda = dl/du*, from which the library forms the gradients
+with respect to the caller's density (through the solver's mean-1
+normalisation) and ln|f_R0|.  Only u* (and the density) is kept between forward
+and backward; the adjoint rebuilds its coarse levels from u*.
 
 ``fifth_force_power_loss`` is a loss of the kind used for emulators: the log of
 the binned power spectrum of the f(R) fifth force F = (c~^2/2) grad f_R on the
@@ -38,12 +38,9 @@ class ScalarSolve(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_field):
         rho, field = ctx.saved_tensors
-        g_n, g_theta, _ = binding.solve_adjoint(ctx.p, ctx.a, field, rho.contiguous(),
-                                                grad_field.contiguous().to(torch.float64), tol=ctx.tol * 0.1)
-        # rho_n = rho / mean(rho): d rho_n_i / d rho_j = delta_ij/mu - rho_i/(mu^2 N^3)
-        r = rho.to(torch.float64)
-        mu = r.mean()
-        g_rho = (g_n - (g_n * (r / mu)).mean()) / mu
+        g_rho, g_theta, _ = binding.solve_adjoint(ctx.p, ctx.a, field, rho.contiguous(),
+                                                  grad_field.contiguous().to(torch.float64), tol=ctx.tol * 0.1,
+                                                  raw=True)
         return g_rho.to(rho.dtype), torch.tensor(g_theta, dtype=torch.float64, device=rho.device), None, None, None
 
 

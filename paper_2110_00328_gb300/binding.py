@@ -137,6 +137,7 @@ def load(path: str = LIB_PATH):
     lib.mgglam_profile_stop.argtypes = [P(CKernelProfile), i, P(ctypes.c_int)]
     lib.mgglam_launch_count.restype = ll
     lib.mgglam_launch_count.argtypes = []
+    lib.mgglam_solve_adjoint.argtypes = [P(CParams), d, vp, vp, i, vp, vp, vp, P(ctypes.c_double), d, P(CStats), vp]
     for name in EXPORTS:
         getattr(lib, name).restype = getattr(lib, name).restype or i
     lib.mgglam_version.restype = ctypes.c_char_p
@@ -326,28 +327,26 @@ def deposit_cic_static(pos, N: int, rho=None, stream=None):
 
 
 def solve_adjoint(prm: Params, a: float, field, rho, grad_field, tol: float = 1e-10, stream=None,
-                  allow_unconverged=False):
-    """Adjoint solve: returns (grad_rho [N^3 float64], dl/d ln|fR0|, Stats)."""
+                  allow_unconverged=False, raw: bool = False):
+    """Adjoint solve: returns (grad_rho [N^3 float64], dl/d ln|fR0|, Stats).
+
+    grad_rho is dl/d delta; with raw=True it is dl/d rho for the rho passed in
+    (the library composes the mean-1 normalisation's Jacobian)."""
     import torch
     lib = load()
-    if not hasattr(lib, "_adjoint_bound"):
-        vp = ctypes.c_void_p
-        lib.mgglam_solve_adjoint.argtypes = [ctypes.POINTER(CParams), ctypes.c_double, vp, vp, ctypes.c_int, vp, vp,
-                                             ctypes.POINTER(ctypes.c_double), ctypes.c_double,
-                                             ctypes.POINTER(CStats), vp]
-        lib.mgglam_solve_adjoint.restype = ctypes.c_int
-        lib._adjoint_bound = True
     N = field.shape[0]
-    grad_rho = torch.empty_like(field)
+    grad_delta = torch.empty_like(field)
+    grad_raw = torch.empty_like(field) if raw else None
     gth = ctypes.c_double()
     st = CStats()
     rc = lib.mgglam_solve_adjoint(ctypes.byref(prm.c()), a, _ptr(field, torch.float64), _ptr(rho, torch.float32), N,
-                                  _ptr(grad_field, torch.float64), _ptr(grad_rho, torch.float64), ctypes.byref(gth),
+                                  _ptr(grad_field, torch.float64), _ptr(grad_delta, torch.float64),
+                                  _ptr(grad_raw, torch.float64) if raw else None, ctypes.byref(gth),
                                   tol, ctypes.byref(st), _stream(stream))
     _check("mgglam_solve_adjoint", rc, (0, -4) if allow_unconverged else (0,))
     nh = min(64, st.outer + 1)
-    return grad_rho, gth.value, Stats(st.cycles, st.outer, bool(st.converged), st.resid0, st.resid, st.seconds,
-                                      list(st.resid_hist[:nh]))
+    return (grad_raw if raw else grad_delta), gth.value, Stats(st.cycles, st.outer, bool(st.converged), st.resid0,
+                                                               st.resid, st.seconds, list(st.resid_hist[:nh]))
 
 
 def cq_background(alpha: float, beta: float, omega_m: float = 0.3, h: float = 0.6774, a: float = 1.0):

@@ -424,17 +424,34 @@ __global__ void k_adj_apply(long long n3, double* __restrict__ lam, const float*
     lam[t] += (double)e[t];
 }
 
+// Also partial sums of (dl/d delta_i) rho_i, the term the mean-1 normalisation
+// of the density adds to the gradient with respect to the caller's rho.
 __global__ void k_adj_outputs(long long n3, const double* __restrict__ lam, const double* __restrict__ gam,
-                              const double* __restrict__ tq, double* __restrict__ grad_rho,
-                              double* __restrict__ partials) {
-  double acc = 0.0;
+                              const double* __restrict__ tq, const float* __restrict__ rho32,
+                              double* __restrict__ grad_rho, double* __restrict__ partials,
+                              double* __restrict__ partials2) {
+  double acc = 0.0, acc2 = 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
        t += (long long)gridDim.x * blockDim.x) {
-    grad_rho[t] = gam[t] * lam[t];
+    const double g = gam[t] * lam[t];
+    grad_rho[t] = g;
     acc += lam[t] * tq[t];
+    acc2 += g * (double)rho32[t];
   }
   acc = block_sum(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  acc2 = block_sum(acc2);
+  if (threadIdx.x == 0) partials2[blockIdx.x] = acc2;
+}
+
+// Chain rule through delta = rho / mu - 1, mu = sum(rho) / N^3:
+//   dl/d rho_j = (dl/d delta_j - sum_i (dl/d delta_i) rho_i / sum(rho)) / mu.
+__global__ void k_adj_grad_raw(long long n3, const double* __restrict__ g, const double* __restrict__ dot,
+                               const double* __restrict__ rho_sum, double* __restrict__ out) {
+  const double S = *rho_sum, shift = *dot / S, inv_mu = (double)n3 / S;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
+       t += (long long)gridDim.x * blockDim.x)
+    out[t] = (g[t] - shift) * inv_mu;
 }
 
 // ---------------------------------------------------------------------------
@@ -579,8 +596,8 @@ static void adj_vcycle(AdjWork* w, int l, double kappa, const mgglam_params* prm
 }
 
 int solve_adjoint(const mgglam_params* prm, double a, const double* field, const float* rho, int N,
-                  const double* grad_field, double* grad_rho, double* grad_theta, double tol, mgglam_stats* stats,
-                  cudaStream_t st) {
+                  const double* grad_field, double* grad_rho, double* grad_rho_raw, double* grad_theta, double tol,
+                  mgglam_stats* stats, cudaStream_t st) {
   auto t0 = std::chrono::steady_clock::now();
   ModelDev m;
   int rc = make_model(prm, a, N, &m);
@@ -676,9 +693,14 @@ int solve_adjoint(const mgglam_params* prm, double a, const double* field, const
       rho_est = fmin(0.5, fmax(0.01, pow(eps / eps_before, 1.0 / done)));
   }
   const int go = grid_for(n3);
-  k_adj_outputs<<<go, kThreads, 0, st>>>(n3, w->lam, w->gam, w->tq, grad_rho, w->partials);
-  k_adj_finalize<<<1, 1024, 0, st>>>(w->partials, w->partials, go, w->scal);
+  k_adj_outputs<<<go, kThreads, 0, st>>>(n3, w->lam, w->gam, w->tq, rho, grad_rho, w->partials, w->partials2);
+  k_adj_finalize<<<1, 1024, 0, st>>>(w->partials, w->partials2, go, w->scal);
   note_launch(2);
+  if (grad_rho_raw) {
+    k_adj_grad_raw<<<stream_grid(n3), kThreads, 0, st>>>(n3, grad_rho, w->scal + 1, ws->scalars + SC_MEAN,
+                                                          grad_rho_raw);
+    note_launch(1);
+  }
   MG_CUDA_TRY(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
   MG_CUDA_TRY(cudaStreamSynchronize(st));
   MG_CUDA_TRY(cudaGetLastError());
@@ -696,11 +718,12 @@ int solve_adjoint(const mgglam_params* prm, double a, const double* field, const
 }  // namespace mg
 
 extern "C" int mgglam_solve_adjoint(const mgglam_params* prm, double a, const double* field, const float* rho,
-                                    int N, const double* grad_field, double* grad_rho, double* grad_logfR0,
-                                    double tol, mgglam_stats* stats, void* stream) {
+                                    int N, const double* grad_field, double* grad_rho, double* grad_rho_raw,
+                                    double* grad_logfR0, double tol, mgglam_stats* stats, void* stream) {
   if (!prm || !field || !rho || !grad_field || !grad_rho || !(tol >= 0.0)) return MGGLAM_ERR_ARG;
+  if (grad_rho_raw == grad_rho) return MGGLAM_ERR_ARG;
   if (N < 4 || N > 2048 || N % 2) return MGGLAM_ERR_SHAPE;
   if (prm->model != MGGLAM_FR && prm->model != MGGLAM_SYMMETRON) return MGGLAM_ERR_ARG;
-  return mg::solve_adjoint(prm, a, field, rho, N, grad_field, grad_rho, grad_logfR0, tol, stats,
+  return mg::solve_adjoint(prm, a, field, rho, N, grad_field, grad_rho, grad_rho_raw, grad_logfR0, tol, stats,
                            (cudaStream_t)stream);
 }

@@ -64,6 +64,29 @@ def test_oracle_adjoint_gradient_matches_solve_differences(orc, key):
         assert fdt == pytest.approx(gt, rel=1e-5)
 
 
+def test_normalisation_jacobian_matches_differences_in_the_raw_density(orc):
+    """The solver rescales any positive density to mean 1 (reading C12), so the
+    gradient with respect to the density as passed in is dl/d delta composed with
+    the Jacobian of rho -> rho/mean(rho): (g_j - sum_i g_i rho_i / sum rho)/mean.
+    Central differences of oracle solves along a direction that changes the mean
+    check that composition (the GPU's grad_rho_raw is compared with it)."""
+    N = 8
+    p, rho, u = solved(orc, "fr1", N)
+    rho = 1.7 * rho                     # a mean other than 1
+    rng = np.random.default_rng(4)
+    c = rng.normal(size=u.shape)
+    _, gd, _ = orc.adjoint(p, u, rho / rho.mean(), c)
+    mu = rho.mean()
+    g_raw = (gd - np.mean(gd * rho / mu)) / mu
+    loss = lambda rr: float(np.sum(c * orc.solve(p, rr, tol=1e-14, max_cycles=80).u))
+    v = rng.normal(size=u.shape) + 0.5  # mean 0.5: the mean density changes too
+    h = 1e-4
+    fd = (loss(rho + h * v) - loss(rho - h * v)) / (2 * h)
+    assert fd == pytest.approx(float(np.sum(g_raw * v)), rel=1e-5)
+    # a uniform rescaling of the density changes nothing
+    assert abs(float(np.sum(g_raw * rho))) <= 1e-10 * np.abs(g_raw).sum() * rho.max()
+
+
 # ---------------------------------------------------------------- GPU
 
 torch = pytest.importorskip("torch")
@@ -111,6 +134,14 @@ def _adjoint_case(orc, mg, key, N):
     assert np.linalg.norm(got - gd) <= 1e-8 * np.linalg.norm(gd)
     if key.startswith("fr"):
         assert gth == pytest.approx(gt, rel=1e-8)
+    # the gradient with respect to the caller's (unnormalised) density: the oracle's
+    # dl/d delta composed with the Jacobian of rho -> rho / mean(rho)
+    raw, _, _ = mg.solve_adjoint(pg, 1.0, torch.from_numpy(u).cuda(), torch.from_numpy(rho).cuda(),
+                                 torch.from_numpy(g).cuda(), tol=1e-12, raw=True)
+    r64 = rho.astype(np.float64)
+    mu = r64.mean()
+    ref_raw = (gd - np.mean(gd * r64 / mu)) / mu
+    assert np.linalg.norm(raw.cpu().numpy() - ref_raw) <= 1e-8 * np.linalg.norm(ref_raw)
 
 
 @pytest.mark.gpu
