@@ -108,7 +108,11 @@ typedef struct {
   int outer;                /* MIXED: FP64 defect-correction steps */
   int converged;            /* 1 if resid <= tol */
   int pad;
-  long long guarded;        /* reserved: positivity-guard replacements (not counted yet) */
+  long long guarded;        /* f(R): cells where the coarse-grid correction would have left the
+                               field not positive and the positivity guard replaced it (reading
+                               of Sec. 3.2.1's correction step: the value is set to half its
+                               value before the correction), summed over all levels and cycles
+                               (MIXED: over the inner FP32 cycles) */
   double resid0;            /* before the first cycle */
   double resid;             /* at return */
   double seconds;           /* host wall time of the call */

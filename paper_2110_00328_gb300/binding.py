@@ -95,6 +95,7 @@ class Stats:
     resid: float
     seconds: float
     hist: list = field(default_factory=list)
+    guarded: int = 0  # f(R) positivity-guard replacements
 
 
 _lib = None
@@ -138,6 +139,14 @@ def load(path: str = LIB_PATH):
     lib.mgglam_launch_count.restype = ll
     lib.mgglam_launch_count.argtypes = []
     lib.mgglam_solve_adjoint.argtypes = [P(CParams), d, vp, vp, i, vp, vp, vp, P(ctypes.c_double), d, P(CStats), vp]
+    lib.mgglam_solve_batch.argtypes = [i, P(CParams), P(d), P(vp), P(i), P(vp), d, P(CStats), vp]
+    lib.mgglam_deposit_cic_host.argtypes = [vp, vp, ll, i, vp, i, vp]
+    lib.mgglam_gather_force_host.argtypes = [P(CParams), d, vp, i, vp, ll, vp, vp, d, i, vp]
+    lib.mgglam_poisson_fft.argtypes = [vp, i, d, vp, vp]
+    lib.mgglam_pm_step.argtypes = [P(CParams), P(CPmStepDesc), i, vp, vp, ll, vp, d, vp, vp, P(CStats), vp]
+    lib.mgglam_cq_background.argtypes = [d, d, d, d, d, P(d), P(d), P(d), P(d)]
+    lib.mgglam_radiation_density.argtypes = [d]
+    lib.mgglam_radiation_density.restype = d
     for name in EXPORTS:
         getattr(lib, name).restype = getattr(lib, name).restype or i
     lib.mgglam_version.restype = ctypes.c_char_p
@@ -201,8 +210,6 @@ def deposit_cic_host(pos_host, pos_dev, N: int, rho=None, chunks: int = 8, strea
     if rho is None:
         rho = torch.empty((N, N, N), dtype=torch.float32, device=pos_dev.device)
     lib = load()
-    lib.mgglam_deposit_cic_host.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int,
-                                            ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
     _check("mgglam_deposit_cic_host",
            lib.mgglam_deposit_cic_host(ctypes.c_void_p(pos_host.data_ptr()), _ptr(pos_dev, torch.float32),
                                        pos_host.shape[0], N, _ptr(rho, torch.float32), chunks, _stream(stream)))
@@ -217,9 +224,6 @@ def gather_force_host(prm: Params, a: float, field, pos_dev, force_dev, force_ho
     if not (isinstance(force_host, torch.Tensor) and force_host.is_pinned()):
         raise TypeError("force_host must be a pinned host tensor")
     lib = load()
-    lib.mgglam_gather_force_host.argtypes = [ctypes.POINTER(CParams), ctypes.c_double, ctypes.c_void_p, ctypes.c_int,
-                                             ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
-                                             ctypes.c_double, ctypes.c_int, ctypes.c_void_p]
     _check("mgglam_gather_force_host",
            lib.mgglam_gather_force_host(ctypes.byref(prm.c()), a, _ptr(field, torch.float64), field.shape[0],
                                         _ptr(pos_dev, torch.float32), pos_dev.shape[0], _ptr(force_dev, torch.float32),
@@ -237,7 +241,7 @@ def solve_scalar(prm: Params, a: float, rho, field, tol: float, stream=None, all
     _check("mgglam_solve_scalar", rc, (0, -4) if allow_unconverged else (0,))
     nh = min(64, (st.outer if prm.precision == MIXED else st.cycles) + 1)
     return Stats(st.cycles, st.outer, bool(st.converged), st.resid0, st.resid, st.seconds,
-                 list(st.resid_hist[:nh]))
+                 list(st.resid_hist[:nh]), st.guarded)
 
 
 def gather_force(prm: Params, a: float, field, pos, prefactor: float = 1.0, force=None, stream=None):
@@ -374,8 +378,6 @@ def poisson_fft(rho, coef: float, phi=None, stream=None):
     if phi is None:
         phi = torch.empty_like(rho)
     lib = load()
-    lib.mgglam_poisson_fft.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
-                                       ctypes.c_void_p]
     _check("mgglam_poisson_fft", lib.mgglam_poisson_fft(_ptr(rho, torch.float32), N, coef,
                                                         _ptr(phi, torch.float32), _stream(stream)))
     return phi
@@ -405,10 +407,6 @@ def pm_step(prm: Params, a: float, da: float, pos, mom, rho_work, psi_work, fiel
     d = CPmStepDesc(a, da, E_a, E_half, dphibar_da, 1 if field is not None else 0)
     st = CStats()
     lib = load()
-    lib.mgglam_pm_step.argtypes = [ctypes.POINTER(CParams), ctypes.POINTER(CPmStepDesc), ctypes.c_int,
-                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
-                                   ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(CStats),
-                                   ctypes.c_void_p]
     rc = lib.mgglam_pm_step(ctypes.byref(prm.c()), ctypes.byref(d), N, _ptr(pos, torch.float32),
                             _ptr(mom, torch.float32), pos.shape[0],
                             _ptr(field, torch.float64) if field is not None else None, tol,
@@ -418,7 +416,8 @@ def pm_step(prm: Params, a: float, da: float, pos, mom, rho_work, psi_work, fiel
     if field is None:
         return None
     nh = min(64, (st.outer if prm.precision == MIXED else st.cycles) + 1)
-    return Stats(st.cycles, st.outer, bool(st.converged), st.resid0, st.resid, st.seconds, list(st.resid_hist[:nh]))
+    return Stats(st.cycles, st.outer, bool(st.converged), st.resid0, st.resid, st.seconds, list(st.resid_hist[:nh]),
+                 st.guarded)
 
 
 def solve_batch(prms, a_list, rhos, fields, tol: float, stream=None, allow_unconverged=False):
@@ -427,13 +426,6 @@ def solve_batch(prms, a_list, rhos, fields, tol: float, stream=None, allow_uncon
     Returns a list of Stats (one per solve)."""
     import torch
     lib = load()
-    if not hasattr(lib, "_batch_bound"):
-        vp = ctypes.c_void_p
-        lib.mgglam_solve_batch.argtypes = [ctypes.c_int, ctypes.POINTER(CParams), ctypes.POINTER(ctypes.c_double),
-                                           ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp),
-                                           ctypes.c_double, ctypes.POINTER(CStats), vp]
-        lib.mgglam_solve_batch.restype = ctypes.c_int
-        lib._batch_bound = True
     n = len(prms)
     cp = (CParams * n)(*[p.c() for p in prms])
     ca = (ctypes.c_double * n)(*a_list)
@@ -444,4 +436,4 @@ def solve_batch(prms, a_list, rhos, fields, tol: float, stream=None, allow_uncon
     rc = lib.mgglam_solve_batch(n, cp, ca, cr, cn, cf, tol, st, _stream(stream))
     _check("mgglam_solve_batch", rc, (0, -4) if allow_unconverged else (0,))
     return [Stats(s.cycles, s.outer, bool(s.converged), s.resid0, s.resid, s.seconds,
-                  list(s.resid_hist[:min(64, s.outer + 1)])) for s in st]
+                  list(s.resid_hist[:min(64, s.outer + 1)]), s.guarded) for s in st]

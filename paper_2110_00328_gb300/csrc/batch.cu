@@ -195,10 +195,11 @@ __global__ void __launch_bounds__(64) kb_fas(const BDesc* __restrict__ D, const 
 // only for the second colour when SO (post-smoothing follows).
 template <bool FR, int QK = -1, bool SO = false>
 __global__ void __launch_bounds__(128) kb_prolong(const BDesc* __restrict__ D, const int* __restrict__ prefix, int cnt,
-                                                  const int* __restrict__ active) {
+                                                  const int* __restrict__ active, unsigned long long* guards) {
   const int s = find_slot(prefix, cnt, blockIdx.x);
   const BDesc& d = D[s];
   if (!active[d.solve]) return;
+  unsigned long long* guard = guards + d.solve;
   const int nf = d.n, nc = nf >> 1;
   const int b = blockIdx.x - prefix[s];
   if (quad_level(nf)) {
@@ -208,12 +209,13 @@ __global__ void __launch_bounds__(128) kb_prolong(const BDesc* __restrict__ D, c
     if constexpr (QK >= 0) {
       if (d.split && d.q) {
         prolong_quad<FR, SplitLayout, QK, SO>(nc, d.eH, d.ReH, d.ub, d.e, i, j, xb * 32 + threadIdx.x, threadIdx.x,
-                                              d.q);
+                                              guard, d.q);
         return;
       }
     }
-    if (d.split) prolong_quad<FR, SplitLayout>(nc, d.eH, d.ReH, d.ub, d.e, i, j, xb * 32 + threadIdx.x, threadIdx.x);
-    else prolong_quad<FR>(nc, d.eH, d.ReH, d.ub, d.e, i, j, xb * 32 + threadIdx.x, threadIdx.x);
+    if (d.split)
+      prolong_quad<FR, SplitLayout>(nc, d.eH, d.ReH, d.ub, d.e, i, j, xb * 32 + threadIdx.x, threadIdx.x, guard);
+    else prolong_quad<FR>(nc, d.eH, d.ReH, d.ub, d.e, i, j, xb * 32 + threadIdx.x, threadIdx.x, guard);
     return;
   }
   const long long t = (long long)b * 128 + threadIdx.y * 32 + threadIdx.x;
@@ -231,7 +233,10 @@ __global__ void __launch_bounds__(128) kb_prolong(const BDesc* __restrict__ D, c
   const size_t o = cidx(nf, i, j, k);
   const float old = d.e[o];
   float v = old + corr;
-  if (FR && !(d.ub[o] + v > 0.f)) v = 0.5f * (old - d.ub[o]);
+  if (FR && !(d.ub[o] + v > 0.f)) {
+    v = 0.5f * (old - d.ub[o]);
+    count_guards(guard, 1u);
+  }
   d.e[o] = v;
 }
 
@@ -337,6 +342,8 @@ struct Batch {
   double* ssum = nullptr;      // per solve: source sum of squares
   double* rmean = nullptr;     // per solve: density sum
   int* active = nullptr;       // per solve flag (device)
+  unsigned long long* guards = nullptr;    // per solve: positivity-guard replacements (device)
+  unsigned long long* h_guards = nullptr;  // pinned host mirror
   int* h_active = nullptr;     // pinned host mirror
   double* h_sums = nullptr;    // pinned host mirror of sums (count) and ssum (count)
   void* tables = nullptr;      // descriptor tables and prefixes
@@ -359,6 +366,7 @@ static void free_batch(Batch* b) {
   if (b->base) cudaFree(b->base);
   if (b->h_active) cudaFreeHost(b->h_active);
   if (b->h_sums) cudaFreeHost(b->h_sums);
+  if (b->h_guards) cudaFreeHost(b->h_guards);
   delete b;
 }
 
@@ -415,13 +423,15 @@ static int get_batch(int count, const int* N, const mgglam_params* prm, Batch** 
   const size_t o_part = take(std::max<size_t>(total_blocks, kMaxReduceBlocks) * 8);
   const size_t o_sums = take(count * 8), o_ssum = take(count * 8), o_rmean = take(count * 8), o_act = take(count * 4);
   const size_t o_ffc = take(count * sizeof(FFC));
+  const size_t o_guard = take(count * sizeof(unsigned long long));
   if (cudaMalloc(&b->base, off) != cudaSuccess) {
     cudaGetLastError();
     delete b;
     return MGGLAM_ERR_OOM;
   }
   if (cudaMallocHost((void**)&b->h_active, count * 4) != cudaSuccess ||
-      cudaMallocHost((void**)&b->h_sums, count * 16) != cudaSuccess) {
+      cudaMallocHost((void**)&b->h_sums, count * 16) != cudaSuccess ||
+      cudaMallocHost((void**)&b->h_guards, count * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     free_batch(b);
     return MGGLAM_ERR_OOM;
@@ -446,6 +456,7 @@ static int get_batch(int count, const int* N, const mgglam_params* prm, Batch** 
   b->rmean = (double*)(base + o_rmean);
   b->active = (int*)(base + o_act);
   b->ffc = (FFC*)(base + o_ffc);
+  b->guards = (unsigned long long*)(base + o_guard);
   g_batches.push_back(b);
   *out = b;
   return MGGLAM_OK;
@@ -679,7 +690,8 @@ static void launch_smooth_phase(const Phase& ph, int rows, const int* active, in
 }
 
 // One V-cycle of every active solve.
-static void batch_vcycle(const Plan& P, const int* active, const mgglam_params& prm, int rows, cudaStream_t st) {
+static void batch_vcycle(const Plan& P, const int* active, unsigned long long* guards, const mgglam_params& prm,
+                         int rows, cudaStream_t st) {
   const int Lmax = (int)P.lv.size();
   for (int l = 0; l < Lmax; ++l) {
     const auto& L = P.lv[l];
@@ -703,12 +715,12 @@ static void batch_vcycle(const Plan& P, const int* active, const mgglam_params& 
       const Phase& p = L.prolong[g];
       const bool so = prm.nu2 >= 1;  // the same for every solve of the batch
       const dim3 b4(32, 4);
-      if (p.kind == KFR1 && so) kb_prolong<true, KFR1, true><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active);
-      else if (p.kind == KFR1) kb_prolong<true, KFR1><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active);
-      else if (p.kind == KFR2 && so) kb_prolong<true, KFR2, true><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active);
-      else if (p.kind == KFR2) kb_prolong<true, KFR2><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active);
-      else if (is_fr(p.kind)) kb_prolong<true><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active);
-      else kb_prolong<false><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active);
+      if (p.kind == KFR1 && so) kb_prolong<true, KFR1, true><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active, guards);
+      else if (p.kind == KFR1) kb_prolong<true, KFR1><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active, guards);
+      else if (p.kind == KFR2 && so) kb_prolong<true, KFR2, true><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active, guards);
+      else if (p.kind == KFR2) kb_prolong<true, KFR2><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active, guards);
+      else if (is_fr(p.kind)) kb_prolong<true><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active, guards);
+      else kb_prolong<false><<<p.blocks, b4, 0, st>>>(p.d, p.prefix, p.cnt, active, guards);
       note_launch(1);
       for (int s = 0; s < prm.nu2; ++s)
         for (int par = 0; par < 2; ++par) launch_smooth_phase(L.smooth[g], rows, active, par, st);
@@ -783,6 +795,7 @@ int solve_batch(int count, const mgglam_params* prm, const double* a, const floa
   };
   for (int s = 0; s < count; ++s) B->h_active[s] = 1;
   MG_CUDA_TRY(cudaMemcpyAsync(B->active, B->h_active, count * 4, cudaMemcpyHostToDevice, st));
+  MG_CUDA_TRY(cudaMemsetAsync(B->guards, 0, count * sizeof(unsigned long long), st));
   if ((rc = outer_residual())) return rc;
   // autotune the smoother's block height once per batch (timed on the fine
   // levels' sweeps, after the first residual has set the base field and source)
@@ -853,7 +866,7 @@ int solve_batch(int count, const mgglam_params* prm, const double* a, const floa
     cudaGraph_t g = nullptr;
     bool ok = cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
-      batch_vcycle(P, B->active, prm[0], B->rows, B->cap);
+      batch_vcycle(P, B->active, B->guards, prm[0], B->rows, B->cap);
       ok = cudaStreamEndCapture(B->cap, &g) == cudaSuccess && g;
     }
     B->vlaunches = launch_count() - n0;
@@ -918,8 +931,12 @@ int solve_batch(int count, const mgglam_params* prm, const double* a, const floa
     if (done > 0 && worst_after > 0.0 && worst_after < worst_before && worst_after / worst_before > kFp32StepGain)
       rho_est = fmin(0.5, fmax(0.01, pow(worst_after / worst_before, 1.0 / done)));
   }
+  MG_CUDA_TRY(cudaMemcpyAsync(B->h_guards, B->guards, count * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                              st));
+  MG_CUDA_TRY(cudaStreamSynchronize(st));
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   for (int s = 0; s < count; ++s) {
+    lst[s].guarded = (long long)B->h_guards[s];
     lst[s].resid = eps[s];
     lst[s].converged = eps[s] <= tol;
     lst[s].seconds = secs;

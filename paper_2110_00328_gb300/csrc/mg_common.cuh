@@ -37,6 +37,13 @@ __device__ __forceinline__ double block_sum(double v) {
   return v;
 }
 
+// Positivity-guard replacements (reading C11): each thread adds its own count to
+// the solve's counter (a 64-bit integer in the workspace scalars); the guard is
+// rare, so the atomic is almost never issued.  guard may be null (not counted).
+__device__ __forceinline__ void count_guards(unsigned long long* guard, unsigned c) {
+  if (c && guard) atomicAdd(guard, (unsigned long long)c);
+}
+
 // Grid for a grid-stride loop over 'work' items, capped so that partial sums fit.
 inline int grid_for(long long work, int threads = kThreads, int cap = kMaxReduceBlocks) {
   long long g = (work + threads - 1) / threads;

@@ -74,7 +74,11 @@ struct Workspace {
 
 // Slots of Workspace::scalars.
 // SC_FFC: start of the float-float residual constants (48 bytes, mixed path).
-enum Scalar { SC_MEAN = 0, SC_SUMSQ = 1, SC_SRC = 2, SC_FLAG = 3, SC_FFC = 8, SC_COUNT = 16 };
+// SC_GUARD holds a 64-bit integer: the positivity-guard replacements of the running solve.
+enum Scalar { SC_MEAN = 0, SC_SUMSQ = 1, SC_SRC = 2, SC_FLAG = 3, SC_GUARD = 4, SC_FFC = 8, SC_COUNT = 16 };
+inline unsigned long long* guard_of(Workspace* ws) {
+  return reinterpret_cast<unsigned long long*>(ws->scalars + SC_GUARD);
+}
 
 int count_levels(int N, int levels);
 
@@ -102,7 +106,7 @@ int launch_residual64(const ModelDev& m, int n, double h, const double* u, const
                       const double* S, double* d, double* partials, double* out_sum,
                       cudaStream_t st);
 int launch_restrict64(int nf, const double* fine, double* coarse, cudaStream_t st);
-int launch_prolong_correct64(const ModelDev& m, int nc, const double* uH, const double* RuH,
+int launch_prolong_correct64(const ModelDev& m, int nc, const double* uH, const double* RuH, unsigned long long* guard,
                              double* uf, cudaStream_t st);
 int launch_coarse64(const ModelDev& m, int n, double h, double* u, const double* rho,
                     const double* S, int sweeps, cudaStream_t st);

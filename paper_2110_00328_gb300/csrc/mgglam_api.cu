@@ -389,7 +389,7 @@ int mgglam_prolong_correct(const mgglam_params* prm, int n, const double* uH, co
   ModelDev m;
   memset(&m, 0, sizeof(m));
   m.kind = prm->model == MGGLAM_FR ? KFR1 : (prm->model == MGGLAM_SYMMETRON ? KSYM : KCQ);
-  return launch_prolong_correct64(m, n / 2, uH, RuH, u_fine, (cudaStream_t)stream);
+  return launch_prolong_correct64(m, n / 2, uH, RuH, nullptr, u_fine, (cudaStream_t)stream);
 }
 
 int mgglam_poisson_fft(const float* rho, int N, double coef, float* phi, void* stream) {

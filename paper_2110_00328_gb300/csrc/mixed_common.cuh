@@ -270,7 +270,8 @@ __device__ __forceinline__ void fas_quad(const LevelF& f, int n, const float* __
 template <bool FR, class FL = NatLayout, int QK = -1, bool SECOND_ONLY = false>
 __device__ __forceinline__ void prolong_quad(int nc, const float* __restrict__ eH, const float* __restrict__ Re,
                                              const float* __restrict__ ub, float* __restrict__ ef, int i, int j,
-                                             int tq, int lane, float* __restrict__ qf = nullptr) {
+                                             int tq, int lane, unsigned long long* guard,
+                                             float* __restrict__ qf = nullptr) {
   static_assert(QK < 0 || (FR && QK != KFR0), "stored q: f(R) n = 1, 2");
   static_assert(!SECOND_ONLY || QK >= 0, "second-colour-only prolongation: split layout with stored q");
   const int nf = nc << 1, nq = nf >> 2;
@@ -312,8 +313,10 @@ __device__ __forceinline__ void prolong_quad(int nc, const float* __restrict__ e
     const long long o1 = (long long)nf * nf * h + ((long long)i * nf + j) * h + (k0 >> 1);
     const float2 old = ld2(ef + o1), u = ld2(ub + o1);
     float vA = old.x + cA, vB = old.y + cB;
-    if (!(u.x + vA > 0.f)) vA = 0.5f * (old.x - u.x);
-    if (!(u.y + vB > 0.f)) vB = 0.5f * (old.y - u.y);
+    const bool gA = !(u.x + vA > 0.f), gB = !(u.y + vB > 0.f);
+    if (gA) vA = 0.5f * (old.x - u.x);
+    if (gB) vB = 0.5f * (old.y - u.y);
+    if (act) count_guards(guard, (unsigned)gA + (unsigned)gB);
     if (act) {
       *reinterpret_cast<float2*>(ef + o1) = make_float2(vA, vB);
       *reinterpret_cast<float2*>(qf + o1) = make_float2(dw<QK>(u.x, vA), dw<QK>(u.y, vB));
@@ -326,10 +329,13 @@ __device__ __forceinline__ void prolong_quad(int nc, const float* __restrict__ e
   float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
   if constexpr (FR) {
     u = FL::q(ub, nf, i, j, k0);
-    if (!(u.x + v.x > 0.f)) v.x = 0.5f * (old.x - u.x);
-    if (!(u.y + v.y > 0.f)) v.y = 0.5f * (old.y - u.y);
-    if (!(u.z + v.z > 0.f)) v.z = 0.5f * (old.z - u.z);
-    if (!(u.w + v.w > 0.f)) v.w = 0.5f * (old.w - u.w);
+    const bool gx = !(u.x + v.x > 0.f), gy = !(u.y + v.y > 0.f), gz = !(u.z + v.z > 0.f),
+               gw = !(u.w + v.w > 0.f);
+    if (gx) v.x = 0.5f * (old.x - u.x);
+    if (gy) v.y = 0.5f * (old.y - u.y);
+    if (gz) v.z = 0.5f * (old.z - u.z);
+    if (gw) v.w = 0.5f * (old.w - u.w);
+    if (act) count_guards(guard, (unsigned)gx + (unsigned)gy + (unsigned)gz + (unsigned)gw);
   }
   if (act) FL::st(ef, nf, i, j, k0, v);
   if constexpr (QK >= 0) {

@@ -199,7 +199,8 @@ __device__ __forceinline__ double prolong_at64(const double* __restrict__ c, int
 template <bool FR>
 __global__ void __launch_bounds__(kThreads) k_prolong_correct64(int nc, const double* __restrict__ uH,
                                                                 const double* __restrict__ RuH,
-                                                                double* __restrict__ uf) {
+                                                                double* __restrict__ uf,
+                                                                unsigned long long* guard) {
   const int nf = nc << 1;
   const int i = blockIdx.z, j = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -216,7 +217,10 @@ __global__ void __launch_bounds__(kThreads) k_prolong_correct64(int nc, const do
 #undef EH
     const double old = uf[t];
     double v = old + corr;
-    if (FR && !(v > 0.0)) v = 0.5 * old;
+    if (FR && !(v > 0.0)) {
+      v = 0.5 * old;
+      count_guards(guard, 1u);
+    }
     uf[t] = v;
   }
 }
@@ -335,12 +339,12 @@ int launch_restrict64(int nf, const double* fine, double* coarse, cudaStream_t s
   return MGGLAM_OK;
 }
 
-int launch_prolong_correct64(const ModelDev& m, int nc, const double* uH, const double* RuH, double* uf,
-                             cudaStream_t st) {
+int launch_prolong_correct64(const ModelDev& m, int nc, const double* uH, const double* RuH,
+                             unsigned long long* guard, double* uf, cudaStream_t st) {
   const long long nf3 = 8LL * nc * nc * nc;
   const dim3 g = grid3d(2 * nc, 2 * nc, 2 * nc);
-  if (is_fr(m.kind)) k_prolong_correct64<true><<<g, k3dThreads, 0, st>>>(nc, uH, RuH, uf);
-  else k_prolong_correct64<false><<<g, k3dThreads, 0, st>>>(nc, uH, RuH, uf);
+  if (is_fr(m.kind)) k_prolong_correct64<true><<<g, k3dThreads, 0, st>>>(nc, uH, RuH, uf, guard);
+  else k_prolong_correct64<false><<<g, k3dThreads, 0, st>>>(nc, uH, RuH, uf, guard);
   note_launch(1);
   MG_CUDA_TRY(cudaGetLastError());
   return MGGLAM_OK;
@@ -429,7 +433,7 @@ static int vcycle64(const ModelDev& m, Workspace* ws, int l, const mgglam_params
   if ((rc = vcycle64(m, ws, l + 1, prm, st, mode))) return rc;
   if (mode != 0 && (rc = vcycle64(m, ws, l + 1, prm, st, mode == 2 ? 2 : 0))) return rc;
   if (l == 0) { prof_end(st); prof_begin(PC_PROLONG64_FINE, st, (16.0 + 2.0) * L.n3); }
-  if ((rc = launch_prolong_correct64(m, C.n, C.u, C.Ru, L.u, st))) return rc;
+  if ((rc = launch_prolong_correct64(m, C.n, C.u, C.Ru, guard_of(ws), L.u, st))) return rc;
   if (l == 0) { prof_end(st); prof_begin(PC_SMOOTH64_FINE, st, 24.0 * L.n3 * prm->nu2); }
   rc = launch_smooth64(m, L.n, L.h, L.u, L.rho, L.S, prm->nu2, st);
   if (l == 0) prof_end(st);
@@ -453,6 +457,7 @@ int solve_fp64(const mgglam_params* prm, double a, const float* rho, int N, doub
   for (int l = 1; l < ws->nlev; ++l)
     if ((rc = launch_restrict64(ws->lev[l - 1].n, ws->lev[l - 1].rho, ws->lev[l].rho, st))) return rc;
   if ((rc = launch_init_background(m, field, n3, st))) return rc;
+  MG_CUDA_TRY(cudaMemsetAsync(guard_of(ws), 0, sizeof(unsigned long long), st));
   if ((rc = launch_src_sumsq(m, F.rho, n3, ws->partials, ws->scalars + SC_SRC, st))) return rc;
   if ((rc = launch_residual64(m, F.n, F.h, field, F.rho, nullptr, nullptr, ws->partials,
                               ws->scalars + SC_SUMSQ, st)))
@@ -486,6 +491,10 @@ int solve_fp64(const mgglam_params* prm, double a, const float* rho, int N, doub
     }
   }
   if (status == MGGLAM_OK && !isfinite(eps)) status = MGGLAM_ERR_NONFINITE;
+  MG_CUDA_TRY(cudaMemcpyAsync(ws->h_scalars + SC_GUARD, guard_of(ws), sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, st));
+  MG_CUDA_TRY(cudaStreamSynchronize(st));
+  S->guarded = (long long)*reinterpret_cast<const unsigned long long*>(ws->h_scalars + SC_GUARD);
   S->cycles = cyc;
   S->resid = eps;
   S->converged = eps <= tol;

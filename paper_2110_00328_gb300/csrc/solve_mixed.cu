@@ -146,9 +146,10 @@ template <bool FR, class FL = NatLayout, int QK = -1, bool SECOND_ONLY = false>
 __global__ void __launch_bounds__(128) k_prolong_correct32q(int nc, const float* __restrict__ eH,
                                                             const float* __restrict__ Re,
                                                             const float* __restrict__ ub, float* __restrict__ ef,
+                                                            unsigned long long* guard,
                                                             float* __restrict__ qf = nullptr) {
   prolong_quad<FR, FL, QK, SECOND_ONLY>(nc, eH, Re, ub, ef, blockIdx.z * 4 + threadIdx.y, blockIdx.y,
-                                        blockIdx.x * 32 + threadIdx.x, threadIdx.x, qf);
+                                        blockIdx.x * 32 + threadIdx.x, threadIdx.x, guard, qf);
 }
 
 // FAS source, four cells per lane (n % 4 == 0, n >= 8): grid (ceil(n/128), n, n/4).
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(128) k_fas_source32(LevelF f, int n, const flo
 template <bool FR>
 __global__ void __launch_bounds__(128) k_prolong_correct32(int nc, const float* __restrict__ eH,
                                                            const float* __restrict__ Re, const float* __restrict__ ub,
-                                                           float* __restrict__ ef) {
+                                                           float* __restrict__ ef, unsigned long long* guard) {
   const int nf = nc << 1;
   const int i = blockIdx.z, j = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -194,7 +195,10 @@ __global__ void __launch_bounds__(128) k_prolong_correct32(int nc, const float* 
   const size_t t = cidx(nf, i, j, k);
   const float old = ef[t];
   float v = old + corr;
-  if (FR && !(ub[t] + v > 0.f)) v = 0.5f * (old - ub[t]);
+  if (FR && !(ub[t] + v > 0.f)) {
+    v = 0.5f * (old - ub[t]);
+    count_guards(guard, 1u);
+  }
   ef[t] = v;
 }
 
@@ -261,6 +265,7 @@ struct MixedCtx {
   bool ff_resid;      // fine residual in float-float (f(R), symmetron) rather than FP64 (CQ)
   int tail_level;     // first level (>= 1) run by the one-block tail kernel, or -1
   float* qs;          // split f(R) n = 1, 2: the finest level's stored neighbour quantity, else nullptr
+  unsigned long long* guard;  // positivity-guard replacements of this solve (workspace scalar)
 };
 
 static FFC* ffc_of(Workspace* ws) { return reinterpret_cast<FFC*>(ws->scalars + SC_FFC); }
@@ -499,6 +504,7 @@ static int launch_tail(const MixedCtx& C, int l, cudaStream_t st) {
   A.nu1 = C.prm->nu1;
   A.nu2 = C.prm->nu2;
   A.coarse_sweeps = C.prm->coarse_sweeps;
+  A.guard = C.guard;
   MG_DISPATCH32(C.m.kind, (launch_tail_t<KK>(A, st)));
   return MGGLAM_OK;
 }
@@ -572,24 +578,28 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode) {
     // with post-smoothing the first colour's corrections would be overwritten unread (prolong_quad)
     const bool second_only = C.prm->nu2 >= 1;
     if (C.qs && C.m.kind == KFR1 && second_only)
-      k_prolong_correct32q<true, SplitLayout, KFR1, true><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.qs);
+      k_prolong_correct32q<true, SplitLayout, KFR1, true><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e,
+                                                                                      C.guard, C.qs);
     else if (C.qs && C.m.kind == KFR1)
-      k_prolong_correct32q<true, SplitLayout, KFR1><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.qs);
+      k_prolong_correct32q<true, SplitLayout, KFR1><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard,
+                                                                                C.qs);
     else if (C.qs && second_only)
-      k_prolong_correct32q<true, SplitLayout, KFR2, true><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.qs);
+      k_prolong_correct32q<true, SplitLayout, KFR2, true><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e,
+                                                                                      C.guard, C.qs);
     else if (C.qs)
-      k_prolong_correct32q<true, SplitLayout, KFR2><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.qs);
+      k_prolong_correct32q<true, SplitLayout, KFR2><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard,
+                                                                                C.qs);
     else if (is_fr(C.m.kind))
-      k_prolong_correct32q<true, SplitLayout><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
-    else k_prolong_correct32q<false, SplitLayout><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
+      k_prolong_correct32q<true, SplitLayout><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard);
+    else k_prolong_correct32q<false, SplitLayout><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard);
   } else if (L.n % 4 == 0 && L.n >= 8) {
     const dim3 g((L.n / 4 + 31) / 32, L.n, L.n / 4);
-    if (is_fr(C.m.kind)) k_prolong_correct32q<true><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
-    else k_prolong_correct32q<false><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
+    if (is_fr(C.m.kind)) k_prolong_correct32q<true><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard);
+    else k_prolong_correct32q<false><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard);
   } else if (is_fr(C.m.kind)) {
-    k_prolong_correct32<true><<<grid3(L.n, L.n, L.n, bf), bf, 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
+    k_prolong_correct32<true><<<grid3(L.n, L.n, L.n, bf), bf, 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard);
   } else {
-    k_prolong_correct32<false><<<grid3(L.n, L.n, L.n, bf), bf, 0, st>>>(H.n, H.e, H.Re, L.ub, L.e);
+    k_prolong_correct32<false><<<grid3(L.n, L.n, L.n, bf), bf, 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard);
   }
   note_launch(1);
   if (l == 0) { prof_end(st); prof_begin(PC_SMOOTH32_FINE, st, 16.0 * L.n3 * C.prm->nu2); }
@@ -716,6 +726,7 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
   C.split = C.ff_resid && prm->sweep_chunk <= 0 && C.ws->lev[0].n % 32 == 0;
   // the split level never runs the fused sweep, so its second buffer holds q
   C.qs = C.split && (C.m.kind == KFR1 || C.m.kind == KFR2) ? C.ws->lev[0].e_alt : nullptr;
+  C.guard = guard_of(C.ws);
   C.tail_level = -1;  // the one-block tail runs V-cycles only
   const long long tail_cells = prm->tail_cells == 0 ? 512 : (prm->tail_cells > kTailMaxCells ? kTailMaxCells : prm->tail_cells);
   for (int l = 1; l < C.ws->nlev && tail_cells > 0 && prm->cycle == 0; ++l)
@@ -756,6 +767,7 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
   // the background start (a NaN first element) is filled here, or inside the first residual
   const bool fused_bg = fused_background_start(C);
   if (!fused_bg && (rc = launch_init_background(C.m, field, F.n3, st))) return rc;
+  MG_CUDA_TRY(cudaMemsetAsync(C.guard, 0, sizeof(unsigned long long), st));
   MG_DISPATCH32(C.m.kind, (k_src_sumsq32<KK><<<g, kThreads, 0, st>>>(C.m, rho, n3, ws->scalars + SC_MEAN,
                                                                       ws->partials)));
   k_finalize_sum32<<<1, 1024, 0, st>>>(ws->partials, g, ws->scalars + SC_SRC);
@@ -813,6 +825,10 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
     }
   }
   if (status == MGGLAM_OK && !isfinite(eps)) status = MGGLAM_ERR_NONFINITE;
+  MG_CUDA_TRY(cudaMemcpyAsync(ws->h_scalars + SC_GUARD, C.guard, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                              st));
+  MG_CUDA_TRY(cudaStreamSynchronize(st));
+  S->guarded = (long long)*reinterpret_cast<const unsigned long long*>(ws->h_scalars + SC_GUARD);
   S->cycles = cyc;
   S->outer = outer;
   S->resid = eps;

@@ -28,6 +28,7 @@ struct TailArgs {
   const float* S;                     // FAS source
   const float* rho[kTailMaxLevels];   // density pyramid (nullptr when the operator takes none)
   int nu1, nu2, coarse_sweeps;
+  unsigned long long* guard;          // positivity-guard replacements (counted), or nullptr
 };
 
 // Shared-memory bytes of a tail: e, u, S per level, R e on all but the first,
@@ -98,7 +99,8 @@ __device__ __forceinline__ void tail_fas(const LevelF& f, int n, const float* Re
 }
 
 template <bool FR>
-__device__ __forceinline__ void tail_prolong(int nc, const float* eH, const float* Re, const float* ub, float* ef) {
+__device__ __forceinline__ void tail_prolong(int nc, const float* eH, const float* Re, const float* ub, float* ef,
+                                             unsigned long long* guard) {
   const int nf = nc << 1, nf3 = nf * nf * nf;
   for (int t = threadIdx.x; t < nf3; t += blockDim.x) {
     const int k = t % nf, j = (t / nf) % nf, i = t / (nf * nf);
@@ -115,7 +117,10 @@ __device__ __forceinline__ void tail_prolong(int nc, const float* eH, const floa
                        (1.f / 64.f);
     const float old = ef[t];
     float v = old + corr;
-    if (FR && !(ub[t] + v > 0.f)) v = 0.5f * (old - ub[t]);
+    if (FR && !(ub[t] + v > 0.f)) {
+      v = 0.5f * (old - ub[t]);
+      count_guards(guard, 1u);
+    }
     ef[t] = v;
   }
   __syncthreads();
@@ -157,7 +162,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail32(TailArgs A) {
   }
   tail_smooth<K>(A.lf[A.T - 1], A.n[A.T - 1], e[A.T - 1], ub[A.T - 1], rh[A.T - 1], S[A.T - 1], A.coarse_sweeps);
   for (int m = A.T - 2; m >= 0; --m) {
-    tail_prolong<is_fr(K)>(A.n[m + 1], e[m + 1], Re[m + 1], ub[m], e[m]);
+    tail_prolong<is_fr(K)>(A.n[m + 1], e[m + 1], Re[m + 1], ub[m], e[m], A.guard);
     tail_smooth<K>(A.lf[m], A.n[m], e[m], ub[m], rh[m], S[m], A.nu2);
   }
   const int n3 = A.n[0] * A.n[0] * A.n[0];

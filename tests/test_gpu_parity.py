@@ -454,3 +454,28 @@ def test_point_mass_matches_oracle_and_decays_at_m_eff(orc, mg, precision):
     assert relL2(u, ref.u) <= (1e-9 if precision == 0 else 1e-6)
     dfR = -(u ** 2) - b["fRbar"]
     assert point_mass_decay(dfR, N, diagonal=True) == pytest.approx(paper_m_eff(p, b), rel=0.01)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_positivity_guard_count_matches_oracle(orc, mg, precision):
+    """Strong screening (|fR0| = 1e-6, lognormal sigma_g = 2 on 64^3) makes the
+    coarse-grid correction overshoot below zero in some cells, where the guard
+    (reading C11) halves the field instead.  The FP64 GPU solve runs the oracle's
+    cycles, so it counts exactly the oracle's replacements (mgglam_stats.guarded);
+    the mixed solve counts its own (its finest level corrects only the second
+    colour before post-smoothing), and both reach the oracle's solution."""
+    N = 64
+    rho32 = inputs.lognormal_density(N, 2.0, seed=5).astype(np.float32)
+    po, pg = both_params(orc, mg, "fr1", box=64.0, fR0_abs=1e-6, precision=precision, max_cycles=60)
+    ref = orc.solve(po, rho32.astype(np.float64), tol=1e-10, max_cycles=60)
+    field = torch.full((N, N, N), float("nan"), dtype=torch.float64, device="cuda")
+    st = mg.solve_scalar(pg, 1.0, cuda32(rho32), field, 1e-10)
+    got = field.cpu().numpy()
+    assert ref.guarded > 0
+    assert st.converged
+    if precision == 0:
+        assert st.cycles == ref.cycles and st.guarded == ref.guarded
+        assert relL2(got, ref.u) <= 1e-9
+    else:
+        assert st.guarded > 0
+        assert relL2(got, ref.u) <= 1e-6
