@@ -101,7 +101,7 @@ def lib():
         _lib.or_prolong_correct.restype = ctypes.c_long
         _lib.or_solve.argtypes = [P(CParams), i, dp, dp, d, i, i, i, i, i, i, dp, dp,
                                   P(ctypes.c_long)]
-        _lib.or_solve_cycle.argtypes = [P(CParams), i, dp, dp, d, i, i, i, i, i, i, i, dp, dp,
+        _lib.or_solve_cycle.argtypes = [P(CParams), i, dp, dp, d, i, i, i, i, i, i, i, i, dp, dp,
                                         ctypes.POINTER(ctypes.c_long)]
         _lib.or_solve_cycle.restype = i
         _lib.or_solve.restype = i
@@ -198,9 +198,10 @@ class SolveResult:
 
 def solve(p: Params, rho, u0=None, tol: float = 1e-10, max_cycles: int = 50, nu1: int = 2,
           nu2: int = 2, coarse_sweeps: int = 16, kind: int = KIND_NONLINEAR, levels: int = 0,
-          cycle: int = 0) -> SolveResult:
+          cycle: int = 0, fmg: bool = False) -> SolveResult:
     """FAS cycles (cycle 0 V, 1 F, 2 W) to relative residual tol (or max_cycles).  u0=None starts
-    from the background."""
+    from the background.  fmg: the first cycle is the full-multigrid start (the coarse problems
+    first; it replaces the initial guess)."""
     rho = _f64(rho)
     N = rho.shape[0]
     u = np.full(rho.shape, np.nan) if u0 is None else _f64(u0).copy()
@@ -208,7 +209,8 @@ def solve(p: Params, rho, u0=None, tol: float = 1e-10, max_cycles: int = 50, nu1
     eps = ctypes.c_double()
     g = ctypes.c_long()
     cyc = lib().or_solve_cycle(ctypes.byref(p.c()), N, _dp(rho), _dp(u), tol, max_cycles, nu1, nu2,
-                               coarse_sweeps, kind, levels, cycle, _dp(hist), ctypes.byref(eps), ctypes.byref(g))
+                               coarse_sweeps, kind, levels, cycle, int(fmg), _dp(hist), ctypes.byref(eps),
+                               ctypes.byref(g))
     return SolveResult(u, cyc, eps.value, hist[: cyc + 1], g.value)
 
 

@@ -29,6 +29,8 @@
  *    unique admissible root is found here by safeguarded Newton-bisection, not
  *    by the closed forms.  kind 1 = Newton-Gauss-Seidel: one step of
  *    Eq. relaxation_iteration per cell (Sec. 3.2.1; the paper's CQ method).
+ *  - Optionally a full-multigrid start (fmg_start): the coarse problems first,
+ *    each level starting from the prolonged coarser solution.
  *  - FAS multigrid V-cycles (Sec. 3.2.1): restriction = mean of the 8 children,
  *    coarse equation Eq. general_pde_numerical_coarse, coarse initial guess =
  *    restricted fine solution, correction Eq. solution_correction with the
@@ -421,6 +423,29 @@ static void vcycle(const or_params* p, const or_background* b, or_hier* H, int l
   or_smooth(p, b, n, h, H->u[l], H->rho[l], H->S[l], o->nu2, o->kind);
 }
 
+/*
+ * Full-multigrid start (the nested-iteration use of the same FAS cycles,
+ * Sec. 3.2.1): the problem is posed on every level (the density restricted by
+ * 8-child means, no FAS source: N^H(u^H) = 0), relaxed on the coarsest level
+ * from the background value, and each finer level starts from the plain
+ * 27/9/3/1 prolongation of the coarser level's result and takes one cycle.
+ * On return level 0 holds the FMG iterate.
+ */
+static void fmg_start(const or_params* p, const or_background* b, or_hier* H, const or_cycle_opts* o,
+                      long* guarded) {
+  const int L = H->nlev;
+  const size_t nL3 = (size_t)H->n[L - 1] * H->n[L - 1] * H->n[L - 1];
+  for (size_t c = 0; c < nL3; ++c) H->u[L - 1][c] = b->ubar;
+  if (L - 1 > 0) memset(H->S[L - 1], 0, nL3 * sizeof(double));
+  or_smooth(p, b, H->n[L - 1], H->h[L - 1], H->u[L - 1], H->rho[L - 1], H->S[L - 1], o->coarse_sweeps, o->kind);
+  for (int l = L - 2; l >= 0; --l) {
+    const size_t n3 = (size_t)H->n[l] * H->n[l] * H->n[l];
+    or_prolong(H->n[l + 1], H->u[l + 1], H->u[l]);
+    if (l > 0) memset(H->S[l], 0, n3 * sizeof(double));
+    vcycle(p, b, H, l, o, guarded, 0);
+  }
+}
+
 /* Source scale used to make the global residual relative (reading C5). */
 static double source_rms(const or_params* p, const or_background* b, int N, const double* rho) {
   size_t n3 = (size_t)N * N * N;
@@ -462,7 +487,7 @@ static int count_levels(int N, int levels) {
  */
 int or_solve_cycle(const or_params* p, int N, const double* rho_in, double* u, double tol,
                    int max_cycles, int nu1, int nu2, int coarse_sweeps, int kind, int levels, int cycle,
-                   double* hist, double* eps_out, long* guarded_out) {
+                   int fmg, double* hist, double* eps_out, long* guarded_out) {
   or_background b;
   or_compute_background(p, N, &b);
   or_hier H;
@@ -495,7 +520,9 @@ int or_solve_cycle(const or_params* p, int N, const double* rho_in, double* u, d
   double eps = sqrt(or_residual(p, &b, N, 1.0, u, H.rho[0], NULL, NULL) / (double)N3) / snorm;
   if (hist) hist[0] = eps;
   while (cyc < max_cycles && !(eps <= tol)) {
-    vcycle(p, &b, &H, 0, &o, &guarded, cycle);
+    /* fmg: the first cycle is the full-multigrid start (it ends with one cycle on level 0) */
+    if (fmg && cyc == 0) fmg_start(p, &b, &H, &o, &guarded);
+    else vcycle(p, &b, &H, 0, &o, &guarded, cycle);
     ++cyc;
     eps = sqrt(or_residual(p, &b, N, 1.0, u, H.rho[0], NULL, NULL) / (double)N3) / snorm;
     if (hist) hist[cyc] = eps;
@@ -512,7 +539,7 @@ int or_solve_cycle(const or_params* p, int N, const double* rho_in, double* u, d
 int or_solve(const or_params* p, int N, const double* rho_in, double* u, double tol,
              int max_cycles, int nu1, int nu2, int coarse_sweeps, int kind, int levels,
              double* hist, double* eps_out, long* guarded_out) {
-  return or_solve_cycle(p, N, rho_in, u, tol, max_cycles, nu1, nu2, coarse_sweeps, kind, levels, 0, hist,
+  return or_solve_cycle(p, N, rho_in, u, tol, max_cycles, nu1, nu2, coarse_sweeps, kind, levels, 0, 0, hist,
                         eps_out, guarded_out);
 }
 

@@ -563,6 +563,36 @@ def test_cq_background_forgets_its_initial_field(orc):
 # F- and W-cycles (Sec. 3.2.1: the arrangements MG-GLAM implements besides V)
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("n", SINE["f(R)"]["n"])
+def test_fmg_start_reaches_discretisation_accuracy(orc, n):
+    """The full-multigrid start solves the coarse problems first and carries each
+    solution up as the next level's start (one cycle per level).  Its error against
+    the exact discrete solution is of discretisation order: it falls by >= 2.5x
+    when the mesh is refined 2x (4x for second order), and it is >= 20x below the
+    error of one V-cycle from the background (whose error does not fall with h).
+    The density is the paper's 1D sine field (Sec. 4.2.2), |fR0| = 1e-5."""
+    errs, v1s = [], []
+    for N in (32, 64):
+        p = fr_params(orc, n=n, box=2.0 * N)
+        b = orc.background(p, N)
+        k, A = 2 * np.pi / N, SINE["A"]
+        s = np.sin(k * _x_centres(N))[:, None, None] * np.ones((1, N, N))
+        delta = (p.a / p.omega_m) * (b["c2"] * b["fRbar"] * k ** 2 * A * s + b["K0"] * (1 + A * s) ** (-1 / (n + 1))
+                                     - b["K0"])
+        rho = 1.0 + delta
+        ex = orc.solve(p, rho, tol=1e-14, max_cycles=60)
+        scale = np.abs(ex.u - b["ubar"]).max()
+        fmg = orc.solve(p, rho, tol=0.0, max_cycles=1, fmg=True)
+        v1 = orc.solve(p, rho, tol=0.0, max_cycles=1)
+        errs.append(np.abs(fmg.u - ex.u).max() / scale)
+        v1s.append(np.abs(v1.u - ex.u).max() / scale)
+        assert errs[-1] <= v1s[-1] / 20
+        # FMG then V-cycles converge to the same discrete solution
+        r = orc.solve(p, rho, tol=1e-13, max_cycles=40, fmg=True)
+        np.testing.assert_allclose(r.u, ex.u, rtol=1e-10)
+    assert errs[1] <= errs[0] / 2.5
+
+
 def test_f_and_w_cycles_reach_the_same_discrete_solution_faster(orc):
     """The cycle shape changes how the fixed point is approached, not the fixed
     point: V, F and W cycles converge to the same discrete solution.  F and W
