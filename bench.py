@@ -373,6 +373,31 @@ def run_models_extra(mg, torch, dev, tol=TOL) -> dict:
     return out
 
 
+def run_fmg_extra(mg, torch, rho, field, stream) -> dict:
+    """Time to 1e-8 on the headline density with the full-multigrid start against
+    the V-cycle start (the background), mixed and plain FP64, same schedule."""
+    out = {"workload": "the headline density (deposited 256^3 Zel'dovich particles), tol 1e-8"}
+    for prec, pname in ((mg.MIXED, "mixed"), (mg.FP64, "fp64")):
+        for fmg in (0, 1):
+            p = headline_params(mg, precision=prec, fmg=fmg)
+            times = []
+            for _ in range(3 if prec == mg.MIXED else 2):
+                field.fill_(float("nan"))
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st = mg.solve_scalar(p, 1.0, rho, field, TOL)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            out[f"{pname}_{'fmg' if fmg else 'v'}"] = {"time_to_tol_ms": round(min(times[1:] or times), 3),
+                                                      "cycles": st.cycles, "outer_steps": st.outer,
+                                                      "resid": st.resid, "hist": st.hist}
+    for pname in ("mixed", "fp64"):
+        out[f"{pname}_fmg_speedup"] = round(out[f"{pname}_v"]["time_to_tol_ms"] / out[f"{pname}_fmg"]["time_to_tol_ms"], 3)
+    return out
+
+
 def run_pm_extra(mg, torch, dev) -> dict:
     """One particle-mesh time step at 256^3 (the headline workload's 256^3 Zel'dovich
     particles and mesh, box 256 Mpc/h, a = 0.9, da = 0.01, momenta from rest):
@@ -707,9 +732,11 @@ def run_ours(args) -> None:
                                     "d2h_bytes_per_step": int(force_host.numel() * 4)}},
         "clocks": clk,
     }
-    extras = {"all": ("batch", "adjoint", "models", "pm"), "none": ()}.get(args.extras, (args.extras,))
+    extras = {"all": ("fmg", "batch", "adjoint", "models", "pm"), "none": ()}.get(args.extras, (args.extras,))
     if args.no_extras:
         extras = ()
+    if "fmg" in extras:
+        line["fmg"] = run_fmg_extra(mg, torch, rho, field, stream)
     if "batch" in extras:
         line["batch"] = run_batch_extra(mg, torch, dev)
     if "adjoint" in extras:
@@ -742,7 +769,7 @@ def main():
     ap.add_argument("--tail-cells", type=int, default=0, help="largest level run by the one-block tail (0 = default)")
     ap.add_argument("--cycle", choices=["V", "F", "W"], default="V", help="multigrid cycle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", choices=["all", "none", "batch", "adjoint", "models", "pm"], default="all",
+    ap.add_argument("--extras", choices=["all", "none", "fmg", "batch", "adjoint", "models", "pm"], default="all",
                     help="extra measurements after the main step: the 48-solve batch, the 512^3 adjoint, "
                          "the symmetron and CQ solves at 256^3")
     ap.add_argument("--no-extras", action="store_true", help="same as --extras none")

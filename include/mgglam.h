@@ -96,6 +96,14 @@ typedef struct {
                          0 (default) = 512; < 0 = off; at most 4096 */
   int cycle;          /* multigrid cycle: 0 (default) V, 1 F, 2 W (Sec. 3.2.1; each level
                          recurses once (V), twice (W), or F then V (F)) */
+  int fmg;            /* 1: full-multigrid start (f(R), symmetron): the first cycle solves
+                         the coarse problems first and starts each level from the prolonged
+                         coarser solution, with one cycle per level (FP64: the whole
+                         problem from the background; MIXED: the first outer step's
+                         correction problem); 0 (default): cycles from the initial guess.
+                         CQ ignores it: its equation is Poisson-like with a mass far below
+                         the mesh scales, so the coarse solutions leave the field's mean
+                         undetermined and the start gains nothing */
 } mgglam_params;
 
 /* Per-solve statistics.  resid values are the relative global residual:

@@ -39,7 +39,7 @@ class CParams(ctypes.Structure):
                 ("coarse_sweeps", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("inner_cycles", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("sweep_chunk", ctypes.c_int), ("sweep_slab", ctypes.c_int), ("tail_cells", ctypes.c_int),
-                ("cycle", ctypes.c_int)]
+                ("cycle", ctypes.c_int), ("fmg", ctypes.c_int)]
 
 
 class CStats(ctypes.Structure):
@@ -78,6 +78,7 @@ class Params:
     sweep_slab: int = 0
     tail_cells: int = 0
     cycle: int = 0
+    fmg: int = 0
 
     def c(self) -> CParams:
         p = CParams()

@@ -28,6 +28,10 @@ constexpr double kFp32StepGain = 1e-5;
 // soon as an outer step is not limited by single precision.
 constexpr double kInitialContraction = 0.1;
 
+// Residual reduction assumed for the full-multigrid start when an outer step is
+// planned (mgglam_params.fmg); like kInitialContraction it errs on the slow side.
+constexpr double kFmgGain = 0.05;
+
 // One multigrid level.  FP64 arrays serve the FP64 path (and the FP64 fine
 // level of the mixed path); FP32 arrays serve the mixed path's inner cycles.
 struct Level {

@@ -295,6 +295,7 @@ static int check_params(const mgglam_params* prm) {
   if (prm->nu1 < 0 || prm->nu2 < 0 || prm->coarse_sweeps < 0 || prm->max_cycles < 0) return MGGLAM_ERR_ARG;
   if (prm->precision != MGGLAM_FP64 && prm->precision != MGGLAM_MIXED) return MGGLAM_ERR_ARG;
   if (prm->cycle < 0 || prm->cycle > 2) return MGGLAM_ERR_ARG;
+  if (prm->fmg != 0 && prm->fmg != 1) return MGGLAM_ERR_ARG;
   return MGGLAM_OK;
 }
 

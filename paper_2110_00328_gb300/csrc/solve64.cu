@@ -440,6 +440,30 @@ static int vcycle64(const ModelDev& m, Workspace* ws, int l, const mgglam_params
   return rc;
 }
 
+// Full-multigrid start (prm->fmg): every level poses N^H(u^H) = 0 on its restricted
+// density; the coarsest level relaxes from the background value, and each finer
+// level starts from the plain prolongation of the coarser result (the correction
+// kernel applied to a zero field with a zero coarse reference) and takes one
+// cycle.  Level 0 (the caller's field) holds the result.
+static int fmg_start64(const ModelDev& m, Workspace* ws, const mgglam_params* prm, cudaStream_t st) {
+  const int L = ws->nlev;
+  Level& C = ws->lev[L - 1];
+  int rc;
+  if ((rc = launch_init_background(m, C.u, C.n3, st))) return rc;
+  if (L > 1) MG_CUDA_TRY(cudaMemsetAsync(C.S, 0, C.n3 * sizeof(double), st));
+  if ((rc = launch_coarse64(m, C.n, C.h, C.u, C.rho, L > 1 ? C.S : nullptr, prm->coarse_sweeps, st))) return rc;
+  for (int l = L - 2; l >= 0; --l) {
+    Level& F = ws->lev[l];
+    Level& H = ws->lev[l + 1];
+    MG_CUDA_TRY(cudaMemsetAsync(F.u, 0, F.n3 * sizeof(double), st));
+    MG_CUDA_TRY(cudaMemsetAsync(H.Ru, 0, H.n3 * sizeof(double), st));
+    if ((rc = launch_prolong_correct64(m, H.n, H.u, H.Ru, nullptr, F.u, st))) return rc;
+    if (l > 0) MG_CUDA_TRY(cudaMemsetAsync(F.S, 0, F.n3 * sizeof(double), st));
+    if ((rc = vcycle64(m, ws, l, prm, st, 0))) return rc;
+  }
+  return MGGLAM_OK;
+}
+
 int solve_fp64(const mgglam_params* prm, double a, const float* rho, int N, double* field, double tol,
                mgglam_stats* stats, cudaStream_t st) {
   auto t0 = std::chrono::steady_clock::now();
@@ -477,7 +501,11 @@ int solve_fp64(const mgglam_params* prm, double a, const float* rho, int N, doub
   int status = MGGLAM_OK;
   while (!(eps <= tol) && cyc < prm->max_cycles) {
     if (!isfinite(eps)) { status = MGGLAM_ERR_NONFINITE; break; }
-    if ((rc = vcycle64(m, ws, 0, prm, st))) return rc;
+    if (prm->fmg && m.kind != KCQ && cyc == 0) {
+      if ((rc = fmg_start64(m, ws, prm, st))) return rc;
+    } else if ((rc = vcycle64(m, ws, 0, prm, st))) {
+      return rc;
+    }
     ++cyc;
     if (cyc % every == 0 || cyc == prm->max_cycles) {
       if ((rc = launch_residual64(m, F.n, F.h, field, F.rho, nullptr, nullptr, ws->partials,

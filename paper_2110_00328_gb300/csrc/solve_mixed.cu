@@ -519,25 +519,14 @@ static void tail_allow_smem() {
   cudaFuncSetAttribute(k_tail32<KCQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-// One multigrid cycle from level l: mode 0 V, 1 F, 2 W (Sec. 3.2.1).
-static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode) {
+// Residual and restriction from level l to l+1: H.Re = R e, H.e = R e (the coarse
+// start), H.ub = R ub, H.S32 = R (M(e) - S); the FAS source follows (fas_source).
+static int restrict_level(const MixedCtx& C, int l, cudaStream_t st) {
   Workspace* ws = C.ws;
   Level& L = ws->lev[l];
   const float* rho = C.need_rho ? L.rho32 : nullptr;
-  int rc;
-  if (l == C.tail_level) return launch_tail(C, l, st);
-  if (l == ws->nlev - 1) {
-    if ((long long)L.n3 > 4096) return smooth32(C, l, C.prm->coarse_sweeps, st);
-    MG_DISPATCH32(C.m.kind, (k_coarse32<KK><<<1, 512, 0, st>>>(C.lf[l], L.n, L.e, L.ub, rho, L.S32,
-                                                                 C.prm->coarse_sweeps)));
-    return MGGLAM_OK;
-  }
-  if (l == 0) prof_begin(PC_SMOOTH32_FINE, st, 16.0 * L.n3 * C.prm->nu1);
-  if ((rc = smooth32(C, l, C.prm->nu1, st))) return rc;
-  if (l == 0) prof_end(st);
   Level& H = ws->lev[l + 1];
   const int bh = bx_for(H.n);
-  if (l == 0) prof_begin(PC_RESTRICT32_FINE, st, 14.0 * L.n3);
   if (l == 0 && C.split) {
     const dim3 g((L.n / 4 + 31) / 32, H.n, (H.n + 3) / 4);
     if (C.qs && C.m.kind == KFR1) {
@@ -560,23 +549,20 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode) {
     MG_DISPATCH32(C.m.kind, (k_residual_restrict32<KK><<<grid3(H.n, H.n, H.n, bh), bh, 0, st>>>(
                                  C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32)));
   }
-  if (l == 0) {
-    prof_end(st);
-    prof_begin(PC_COARSE_LEVELS, st, 0.0);
-    if ((rc = coarse_part(C, st))) return rc;
-  } else {
-    if ((rc = fas_source(C, l + 1, st))) return rc;
-    if ((rc = vcycle32(C, l + 1, st, mode))) return rc;
-    if (mode != 0 && (rc = vcycle32(C, l + 1, st, mode == 2 ? 2 : 0))) return rc;
-  }
-  // algorithmic bytes per fine cell: e, u read and e written (12), the coarse pair (1); the
-  // second-colour-only form reads and writes half of e and u and writes half of q (9)
-  if (l == 0) { prof_end(st); prof_begin(PC_PROLONG32_FINE, st, (C.qs && C.prm->nu2 >= 1 ? 9.0 : 13.0) * L.n3); }
+  return MGGLAM_OK;
+}
+
+// Coarse-grid correction of level l from l+1 (e += P(H.e - H.Re)).  both: correct
+// both colours of a split finest level even when post-smoothing follows.
+static int prolong_level(const MixedCtx& C, int l, cudaStream_t st, bool both = false) {
+  Workspace* ws = C.ws;
+  Level& L = ws->lev[l];
+  Level& H = ws->lev[l + 1];
   const int bf = bx_for(L.n);
   if (l == 0 && C.split) {
     const dim3 g((L.n / 4 + 31) / 32, L.n, L.n / 4);
     // with post-smoothing the first colour's corrections would be overwritten unread (prolong_quad)
-    const bool second_only = C.prm->nu2 >= 1;
+    const bool second_only = !both && C.prm->nu2 >= 1;
     if (C.qs && C.m.kind == KFR1 && second_only)
       k_prolong_correct32q<true, SplitLayout, KFR1, true><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e,
                                                                                       C.guard, C.qs);
@@ -602,10 +588,72 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode) {
     k_prolong_correct32<false><<<grid3(L.n, L.n, L.n, bf), bf, 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard);
   }
   note_launch(1);
+  return MGGLAM_OK;
+}
+
+// One multigrid cycle from level l: mode 0 V, 1 F, 2 W (Sec. 3.2.1).
+static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode) {
+  Workspace* ws = C.ws;
+  Level& L = ws->lev[l];
+  const float* rho = C.need_rho ? L.rho32 : nullptr;
+  int rc;
+  if (l == C.tail_level) return launch_tail(C, l, st);
+  if (l == ws->nlev - 1) {
+    if ((long long)L.n3 > 4096) return smooth32(C, l, C.prm->coarse_sweeps, st);
+    MG_DISPATCH32(C.m.kind, (k_coarse32<KK><<<1, 512, 0, st>>>(C.lf[l], L.n, L.e, L.ub, rho, L.S32,
+                                                                 C.prm->coarse_sweeps)));
+    return MGGLAM_OK;
+  }
+  if (l == 0) prof_begin(PC_SMOOTH32_FINE, st, 16.0 * L.n3 * C.prm->nu1);
+  if ((rc = smooth32(C, l, C.prm->nu1, st))) return rc;
+  if (l == 0) prof_end(st);
+  if (l == 0) prof_begin(PC_RESTRICT32_FINE, st, 14.0 * L.n3);
+  if ((rc = restrict_level(C, l, st))) return rc;
+  if (l == 0) {
+    prof_end(st);
+    prof_begin(PC_COARSE_LEVELS, st, 0.0);
+    if ((rc = coarse_part(C, st))) return rc;
+  } else {
+    if ((rc = fas_source(C, l + 1, st))) return rc;
+    if ((rc = vcycle32(C, l + 1, st, mode))) return rc;
+    if (mode != 0 && (rc = vcycle32(C, l + 1, st, mode == 2 ? 2 : 0))) return rc;
+  }
+  // algorithmic bytes per fine cell: e, u read and e written (12), the coarse pair (1); the
+  // second-colour-only form reads and writes half of e and u and writes half of q (9)
+  if (l == 0) { prof_end(st); prof_begin(PC_PROLONG32_FINE, st, (C.qs && C.prm->nu2 >= 1 ? 9.0 : 13.0) * L.n3); }
+  if ((rc = prolong_level(C, l, st))) return rc;
   if (l == 0) { prof_end(st); prof_begin(PC_SMOOTH32_FINE, st, 16.0 * L.n3 * C.prm->nu2); }
   rc = smooth32(C, l, C.prm->nu2, st);
   if (l == 0) prof_end(st);
   return rc;
+}
+
+// Full-multigrid start of the first outer step (prm->fmg), on the correction
+// problem M(e) = S.  With e = 0 on every level, the residual-restriction and FAS-
+// source kernels hand each coarser level the restricted base field and the
+// restricted source (M(0) = 0, so S^H = M^H(0) - R(M(0) - S) = R S, and R e = 0).
+// The coarsest level relaxes from e = 0; every finer level starts from the
+// prolonged coarser correction (e = 0 + P(e^H - 0), both colours) and takes one
+// V-cycle, the coarse stages without the one-block tail (so that each stage is
+// the oracle's: relax the coarsest, prolong, cycle), the last one (level 0)
+// as every other cycle of the solve.  From a uniform base field (the
+// background start) this is the FMG of the total-field problem.
+static int fmg_start32(const MixedCtx& C, cudaStream_t st) {
+  Workspace* ws = C.ws;
+  MixedCtx Cs = C;
+  Cs.tail_level = -1;
+  const int base = ws->nlev - 1;
+  int rc;
+  for (int l = 0; l < base; ++l) {
+    if ((rc = restrict_level(C, l, st))) return rc;
+    if ((rc = fas_source(C, l + 1, st))) return rc;
+  }
+  if ((rc = vcycle32(Cs, base, st, 0))) return rc;
+  for (int l = base - 1; l >= 0; --l) {
+    if ((rc = prolong_level(C, l, st, true))) return rc;
+    if ((rc = vcycle32(l == 0 ? C : Cs, l, st, 0))) return rc;
+  }
+  return MGGLAM_OK;
 }
 
 // Tile of the FP64 outer-residual kernel.
@@ -792,11 +840,14 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
   int status = MGGLAM_OK;
   while (!(eps <= tol) && cyc < prm->max_cycles) {
     if (!isfinite(eps)) { status = MGGLAM_ERR_NONFINITE; break; }
+    // the first cycle of the first outer step is the FMG start (fmg_start32),
+    // planned as a gain of kFmgGain followed by cycles at the estimated contraction
+    const bool fmg = prm->fmg && C.m.kind != KCQ && outer == 0;
     int inner = prm->inner_cycles;
     if (inner <= 0) {
-      const double lr = log(rho_est);
-      const int need = (int)ceil(log(fmax(tol, 1e-300) / eps) / lr - 1e-9);
-      const int cap = (int)ceil(log(kFp32StepGain) / lr - 1e-9);
+      const double lr = log(rho_est), lg = fmg ? log(kFmgGain) : 0.0;
+      const int need = (fmg ? 1 : 0) + (int)ceil((log(fmax(tol, 1e-300) / eps) - lg) / lr - 1e-9);
+      const int cap = (fmg ? 1 : 0) + (int)ceil((log(kFp32StepGain) - lg) / lr - 1e-9);
       inner = need < 1 ? 1 : (need > cap ? cap : need);
     }
     const double eps_before = eps;
@@ -804,7 +855,7 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
     MG_CUDA_TRY(cudaMemsetAsync(F.e, 0, F.n3 * sizeof(float), st));
     if (C.qs) MG_CUDA_TRY(cudaMemsetAsync(C.qs, 0, F.n3 * sizeof(float), st));  // Delta w(u, 0) = 0
     for (int c = 0; c < inner && cyc < prm->max_cycles; ++c, ++cyc, ++done)
-      if ((rc = vcycle32(C, 0, st, C.prm->cycle))) return rc;
+      if ((rc = (fmg && c == 0) ? fmg_start32(C, st) : vcycle32(C, 0, st, C.prm->cycle))) return rc;
     prof_begin(PC_APPLY_CORR, st, 20.0 * n3);
     if (C.split) k_apply_correction_split<<<kStreamBlocks, 128, 0, st>>>(field, F.e, F.n);
     else k_apply_correction<<<stream_grid(n3), kThreads, 0, st>>>(field, F.e, n3);
@@ -818,9 +869,11 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
     MG_CUDA_TRY(cudaGetLastError());
     eps = sqrt(ws->h_scalars[SC_SUMSQ] / (double)n3) / snorm;
     if (nh < 64) S->resid_hist[nh++] = eps;
-    if (done > 0 && eps > 0.0 && eps < eps_before) {
+    const int vdone = fmg ? done - 1 : done;  // V-cycles after the FMG start
+    if (vdone > 0 && eps > 0.0 && eps < eps_before) {
       // per-cycle contraction of this step, when it was not limited by single precision
-      const double r = pow(eps / eps_before, 1.0 / done);
+      const double g = (eps / eps_before) / (fmg ? kFmgGain : 1.0);
+      const double r = pow(g, 1.0 / vdone);
       if (eps / eps_before > kFp32StepGain) rho_est = fmin(0.5, fmax(0.01, r));
     }
   }

@@ -68,6 +68,8 @@ def test_argument_errors_are_reported_before_any_device_work(lib):
     assert lib.mgglam_solve_scalar(ctypes.byref(p), 1.0, fake, 32, fake, -1.0, ctypes.byref(st), None) == -1
     bad = binding.Params(precision=7).c()
     assert lib.mgglam_solve_scalar(ctypes.byref(bad), 1.0, fake, 32, fake, 1e-8, ctypes.byref(st), None) == -1
+    bad = binding.Params(fmg=2).c()
+    assert lib.mgglam_solve_scalar(ctypes.byref(bad), 1.0, fake, 32, fake, 1e-8, ctypes.byref(st), None) == -1
     assert lib.mgglam_deposit_cic(nullp, 10, 32, fake, None) == -1
     assert lib.mgglam_deposit_cic(fake, 0, 32, fake, None) == -1
     assert lib.mgglam_deposit_cic(fake, 10, 4096, fake, None) == -2
