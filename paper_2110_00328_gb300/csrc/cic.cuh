@@ -27,6 +27,49 @@ __device__ __forceinline__ void cic_axis_f(float x, int N, int& c0, int& c1, flo
   w1 = f;
 }
 
+// The CIC-weighted central differences of a mesh scalar around one particle:
+// Tv(a, b, c) returns T at the cell with per-axis positions a, b, c in 0..3,
+// meaning (c0 - 1, c0, c1, c1 + 1) of that axis.  Shared by the gather from
+// global memory and the gather from a tile staged in shared memory, so that
+// both form the same sums in the same order.
+template <class Tv>
+__device__ __forceinline__ float3 cic_grad_core(const Tv& Tat, const float wx[2], const float wy[2],
+                                                const float wz[2]) {
+  float C[2][2][2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) C[a][b][c] = Tat(a + 1, b + 1, c + 1);
+  float fx = 0.f, fy = 0.f, fz = 0.f;
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float xm = Tat(0, b + 1, c + 1), xp = Tat(3, b + 1, c + 1);
+      const float w = wy[b] * wz[c];
+      fx += w * (wx[0] * (C[1][b][c] - xm) + wx[1] * (xp - C[0][b][c]));
+    }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float ym = Tat(a + 1, 0, c + 1), yp = Tat(a + 1, 3, c + 1);
+      const float w = wx[a] * wz[c];
+      fy += w * (wy[0] * (C[a][1][c] - ym) + wy[1] * (yp - C[a][0][c]));
+    }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const float zm = Tat(a + 1, b + 1, 0), zp = Tat(a + 1, b + 1, 3);
+      const float w = wx[a] * wy[b];
+      fz += w * (wz[0] * (C[a][b][1] - zm) + wz[1] * (zp - C[a][b][0]));
+    }
+  return make_float3(0.5f * fx, 0.5f * fy, 0.5f * fz);
+}
+
 // Gradient of the mesh scalar T at (x, y, z): the central differences
 // (T_{c+1} - T_{c-1})/2 at the 8 CIC cells, weighted with the particle's CIC
 // weights.  Reads the 32 distinct cells those differences touch: the 2x2x2
@@ -44,39 +87,8 @@ __device__ __forceinline__ float3 cic_grad(const float* __restrict__ T, int N, f
   const long long oy[4] = {(long long)(j0 == 0 ? N - 1 : j0 - 1) * N, (long long)j0 * N, (long long)j1 * N,
                            (long long)(j1 + 1 == N ? 0 : j1 + 1) * N};
   const int oz[4] = {k0 == 0 ? N - 1 : k0 - 1, k0, k1, k1 + 1 == N ? 0 : k1 + 1};
-  float C[2][2][2];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 2; ++b)
-#pragma unroll
-      for (int c = 0; c < 2; ++c) C[a][b][c] = T[ox[a + 1] + oy[b + 1] + oz[c + 1]];
-  float fx = 0.f, fy = 0.f, fz = 0.f;
-#pragma unroll
-  for (int b = 0; b < 2; ++b)
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const float xm = T[ox[0] + oy[b + 1] + oz[c + 1]], xp = T[ox[3] + oy[b + 1] + oz[c + 1]];
-      const float w = wy[b] * wz[c];
-      fx += w * (wx[0] * (C[1][b][c] - xm) + wx[1] * (xp - C[0][b][c]));
-    }
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const float ym = T[ox[a + 1] + oy[0] + oz[c + 1]], yp = T[ox[a + 1] + oy[3] + oz[c + 1]];
-      const float w = wx[a] * wz[c];
-      fy += w * (wy[0] * (C[a][1][c] - ym) + wy[1] * (yp - C[a][0][c]));
-    }
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const float zm = T[ox[a + 1] + oy[b + 1] + oz[0]], zp = T[ox[a + 1] + oy[b + 1] + oz[3]];
-      const float w = wx[a] * wy[b];
-      fz += w * (wz[0] * (C[a][b][1] - zm) + wz[1] * (zp - C[a][b][0]));
-    }
-  return make_float3(0.5f * fx, 0.5f * fy, 0.5f * fz);
+  auto Tat = [&](int a, int b, int c) { return T[ox[a] + oy[b] + oz[c]]; };
+  return cic_grad_core(Tat, wx, wy, wz);
 }
 
 }  // namespace mg

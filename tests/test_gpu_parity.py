@@ -479,3 +479,24 @@ def test_positivity_guard_count_matches_oracle(orc, mg, precision):
     else:
         assert st.guarded > 0
         assert relL2(got, ref.u) <= 1e-6
+
+
+def test_deposit_and_gather_of_a_dense_clump(orc, mg):
+    """Degenerate clustering: 20000 particles in one 8.5^3-cell clump (hundreds per
+    cell, so the fixed-point sums carry far above 2^32 units), a few on the periodic
+    wrap and a few elsewhere, most of the mesh empty.  Mesh and forces match the
+    oracle (deposit: float32 rounding of the exact fixed-point sum; forces: rel-L2
+    1e-5)."""
+    N = 32
+    rng = np.random.default_rng(91)
+    clump = rng.uniform(8.0, 16.49, size=(20000, 3))
+    edge = np.array([[31.7, 0.2, 15.9], [0.49, 31.51, 8.5], [16.5, 16.5, 16.5], [7.99, 8.0, 23.4]])
+    pos = np.concatenate([clump, edge, rng.uniform(0, N, size=(37, 3))]).astype(np.float32)
+    ref = orc.deposit_cic(pos, N)
+    got = mg.deposit_cic(cuda32(pos), N).cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=2e-7, atol=1e-8 * N ** 3 / pos.shape[0])
+    po, pg = both_params(orc, mg, "fr1", box=64.0)
+    u = trial_field(orc, po, inputs.lognormal_density(N, 1.0, seed=46), "fr1", seed=47)
+    F_ref = orc.gather_force(po, u, pos, prefactor=0.7)
+    F = mg.gather_force(pg, 1.0, cuda64(u), cuda32(pos), prefactor=0.7).cpu().numpy()
+    assert relL2(F.astype(np.float64), F_ref) <= 1e-5
