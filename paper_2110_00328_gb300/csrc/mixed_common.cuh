@@ -248,6 +248,91 @@ __device__ __forceinline__ void fas_quad(const LevelF& f, int n, const float* __
   if (act) *reinterpret_cast<float4*>(S + c0) = out;
 }
 
+// Restriction of the defect after pre-smoothing on a split finest level with
+// stored q (f(R) n = 1, 2): the last pre-smoothing pass relaxed the second
+// colour, and each of its cells then satisfies its own local equation (the
+// closed-form root polished by Newton steps, or the warm-started Newton
+// steps), so the defect d = M(e) - S vanishes there up to the local solve's
+// rounding; it is formed at the first colour's cells only.  The lane mapping
+// is restrict_quad's (coarse cells (I, J, 2tq), (I, J, 2tq+1); fine quads
+// k0 = 4tq .. k0+3 of the rows (2I+a, 2J+b)).  In the split layout a row's quad
+// is one float2 per colour half; the first colour's two cells of row (i, j)
+// sit at k0 + p and k0 + p + 2, p = (i + j) & 1, one in each coarse cell, and
+// all six neighbours of a first-colour cell are second-colour cells, whose
+// stored q lies in the second colour's half at the same index (the i and j
+// neighbours) or the adjacent ones (the k neighbours).
+template <int K>
+__device__ __forceinline__ void restrict_split_zr(const LevelF& f, int nf, const float* __restrict__ e,
+                                                  const float* __restrict__ ub, const float* __restrict__ S,
+                                                  const float* __restrict__ qf, float* __restrict__ Re,
+                                                  float* __restrict__ eH, float* __restrict__ ubH,
+                                                  float* __restrict__ SH, int I, int J, int tq, int lane) {
+  static_assert(K == KFR1 || K == KFR2, "stored q: f(R) n = 1, 2");
+  const int nc = nf >> 1, nq = nf >> 2, h = nf >> 1;
+  const bool act = tq < nq;
+  const int m0 = 2 * (act ? tq : nq - 1);  // index of the quad in a colour half-row
+  const long long H = (long long)nf * nf * h;
+  const int i0 = 2 * I, j0 = 2 * J;
+  const int iA = i0 == 0 ? nf - 1 : i0 - 1, iB = i0 + 2 == nf ? 0 : i0 + 2;
+  const int jA = j0 == 0 ? nf - 1 : j0 - 1, jB = j0 + 2 == nf ? 0 : j0 + 2;
+  auto row = [&](int i, int j) { return ((long long)i * nf + j) * h + m0; };
+  const float* q1 = qf + H;  // second-colour half of q
+  // second-colour q of the own rows and of the halo rows around them
+  float2 Q[2][2], qi[2][2], qj[2][2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) Q[a][b] = ld2(q1 + row(i0 + a, j0 + b));
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    qi[0][b] = ld2(q1 + row(iA, j0 + b));
+    qi[1][b] = ld2(q1 + row(iB, j0 + b));
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    qj[a][0] = ld2(q1 + row(i0 + a, jA));
+    qj[a][1] = ld2(q1 + row(i0 + a, jB));
+  }
+  float se0 = 0.f, se1 = 0.f, su0 = 0.f, su1 = 0.f, sd0 = 0.f, sd1 = 0.f;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const long long r = row(i0 + a, j0 + b);
+      const float2 E0 = ld2(e + r), E1 = ld2(e + H + r), U0 = ld2(ub + r), U1 = ld2(ub + H + r);
+      const float2 S0 = ld2(S + r);
+      se0 += E0.x + E1.x;
+      se1 += E0.y + E1.y;
+      su0 += U0.x + U1.x;
+      su1 += U0.y + U1.y;
+      // k neighbours of the first-colour cells k0 + p + 2m: p = 0 -> (m - 1/2 +- 1/2) in the
+      // second colour's half-row, the one before the quad from the previous lane; p = 1 ->
+      // (m, m + 1), the one after the quad from the next lane
+      const int p = (a + b) & 1;
+      const float2 q = Q[a][b];
+      float qm = __shfl_up_sync(0xffffffffu, q.y, 1);
+      float qp = __shfl_down_sync(0xffffffffu, q.x, 1);
+      if (p == 0 && lane == 0) qm = q1[row(i0 + a, j0 + b) + (m0 == 0 ? h - 1 : -1)];
+      if (p == 1 && (lane == 31 || tq + 1 >= nq)) qp = q1[row(i0 + a, j0 + b) + (m0 + 2 == h ? 2 - h : 2)];
+      const float k0s = p ? q.x + q.y : qm + q.x;
+      const float k1s = p ? q.y + qp : q.x + q.y;
+      const float2 ni = a == 0 ? qi[0][b] : Q[0][b], pi = a == 0 ? Q[1][b] : qi[1][b];
+      const float2 nj = b == 0 ? qj[a][0] : Q[a][0], pj = b == 0 ? Q[a][1] : qj[a][1];
+      const float dx = local_M<K>(f, U0.x, E0.x, 1.f, k0s + (ni.x + pi.x) + (nj.x + pj.x)) - S0.x;
+      const float dy = local_M<K>(f, U0.y, E0.y, 1.f, k1s + (ni.y + pi.y) + (nj.y + pj.y)) - S0.y;
+      sd0 += dx;
+      sd1 += dy;
+    }
+  if (act) {
+    const long long t = ((long long)I * nc + J) * nc + m0;
+    const float2 me = make_float2(0.125f * se0, 0.125f * se1);
+    *reinterpret_cast<float2*>(Re + t) = me;
+    *reinterpret_cast<float2*>(eH + t) = me;
+    *reinterpret_cast<float2*>(ubH + t) = make_float2(0.125f * su0, 0.125f * su1);
+    *reinterpret_cast<float2*>(SH + t) = make_float2(0.125f * sd0, 0.125f * sd1);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Prolongation-correction, four fine cells per lane (fine side % 4 == 0)
 // ---------------------------------------------------------------------------

@@ -152,6 +152,20 @@ __global__ void __launch_bounds__(128) k_prolong_correct32q(int nc, const float*
                                         blockIdx.x * 32 + threadIdx.x, threadIdx.x, guard, qf);
 }
 
+// Restriction after pre-smoothing on a split finest level with stored q, the
+// defect formed at the first colour only (restrict_split_zr); grid as above.
+template <int K>
+__global__ void __launch_bounds__(128) k_restrict32_split_zr(LevelF f, int nf, const float* __restrict__ e,
+                                                             const float* __restrict__ ub,
+                                                             const float* __restrict__ S, const float* __restrict__ qf,
+                                                             float* __restrict__ Re, float* __restrict__ eH,
+                                                             float* __restrict__ ubH, float* __restrict__ SH) {
+  const int I = blockIdx.z * 4 + threadIdx.y;
+  if (I >= (nf >> 1)) return;  // whole warps
+  restrict_split_zr<K>(f, nf, e, ub, S, qf, Re, eH, ubH, SH, I, blockIdx.y, blockIdx.x * 32 + threadIdx.x,
+                       threadIdx.x);
+}
+
 // FAS source, four cells per lane (n % 4 == 0, n >= 8): grid (ceil(n/128), n, n/4).
 template <int K>
 __global__ void __launch_bounds__(128) k_fas_source32q(LevelF f, int n, const float* __restrict__ Re,
@@ -521,7 +535,10 @@ static void tail_allow_smem() {
 
 // Residual and restriction from level l to l+1: H.Re = R e, H.e = R e (the coarse
 // start), H.ub = R ub, H.S32 = R (M(e) - S); the FAS source follows (fas_source).
-static int restrict_level(const MixedCtx& C, int l, cudaStream_t st) {
+// relaxed: the level's second colour was the last one relaxed (pre-smoothing
+// ran), so on a split finest level with stored q the defect is formed at the
+// first colour only (restrict_split_zr).
+static int restrict_level(const MixedCtx& C, int l, cudaStream_t st, bool relaxed = false) {
   Workspace* ws = C.ws;
   Level& L = ws->lev[l];
   const float* rho = C.need_rho ? L.rho32 : nullptr;
@@ -529,7 +546,15 @@ static int restrict_level(const MixedCtx& C, int l, cudaStream_t st) {
   const int bh = bx_for(H.n);
   if (l == 0 && C.split) {
     const dim3 g((L.n / 4 + 31) / 32, H.n, (H.n + 3) / 4);
-    if (C.qs && C.m.kind == KFR1) {
+    if (C.qs && relaxed) {
+      if (C.m.kind == KFR1)
+        k_restrict32_split_zr<KFR1><<<g, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, L.S32, C.qs, H.Re, H.e, H.ub,
+                                                                H.S32);
+      else
+        k_restrict32_split_zr<KFR2><<<g, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, L.S32, C.qs, H.Re, H.e, H.ub,
+                                                                H.S32);
+      note_launch(1);
+    } else if (C.qs && C.m.kind == KFR1) {
       k_residual_restrict32q<KFR1, SplitLayout, true><<<g, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, rho, L.S32,
                                                                                  H.Re, H.e, H.ub, H.S32, C.qs);
       note_launch(1);
@@ -608,7 +633,7 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode) {
   if ((rc = smooth32(C, l, C.prm->nu1, st))) return rc;
   if (l == 0) prof_end(st);
   if (l == 0) prof_begin(PC_RESTRICT32_FINE, st, 14.0 * L.n3);
-  if ((rc = restrict_level(C, l, st))) return rc;
+  if ((rc = restrict_level(C, l, st, C.prm->nu1 > 0))) return rc;
   if (l == 0) {
     prof_end(st);
     prof_begin(PC_COARSE_LEVELS, st, 0.0);
