@@ -92,7 +92,10 @@ __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast
 // clamped quad and store nothing.
 // QH (f(R) n = 1, 2 on a split level with stored q, in qf): the halo rows'
 // neighbour quantities are read from qf instead of formed from e and u.
-template <int K, class FL = NatLayout, bool QH = false>
+// ZR (f(R), symmetron, after pre-smoothing): the second colour ((i+j+k) odd)
+// was relaxed last and satisfies its local equations, so its defect is taken as
+// zero and only the first colour's is formed (see restrict_split_zr).
+template <int K, class FL = NatLayout, bool QH = false, bool ZR = false>
 __device__ __forceinline__ void restrict_quad(const LevelF& f, int nf, const float* __restrict__ e,
                                               const float* __restrict__ ub, const float* __restrict__ rho,
                                               const float* __restrict__ S, float* __restrict__ Re,
@@ -168,10 +171,18 @@ __device__ __forceinline__ void restrict_quad(const LevelF& f, int nf, const flo
         if (rho) R = FL::q(rho, nf, i0 + a, j0 + b, k0);
       }
       const float4 Ev = E[a][b], Uv = U[a][b];
-      const float dx = local_M<K>(f, Uv.x, Ev.x, R.x, (qm + q.y) + (ni.x + pi.x) + (nj.x + pj.x)) - Sv.x;
-      const float dy = local_M<K>(f, Uv.y, Ev.y, R.y, (q.x + q.z) + (ni.y + pi.y) + (nj.y + pj.y)) - Sv.y;
-      const float dz = local_M<K>(f, Uv.z, Ev.z, R.z, (q.y + q.w) + (ni.z + pi.z) + (nj.z + pj.z)) - Sv.z;
-      const float dv = local_M<K>(f, Uv.w, Ev.w, R.w, (q.z + qp) + (ni.w + pi.w) + (nj.w + pj.w)) - Sv.w;
+      // with ZR the cells k0 + c of colour (a + b + c) & 1 = 1 have zero defect (k0, 2I, 2J even)
+      static_assert(!ZR || K != KCQ, "CQ relaxes by one Newton step: its defect is not zero");
+      const bool odd = (a + b) & 1;
+      float dx = 0.f, dy = 0.f, dz = 0.f, dv = 0.f;
+      if (!ZR || !odd) {
+        dx = local_M<K>(f, Uv.x, Ev.x, R.x, (qm + q.y) + (ni.x + pi.x) + (nj.x + pj.x)) - Sv.x;
+        dz = local_M<K>(f, Uv.z, Ev.z, R.z, (q.y + q.w) + (ni.z + pi.z) + (nj.z + pj.z)) - Sv.z;
+      }
+      if (!ZR || odd) {
+        dy = local_M<K>(f, Uv.y, Ev.y, R.y, (q.x + q.z) + (ni.y + pi.y) + (nj.y + pj.y)) - Sv.y;
+        dv = local_M<K>(f, Uv.w, Ev.w, R.w, (q.z + qp) + (ni.w + pi.w) + (nj.w + pj.w)) - Sv.w;
+      }
       se0 += Ev.x + Ev.y;
       se1 += Ev.z + Ev.w;
       su0 += Uv.x + Uv.y;

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(128) k_residual_restrict32(LevelF f, int nf, c
 
 // Quad versions (fine side % 4 == 0): block (32, 4), lanes along k; FL is the
 // fine level's layout.  Restriction: grid (ceil(nf/128), nc [J], ceil(nc/4) [I]).
-template <int K, class FL = NatLayout, bool QH = false>
+template <int K, class FL = NatLayout, bool QH = false, bool ZR = false>
 __global__ void __launch_bounds__(128) k_residual_restrict32q(LevelF f, int nf, const float* __restrict__ e,
                                                               const float* __restrict__ ub,
                                                               const float* __restrict__ rho,
@@ -137,8 +137,8 @@ __global__ void __launch_bounds__(128) k_residual_restrict32q(LevelF f, int nf, 
                                                               const float* __restrict__ qf) {
   const int I = blockIdx.z * 4 + threadIdx.y;
   if (I >= (nf >> 1)) return;  // whole warps
-  restrict_quad<K, FL, QH>(f, nf, e, ub, rho, S, Re, eH, ubH, SH, I, blockIdx.y, blockIdx.x * 32 + threadIdx.x,
-                           threadIdx.x, qf);
+  restrict_quad<K, FL, QH, ZR>(f, nf, e, ub, rho, S, Re, eH, ubH, SH, I, blockIdx.y, blockIdx.x * 32 + threadIdx.x,
+                               threadIdx.x, qf);
 }
 
 // Prolongation: grid (ceil(nf/128), nf [j], nf/4 [i]).
@@ -568,8 +568,22 @@ static int restrict_level(const MixedCtx& C, int l, cudaStream_t st, bool relaxe
     }
   } else if (L.n % 4 == 0 && L.n >= 8) {
     const dim3 g((L.n / 4 + 31) / 32, H.n, (H.n + 3) / 4);
-    MG_DISPATCH32(C.m.kind, (k_residual_restrict32q<KK><<<g, dim3(32, 4), 0, st>>>(
-                                 C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32, nullptr)));
+    if (relaxed && C.m.kind != KCQ) {
+      switch (C.m.kind) {
+        case KFR0: k_residual_restrict32q<KFR0, NatLayout, false, true><<<g, dim3(32, 4), 0, st>>>(
+                       C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32, nullptr); break;
+        case KFR1: k_residual_restrict32q<KFR1, NatLayout, false, true><<<g, dim3(32, 4), 0, st>>>(
+                       C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32, nullptr); break;
+        case KFR2: k_residual_restrict32q<KFR2, NatLayout, false, true><<<g, dim3(32, 4), 0, st>>>(
+                       C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32, nullptr); break;
+        default: k_residual_restrict32q<KSYM, NatLayout, false, true><<<g, dim3(32, 4), 0, st>>>(
+                       C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32, nullptr); break;
+      }
+      note_launch(1);
+    } else {
+      MG_DISPATCH32(C.m.kind, (k_residual_restrict32q<KK><<<g, dim3(32, 4), 0, st>>>(
+                                   C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32, nullptr)));
+    }
   } else {
     MG_DISPATCH32(C.m.kind, (k_residual_restrict32<KK><<<grid3(H.n, H.n, H.n, bh), bh, 0, st>>>(
                                  C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32)));
