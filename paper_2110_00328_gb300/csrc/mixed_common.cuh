@@ -446,6 +446,75 @@ __device__ __forceinline__ void prolong_quad(int nc, const float* __restrict__ e
   }
 }
 
+// Prolongation-correction of the second colour on a split finest level with
+// stored q (f(R) n = QK), four fine rows per lane: the lane owns the quad
+// k0 = 4tq .. k0+3 of the fine rows (2I+a, 2J+b), a, b in {0, 1} -- the children
+// of the coarse row pair (I, J) -- which interpolate from the nine coarse rows
+// (I-1..I+1, J-1..J+1); prolong_quad reads four coarse rows for each fine row.
+// Each fine row's second-colour pair is corrected (and its q written) exactly
+// as prolong_quad<true, SplitLayout, QK, true> does it.  Grid as the
+// restriction's: (ceil(nf/128), nc [J], ceil(nc/4) [I]), block (32, 4).
+template <int QK>
+__device__ __forceinline__ void prolong_split2x2_second(int nc, const float* __restrict__ eH,
+                                                        const float* __restrict__ Re, const float* __restrict__ ub,
+                                                        float* __restrict__ ef, int I, int J, int tq, int lane,
+                                                        unsigned long long* guard, float* __restrict__ qf) {
+  static_assert(QK == KFR1 || QK == KFR2, "stored q: f(R) n = 1, 2");
+  const int nf = nc << 1, nq = nf >> 2, h = nf >> 1;
+  const bool act = tq < nq;
+  const int t = act ? tq : nq - 1;
+  const int k0 = 4 * t, K0 = 2 * t;
+  const int Km = K0 == 0 ? nc - 1 : K0 - 1, Kp = K0 + 2 == nc ? 0 : K0 + 2;
+  const int Iv[3] = {I == 0 ? nc - 1 : I - 1, I, I + 1 == nc ? 0 : I + 1};
+  const int Jv[3] = {J == 0 ? nc - 1 : J - 1, J, J + 1 == nc ? 0 : J + 1};
+  const bool edge_m = lane == 0, edge_p = lane == 31 || tq + 1 >= nq;
+  // coarse differences eH - Re of the nine rows at K0, K0+1 (and K0-1, K0+2 at the row ends)
+  float2 d[3][3];
+  float dm[3][3], dp[3][3];
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+#pragma unroll
+    for (int y = 0; y < 3; ++y) {
+      const long long r = ((long long)Iv[x] * nc + Jv[y]) * nc;
+      const float2 a = ld2(eH + r + K0), b = ld2(Re + r + K0);
+      d[x][y] = make_float2(a.x - b.x, a.y - b.y);
+      dm[x][y] = edge_m ? eH[r + Km] - Re[r + Km] : 0.f;
+      dp[x][y] = edge_p ? eH[r + Kp] - Re[r + Kp] : 0.f;
+    }
+  constexpr float w = 1.f / 64.f;
+  const long long H = (long long)nf * nf * h;
+  unsigned ng = 0;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int x2 = a ? 2 : 0, y2 = b ? 2 : 0;  // the coarse neighbour rows of fine row (2I+a, 2J+b)
+      const float2 A = d[1][1], B = d[x2][1], Cc = d[1][y2], D = d[x2][y2];
+      const float Rx = 9.f * A.x + 3.f * (B.x + Cc.x) + D.x;
+      const float Ry = 9.f * A.y + 3.f * (B.y + Cc.y) + D.y;
+      float Rm = __shfl_up_sync(0xffffffffu, Ry, 1);
+      float Rp = __shfl_down_sync(0xffffffffu, Rx, 1);
+      if (edge_m) Rm = 9.f * dm[1][1] + 3.f * (dm[x2][1] + dm[1][y2]) + dm[x2][y2];
+      if (edge_p) Rp = 9.f * dp[1][1] + 3.f * (dp[x2][1] + dp[1][y2]) + dp[x2][y2];
+      const bool odd = (a + b) & 1;  // (i + j) & 1 of the fine row
+      const float cA = odd ? (3.f * Rx + Rm) * w : (3.f * Rx + Ry) * w;
+      const float cB = odd ? (3.f * Ry + Rx) * w : (3.f * Ry + Rp) * w;
+      const int i = 2 * I + a, j = 2 * J + b;
+      const long long o1 = H + ((long long)i * nf + j) * h + (k0 >> 1);
+      const float2 old = ld2(ef + o1), u = ld2(ub + o1);
+      float vA = old.x + cA, vB = old.y + cB;
+      const bool gA = !(u.x + vA > 0.f), gB = !(u.y + vB > 0.f);
+      if (gA) vA = 0.5f * (old.x - u.x);
+      if (gB) vB = 0.5f * (old.y - u.y);
+      ng += (unsigned)gA + (unsigned)gB;
+      if (act) {
+        *reinterpret_cast<float2*>(ef + o1) = make_float2(vA, vB);
+        *reinterpret_cast<float2*>(qf + o1) = make_float2(dw<QK>(u.x, vA), dw<QK>(u.y, vB));
+      }
+    }
+  if (act) count_guards(guard, ng);
+}
+
 // 1/x in FP64 by one Newton-Raphson refinement y1 = y0 (2 - x y0) of a
 // single-precision reciprocal y0: the relative error of y0 (below 2^-22) is
 // squared, leaving about 2^-44 ~ 6e-14, far below what the residual needs.

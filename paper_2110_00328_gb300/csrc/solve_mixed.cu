@@ -27,6 +27,8 @@
 
 #include <chrono>
 
+#include <mutex>
+
 #include "mg_common.cuh"
 #include "mg_internal.h"
 #include "mixed_common.cuh"
@@ -150,6 +152,19 @@ __global__ void __launch_bounds__(128) k_prolong_correct32q(int nc, const float*
                                                             float* __restrict__ qf = nullptr) {
   prolong_quad<FR, FL, QK, SECOND_ONLY>(nc, eH, Re, ub, ef, blockIdx.z * 4 + threadIdx.y, blockIdx.y,
                                         blockIdx.x * 32 + threadIdx.x, threadIdx.x, guard, qf);
+}
+
+// Second-colour prolongation on a split finest level with stored q, four fine
+// rows per lane (prolong_split2x2_second); grid as the restriction's.
+template <int QK>
+__global__ void __launch_bounds__(128) k_prolong32_split2x2(int nc, const float* __restrict__ eH,
+                                                            const float* __restrict__ Re, const float* __restrict__ ub,
+                                                            float* __restrict__ ef, unsigned long long* guard,
+                                                            float* __restrict__ qf) {
+  const int I = blockIdx.z * 4 + threadIdx.y;
+  if (I >= nc) return;  // whole warps
+  prolong_split2x2_second<QK>(nc, eH, Re, ub, ef, I, blockIdx.y, blockIdx.x * 32 + threadIdx.x, threadIdx.x, guard,
+                              qf);
 }
 
 // Restriction after pre-smoothing on a split finest level with stored q, the
@@ -322,6 +337,67 @@ static int slab_planes(const MixedCtx& C, int n) {
   return P >= n ? 0 : (P < 2 ? 2 : P);
 }
 
+// L2 residency of the stored neighbour quantity q on the split finest level:
+// each colour pass reads the other colour's q and writes its own, and the
+// restriction reads q of its halo rows, so keeping q in L2 (a persisting
+// access-policy window on the colour-pass launches) spares those DRAM round
+// trips (measured at 256^3: 60.6 instead of 66.7 us per sweep, 37 instead of
+// 43 us per restriction).  The set-aside (cudaLimitPersistingL2CacheSize) is a
+// per-context cache configuration, raised once per device to the size of q
+// (capped by the device); the window's hit ratio is scaled so that the
+// persisting lines fit in it, and every solve returns its lines to normal
+// status at its end.  Device attributes are read once per device.
+struct L2Window {
+  bool ok = false;
+  cudaAccessPolicyWindow w = {};
+};
+static L2Window q_window(const MixedCtx& C) {
+  L2Window r;
+  if (!C.qs) return r;
+  struct Caps {
+    int state = 0;  // 0 unknown, 1 usable, -1 not offered
+    size_t max_persist = 0, max_window = 0, limit = 0;
+  };
+  static std::mutex mu;
+  static Caps caps[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return r;
+  }
+  const size_t bytes = C.ws->lev[0].n3 * sizeof(float);
+  std::lock_guard<std::mutex> lk(mu);
+  Caps& c = caps[dev];
+  if (c.state == 0) {
+    int mp = 0, mw = 0;
+    const bool got = cudaDeviceGetAttribute(&mp, cudaDevAttrMaxPersistingL2CacheSize, dev) == cudaSuccess &&
+                     cudaDeviceGetAttribute(&mw, cudaDevAttrMaxAccessPolicyWindowSize, dev) == cudaSuccess &&
+                     cudaDeviceGetLimit(&c.limit, cudaLimitPersistingL2CacheSize) == cudaSuccess;
+    if (!got) cudaGetLastError();
+    c.state = got && mp > 0 && mw > 0 ? 1 : -1;
+    c.max_persist = (size_t)mp;
+    c.max_window = (size_t)mw;
+  }
+  if (c.state < 0) return r;
+  const size_t want = bytes < c.max_persist ? bytes : c.max_persist;
+  if (c.limit < want) {
+    if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
+      cudaGetLastError();
+      c.state = -1;
+      return r;
+    }
+    c.limit = want;
+  }
+  const size_t nb = bytes < c.max_window ? bytes : c.max_window;
+  r.w.base_ptr = C.qs;
+  r.w.num_bytes = nb;
+  r.w.hitRatio = (float)(c.limit >= nb ? 1.0 : (double)c.limit / (double)nb);
+  r.w.hitProp = cudaAccessPropertyPersisting;
+  r.w.missProp = cudaAccessPropertyStreaming;
+  r.ok = true;
+  return r;
+}
+
 static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
   Level& L = C.ws->lev[l];
   const float* rho = C.need_rho ? L.rho32 : nullptr;
@@ -352,11 +428,17 @@ static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
             cfg.gridDim = dim3(blocks);
             cfg.blockDim = dim3(32, 4);
             cfg.stream = st;
-            cudaLaunchAttribute attr[1];
+            cudaLaunchAttribute attr[2];
             attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
             attr[0].val.programmaticStreamSerializationAllowed = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
+            const L2Window qw = q_window(C);
+            if (qw.ok) {
+              attr[1].id = cudaLaunchAttributeAccessPolicyWindow;
+              attr[1].val.accessPolicyWindow = qw.w;
+              cfg.numAttrs = 2;
+            }
             const int pdl = passes++ > 0 ? 1 : 2;
             const float *ubc = L.ub, *Sc = L.S32, *no_rho = nullptr;
             if (C.m.kind == KFR1)
@@ -602,15 +684,14 @@ static int prolong_level(const MixedCtx& C, int l, cudaStream_t st, bool both = 
     const dim3 g((L.n / 4 + 31) / 32, L.n, L.n / 4);
     // with post-smoothing the first colour's corrections would be overwritten unread (prolong_quad)
     const bool second_only = !both && C.prm->nu2 >= 1;
+    const dim3 g2((L.n / 4 + 31) / 32, H.n, (H.n + 3) / 4);
     if (C.qs && C.m.kind == KFR1 && second_only)
-      k_prolong_correct32q<true, SplitLayout, KFR1, true><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e,
-                                                                                      C.guard, C.qs);
+      k_prolong32_split2x2<KFR1><<<g2, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard, C.qs);
+    else if (C.qs && C.m.kind == KFR2 && second_only)
+      k_prolong32_split2x2<KFR2><<<g2, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard, C.qs);
     else if (C.qs && C.m.kind == KFR1)
       k_prolong_correct32q<true, SplitLayout, KFR1><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard,
                                                                                 C.qs);
-    else if (C.qs && second_only)
-      k_prolong_correct32q<true, SplitLayout, KFR2, true><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e,
-                                                                                      C.guard, C.qs);
     else if (C.qs)
       k_prolong_correct32q<true, SplitLayout, KFR2><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard,
                                                                                 C.qs);
@@ -917,6 +998,7 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
     }
   }
   if (status == MGGLAM_OK && !isfinite(eps)) status = MGGLAM_ERR_NONFINITE;
+  if (q_window(C).ok) cudaCtxResetPersistingL2Cache();  // q's lines back to normal for later kernels
   MG_CUDA_TRY(cudaMemcpyAsync(ws->h_scalars + SC_GUARD, C.guard, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                               st));
   MG_CUDA_TRY(cudaStreamSynchronize(st));
