@@ -270,6 +270,15 @@ __device__ __forceinline__ float update_e_warm(const LevelF& f, float u, float e
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
+// Local update of the quad smoother: f(R) n = 1, 2 warm-started from the cell's
+// current correction (update_e_warm, the whole warp together), else the closed
+// form (update_e_fast).
+template <int K>
+__device__ __forceinline__ float update_quad(const LevelF& f, float u, float e, float rho, float s, float Lnb) {
+  if constexpr (K == KFR1 || K == KFR2) return update_e_warm<K>(f, u, e, s, Lnb);
+  else return update_e_fast<K>(f, u, e, rho, s, Lnb);
+}
+
 template <int K>
 __device__ __forceinline__ void smooth_quad(const LevelF& f, int n, float* __restrict__ e,
                                             const float* __restrict__ ub, const float* __restrict__ rho,
@@ -313,8 +322,8 @@ __device__ __forceinline__ void smooth_quad(const LevelF& f, int n, float* __res
                      (nbq<K>(Uip.x, Eip.x) + nbq<K>(Uim.x, Eim.x));
     const float LB = (qy + qw) + (nbq<K>(Ujp.z, Ejp.z) + nbq<K>(Ujm.z, Ejm.z)) +
                      (nbq<K>(Uip.z, Eip.z) + nbq<K>(Uim.z, Eim.z));
-    const float eA = update_e_fast<K>(f, U.x, E.x, R.x, Sv.x, LA);
-    const float eB = update_e_fast<K>(f, U.z, E.z, R.z, Sv.z, LB);
+    const float eA = update_quad<K>(f, U.x, E.x, R.x, Sv.x, LA);
+    const float eB = update_quad<K>(f, U.z, E.z, R.z, Sv.z, LB);
     if (act) {
       e0[0] = eA;
       e0[2] = eB;
@@ -331,8 +340,8 @@ __device__ __forceinline__ void smooth_quad(const LevelF& f, int n, float* __res
                      (nbq<K>(Uip.y, Eip.y) + nbq<K>(Uim.y, Eim.y));
     const float LB = (qz + qp) + (nbq<K>(Ujp.w, Ejp.w) + nbq<K>(Ujm.w, Ejm.w)) +
                      (nbq<K>(Uip.w, Eip.w) + nbq<K>(Uim.w, Eim.w));
-    const float eA = update_e_fast<K>(f, U.y, E.y, R.y, Sv.y, LA);
-    const float eB = update_e_fast<K>(f, U.w, E.w, R.w, Sv.w, LB);
+    const float eA = update_quad<K>(f, U.y, E.y, R.y, Sv.y, LA);
+    const float eB = update_quad<K>(f, U.w, E.w, R.w, Sv.w, LB);
     if (act) {
       e0[1] = eA;
       e0[3] = eB;
