@@ -295,6 +295,7 @@ struct MixedCtx {
   int tail_level;     // first level (>= 1) run by the one-block tail kernel, or -1
   float* qs;          // split f(R) n = 1, 2: the finest level's stored neighbour quantity, else nullptr
   unsigned long long* guard;  // positivity-guard replacements of this solve (workspace scalar)
+  const struct L2Window* l2 = nullptr;  // persisting L2 window over qs for the colour passes, or nullptr
 };
 
 static FFC* ffc_of(Workspace* ws) { return reinterpret_cast<FFC*>(ws->scalars + SC_FFC); }
@@ -342,61 +343,85 @@ static int slab_planes(const MixedCtx& C, int n) {
 // restriction reads q of its halo rows, so keeping q in L2 (a persisting
 // access-policy window on the colour-pass launches) spares those DRAM round
 // trips (measured at 256^3: 60.6 instead of 66.7 us per sweep, 37 instead of
-// 43 us per restriction).  The set-aside (cudaLimitPersistingL2CacheSize) is a
-// per-context cache configuration, raised once per device to the size of q
-// (capped by the device); the window's hit ratio is scaled so that the
-// persisting lines fit in it, and every solve returns its lines to normal
-// status at its end.  Device attributes are read once per device.
+// 43 us per restriction).  The L2 set-aside for persisting lines
+// (cudaLimitPersistingL2CacheSize, a per-context setting) takes that capacity
+// from every other kernel of the process, so a solve raises it to the size of
+// q only for its own duration and restores the previous value at its end
+// (with its persisting lines returned to normal status); meshes whose q does
+// not fit in the device's persisting capacity go without.
 struct L2Window {
   bool ok = false;
   cudaAccessPolicyWindow w = {};
+  size_t prev_limit = 0;  // the set-aside before the solve
 };
-static L2Window q_window(const MixedCtx& C) {
-  L2Window r;
-  if (!C.qs) return r;
-  struct Caps {
-    int state = 0;  // 0 unknown, 1 usable, -1 not offered
-    size_t max_persist = 0, max_window = 0, limit = 0;
-  };
+
+// Device capacities, read once per device.
+struct L2Caps {
+  int state = 0;  // 0 unknown, 1 usable, -1 not offered
+  size_t max_persist = 0, max_window = 0;
+};
+static bool l2_caps(int dev, L2Caps* out) {
   static std::mutex mu;
-  static Caps caps[64];
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
-    cudaGetLastError();
-    return r;
-  }
-  const size_t bytes = C.ws->lev[0].n3 * sizeof(float);
+  static L2Caps caps[64];
+  if (dev < 0 || dev >= 64) return false;
   std::lock_guard<std::mutex> lk(mu);
-  Caps& c = caps[dev];
+  L2Caps& c = caps[dev];
   if (c.state == 0) {
     int mp = 0, mw = 0;
     const bool got = cudaDeviceGetAttribute(&mp, cudaDevAttrMaxPersistingL2CacheSize, dev) == cudaSuccess &&
-                     cudaDeviceGetAttribute(&mw, cudaDevAttrMaxAccessPolicyWindowSize, dev) == cudaSuccess &&
-                     cudaDeviceGetLimit(&c.limit, cudaLimitPersistingL2CacheSize) == cudaSuccess;
+                     cudaDeviceGetAttribute(&mw, cudaDevAttrMaxAccessPolicyWindowSize, dev) == cudaSuccess;
     if (!got) cudaGetLastError();
     c.state = got && mp > 0 && mw > 0 ? 1 : -1;
     c.max_persist = (size_t)mp;
     c.max_window = (size_t)mw;
   }
-  if (c.state < 0) return r;
-  const size_t want = bytes < c.max_persist ? bytes : c.max_persist;
-  if (c.limit < want) {
-    if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
-      cudaGetLastError();
-      c.state = -1;
-      return r;
-    }
-    c.limit = want;
+  *out = c;
+  return c.state > 0;
+}
+
+// At the start of a solve: the window over q and the raised set-aside, if q fits.
+static L2Window q_window_begin(const MixedCtx& C) {
+  L2Window r;
+  if (!C.qs) return r;
+  int dev = 0;
+  L2Caps caps;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return r;
   }
-  const size_t nb = bytes < c.max_window ? bytes : c.max_window;
+  if (!l2_caps(dev, &caps)) return r;
+  const size_t bytes = C.ws->lev[0].n3 * sizeof(float);
+  if (bytes > caps.max_persist || bytes > caps.max_window) return r;
+  if (cudaDeviceGetLimit(&r.prev_limit, cudaLimitPersistingL2CacheSize) != cudaSuccess ||
+      (r.prev_limit < bytes && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, bytes) != cudaSuccess)) {
+    cudaGetLastError();
+    return r;
+  }
   r.w.base_ptr = C.qs;
-  r.w.num_bytes = nb;
-  r.w.hitRatio = (float)(c.limit >= nb ? 1.0 : (double)c.limit / (double)nb);
+  r.w.num_bytes = bytes;
+  r.w.hitRatio = 1.f;
   r.w.hitProp = cudaAccessPropertyPersisting;
   r.w.missProp = cudaAccessPropertyStreaming;
   r.ok = true;
   return r;
 }
+
+// At the end of a solve (every return path): q's lines back to normal, the
+// set-aside as it was.
+struct L2Scope {
+  L2Window w;
+  explicit L2Scope(const L2Window& v) : w(v) {}
+  L2Scope(const L2Scope&) = delete;
+  L2Scope& operator=(const L2Scope&) = delete;
+  ~L2Scope() {
+    if (!w.ok) return;
+    cudaCtxResetPersistingL2Cache();
+    size_t now = 0;
+    if (cudaDeviceGetLimit(&now, cudaLimitPersistingL2CacheSize) == cudaSuccess && now != w.prev_limit)
+      cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, w.prev_limit);
+    cudaGetLastError();
+  }
+};
 
 static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
   Level& L = C.ws->lev[l];
@@ -433,10 +458,9 @@ static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
             attr[0].val.programmaticStreamSerializationAllowed = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            const L2Window qw = q_window(C);
-            if (qw.ok) {
+            if (C.l2 && C.l2->ok) {
               attr[1].id = cudaLaunchAttributeAccessPolicyWindow;
-              attr[1].val.accessPolicyWindow = qw.w;
+              attr[1].val.accessPolicyWindow = C.l2->w;
               cfg.numAttrs = 2;
             }
             const int pdl = passes++ > 0 ? 1 : 2;
@@ -895,6 +919,8 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
   // the split level never runs the fused sweep, so its second buffer holds q
   C.qs = C.split && (C.m.kind == KFR1 || C.m.kind == KFR2) ? C.ws->lev[0].e_alt : nullptr;
   C.guard = guard_of(C.ws);
+  const L2Scope l2s(q_window_begin(C));
+  C.l2 = &l2s.w;
   C.tail_level = -1;  // the one-block tail runs V-cycles only
   const long long tail_cells = prm->tail_cells == 0 ? 512 : (prm->tail_cells > kTailMaxCells ? kTailMaxCells : prm->tail_cells);
   for (int l = 1; l < C.ws->nlev && tail_cells > 0 && prm->cycle == 0; ++l)
@@ -998,7 +1024,6 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
     }
   }
   if (status == MGGLAM_OK && !isfinite(eps)) status = MGGLAM_ERR_NONFINITE;
-  if (q_window(C).ok) cudaCtxResetPersistingL2Cache();  // q's lines back to normal for later kernels
   MG_CUDA_TRY(cudaMemcpyAsync(ws->h_scalars + SC_GUARD, C.guard, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                               st));
   MG_CUDA_TRY(cudaStreamSynchronize(st));
