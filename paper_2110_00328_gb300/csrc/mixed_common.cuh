@@ -648,10 +648,14 @@ __device__ __forceinline__ ff ff_w(ff u) {
 // The CTA marches up its chunk of planes with a three-plane ring of w and u in
 // shared memory; the doubles of plane i+2 are loaded into registers while
 // plane i is computed, so the global-load latency overlaps the arithmetic.
+// zero_e, zero_q (may be null): arrays of the level's layout set to zero at every
+// cell, the next inner solve's initial correction and its stored Delta w(u, 0).
 template <int K, int TJ, int TK, bool SPLIT = false>
 __device__ __forceinline__ double outer_residual_tile_ff(const FFC& C, int n, int chunk, const double* __restrict__ u,
                                                          const float* __restrict__ rho, float* __restrict__ ub,
-                                                         float* __restrict__ tau, int tile, int cb) {
+                                                         float* __restrict__ tau, int tile, int cb,
+                                                         float* __restrict__ zero_e = nullptr,
+                                                         float* __restrict__ zero_q = nullptr) {
   static_assert(K != KCQ, "CQ keeps the FP64 residual");
   constexpr int PJ = TJ + 2, PK = TK + 2, PS = PJ * PK, NT = TJ * TK, NE = (PS + NT - 1) / NT;
   __shared__ float s_wh[3][PS], s_wl[3][PS], s_uh[3][PS], s_ul[3][PS];
@@ -744,6 +748,8 @@ __device__ __forceinline__ double outer_residual_tile_ff(const FFC& C, int n, in
     const long long o = SPLIT ? split_idx(n, i, jg, kg) : (long long)g;  // the level's layout
     ub[o] = ff_to_float(uc);
     tau[o] = tv;
+    if (zero_e) zero_e[o] = 0.f;
+    if (zero_q) zero_q[o] = 0.f;
     acc += tv * tv;
     __syncthreads();
   }
@@ -758,10 +764,13 @@ __global__ void __launch_bounds__(TJ* TK) k_outer_residual_ff(const FFC* __restr
                                                               const float* __restrict__ rho,
                                                               float* __restrict__ ub, float* __restrict__ tau,
                                                               double* __restrict__ partials,
-                                                              const int* __restrict__ skip = nullptr) {
+                                                              const int* __restrict__ skip = nullptr,
+                                                              float* __restrict__ zero_e = nullptr,
+                                                              float* __restrict__ zero_q = nullptr) {
   if (skip && *skip) return;
   const FFC c = *C;
-  const double a = outer_residual_tile_ff<K, TJ, TK, SPLIT>(c, n, chunk, u, rho, ub, tau, blockIdx.x, blockIdx.y);
+  const double a = outer_residual_tile_ff<K, TJ, TK, SPLIT>(c, n, chunk, u, rho, ub, tau, blockIdx.x, blockIdx.y,
+                                                            zero_e, zero_q);
   if (threadIdx.x == 0) partials[blockIdx.x + blockIdx.y * gridDim.x] = a;
 }
 
@@ -780,7 +789,9 @@ __global__ void __launch_bounds__(256) k_background_residual_ff(const FFC* __res
                                                                 double* __restrict__ u, double ubar,
                                                                 const float* __restrict__ rho,
                                                                 float* __restrict__ ub, float* __restrict__ tau,
-                                                                double* __restrict__ partials) {
+                                                                double* __restrict__ partials,
+                                                                float* __restrict__ zero_e = nullptr,
+                                                                float* __restrict__ zero_q = nullptr) {
   static_assert(K != KCQ, "CQ keeps the FP64 residual");
   if (!isnan(u[0])) return;
   const FFC c = *C;
@@ -813,6 +824,8 @@ __global__ void __launch_bounds__(256) k_background_residual_ff(const FFC* __res
       const long long o = SPLIT ? split_idx(n, i, j, k) : t;
       ub[o] = ubf;
       tau[o] = tv;
+      if (zero_e) zero_e[o] = 0.f;
+      if (zero_q) zero_q[o] = 0.f;
       acc += tv * tv;
     }
   }

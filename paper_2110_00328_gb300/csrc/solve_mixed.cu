@@ -824,7 +824,7 @@ static int launch_outer_residual_ff(const MixedCtx& C, double* field, int* block
       int* flag = reinterpret_cast<int*>(ws->scalars + SC_FLAG);
       if (C.split)
         k_background_residual_ff<K, true><<<grid, 256, 0, st>>>(ffc, F.n, field, C.m.ubar, C.rho, F.ub, F.S32,
-                                                                 ws->partials);
+                                                                 ws->partials, F.e, C.qs);
       else
         k_background_residual_ff<K, false><<<grid, 256, 0, st>>>(ffc, F.n, field, C.m.ubar, C.rho, F.ub, F.S32,
                                                                   ws->partials);
@@ -834,7 +834,7 @@ static int launch_outer_residual_ff(const MixedCtx& C, double* field, int* block
     }
     if (C.split)
       k_outer_residual_ff<K, kRTJ, kRTK, true><<<grid, kRTJ * kRTK, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub,
-                                                                             F.S32, ws->partials, skip);
+                                                                             F.S32, ws->partials, skip, F.e, C.qs);
     else
       k_outer_residual_ff<K, kRTJ, kRTK><<<grid, kRTJ * kRTK, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub, F.S32,
                                                                        ws->partials, skip);
@@ -883,6 +883,11 @@ static int launch_outer_residual_t(const MixedCtx& C, double* field, int* blocks
   }
   return MGGLAM_OK;
 }
+
+// Whether the outer residual pass also zeroes the finest level's e and q (the
+// split tiled float-float kernels write the zeros beside ub and tau; otherwise
+// the outer step clears them with memsets).
+static bool residual_zeroes_e(const MixedCtx& C) { return C.split && C.ff_resid && bg_residual_tiled(C.ws->lev[0].n); }
 
 // bg_first: the solve's first residual, on a mesh where the background start is
 // fused into it (fused_background_start); the field's background fill happens there.
@@ -998,8 +1003,10 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
     }
     const double eps_before = eps;
     int done = 0;
-    MG_CUDA_TRY(cudaMemsetAsync(F.e, 0, F.n3 * sizeof(float), st));
-    if (C.qs) MG_CUDA_TRY(cudaMemsetAsync(C.qs, 0, F.n3 * sizeof(float), st));  // Delta w(u, 0) = 0
+    if (!residual_zeroes_e(C)) {
+      MG_CUDA_TRY(cudaMemsetAsync(F.e, 0, F.n3 * sizeof(float), st));
+      if (C.qs) MG_CUDA_TRY(cudaMemsetAsync(C.qs, 0, F.n3 * sizeof(float), st));  // Delta w(u, 0) = 0
+    }
     for (int c = 0; c < inner && cyc < prm->max_cycles; ++c, ++cyc, ++done)
       if ((rc = (fmg && c == 0) ? fmg_start32(C, st) : vcycle32(C, 0, st, C.prm->cycle))) return rc;
     prof_begin(PC_APPLY_CORR, st, 20.0 * n3);
