@@ -226,10 +226,11 @@ constexpr float kWarmStep = 1e-2f;
 // When the first step of every lane of the warp is at most kWarmStep (u + e),
 // a second step leaves at most eps^4 <= 1e-8: an error of at most ~1e-6 of the
 // update itself, which shrinks with it as the iteration converges.  Otherwise
-// the warp takes the closed-form start and its polish (update_e_fast).  All 32
-// lanes of the warp call this together.
+// the warp takes the closed-form start and its polish (update_e_fast).  The
+// lanes named in warp_mask (all 32 by default) call this together.
 template <int K>
-__device__ __forceinline__ float update_e_warm(const LevelF& f, float u, float e, float s, float Lnb) {
+__device__ __forceinline__ float update_e_warm(const LevelF& f, float u, float e, float s, float Lnb,
+                                               unsigned warp_mask = 0xffffffffu) {
   static_assert(K == KFR1 || K == KFR2, "warm start: f(R) n = 1, 2");
   const float B = Lnb * (1.f / 6.f) + f.al * s;
   const float ru = frcp(u);
@@ -246,7 +247,7 @@ __device__ __forceinline__ float update_e_warm(const LevelF& f, float u, float e
   float Ue;
   const float dx = newton(e, &Ue);
   const bool near = Ue > 0.f && fabsf(dx) <= kWarmStep * Ue;
-  if (__all_sync(0xffffffffu, near)) {
+  if (__all_sync(warp_mask, near)) {
     const float x = e - dx;
     return x - newton(x, &Ue);
   }

@@ -53,7 +53,10 @@ __device__ __forceinline__ void tail_smooth(const LevelF& f, int n, float* e, co
         const int k = 2 * kk + ((i + j + parity) & 1);
         const int c = (i * n + j) * n + k;
         const float Lnb = nb_sum_g<K>(e, ub, n, i, j, k);
-        e[c] = update_e_fast<K>(f, ub[c], e[c], rho ? rho[c] : 1.f, S[c], Lnb);
+        if constexpr (K == KFR1 || K == KFR2)
+          e[c] = update_e_warm<K>(f, ub[c], e[c], S[c], Lnb, __activemask());  // the lanes still in the loop
+        else
+          e[c] = update_e_fast<K>(f, ub[c], e[c], rho ? rho[c] : 1.f, S[c], Lnb);
       }
       __syncthreads();
     }
