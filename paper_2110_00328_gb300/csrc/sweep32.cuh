@@ -233,16 +233,19 @@ __device__ __forceinline__ float update_e_warm(const LevelF& f, float u, float e
                                                unsigned warp_mask = 0xffffffffu) {
   static_assert(K == KFR1 || K == KFR2, "warm start: f(R) n = 1, 2");
   const float B = Lnb * (1.f / 6.f) + f.al * s;
-  const float ru = frcp(u);
+  const float c = f.alK * frcp(u);
+  // Newton step G/G' with numerator and denominator multiplied by U^2 (U = u + x),
+  // so that one reciprocal serves: G U^2 = (Delta w(x) - B) U^2 + (al K/u) x U and
+  // G' U^2 = w'(U) U^2 + al K, with w'(U) = 2U (n = 1) or 3U^2 (n = 2).
   auto newton = [&](float x, float* Ue_out) {
     const float Ue = u + x;
-    const float rU = frcp(Ue);
-    const float G = dw<K>(u, x) + f.alK * x * ru * rU - B;
-    float dG = f.alK * rU * rU;
-    if constexpr (K == KFR1) dG += 2.f * Ue;
-    else dG += 3.f * Ue * Ue;
+    const float U2 = Ue * Ue;
+    const float num = fmaf(c * x, Ue, (dw<K>(u, x) - B) * U2);
+    float den;
+    if constexpr (K == KFR1) den = fmaf(2.f * Ue, U2, f.alK);
+    else den = fmaf(3.f * U2, U2, f.alK);
     *Ue_out = Ue;
-    return fdiv(G, dG);
+    return num * frcp(den);
   };
   float Ue;
   const float dx = newton(e, &Ue);
