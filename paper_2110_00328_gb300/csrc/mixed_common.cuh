@@ -756,6 +756,157 @@ __device__ __forceinline__ double outer_residual_tile_ff(const FFC& C, int n, in
   return block_sum((double)acc);
 }
 
+// The same residual for two adjacent cells per thread (k = k0 + 2x and
+// k0 + 2x + 1) on a TJ x 64 tile, TJ x 32 threads.  The three-plane ring holds
+// w and u as (hi, lo) pairs, rows padded so that a thread's two cells are one
+// 16-byte shared-memory access; the halo (TJ + 2) x 66 is converted once per
+// plane (1.29 conversions a cell instead of 1.33 with 8 x 32 tiles of one cell
+// a thread), and the two cells share the per-plane bookkeeping, the address
+// arithmetic and, on a split level, one index into both colours (cells 2m and
+// 2m + 1 of a row sit at the same k/2 of the two colour arrays).  The six-
+// neighbour sum and the source terms of each cell are formed in the same order
+// as in outer_residual_tile_ff, so each cell's residual is the same float.
+template <int K, int TJ, bool SPLIT>
+__global__ void __launch_bounds__(TJ * 32) k_outer_residual_ff2(const FFC* __restrict__ Cp, int n, int chunk,
+                                                               const double* __restrict__ u,
+                                                               const float* __restrict__ rho, float* __restrict__ ub,
+                                                               float* __restrict__ tau, double* __restrict__ partials,
+                                                               const int* __restrict__ skip,
+                                                               float* __restrict__ zero_e, float* __restrict__ zero_q) {
+  static_assert(K != KCQ, "CQ keeps the FP64 residual");
+  if (skip && *skip) return;
+  const FFC C = *Cp;
+  constexpr int TK = 64, NT = TJ * 32;
+  constexpr int RW = TK + 2;         // halo row: k0 - 1 .. k0 + 64
+  constexpr int RS = RW + 2;         // slot row stride; element x of a halo row at x + 1
+  constexpr int PE = (TJ + 2) * RW;  // halo elements a plane
+  constexpr int PS = (TJ + 2) * RS;
+  constexpr int NE = (PE + NT - 1) / NT;
+  __shared__ __align__(16) float2 s_w[3][PS];
+  __shared__ __align__(16) float2 s_u[3][PS];
+  const int tiles_k = n / TK;
+  const int k0 = (blockIdx.x % tiles_k) * TK;
+  const int j0 = (blockIdx.x / tiles_k) * TJ;
+  const int i0 = blockIdx.y * chunk;
+  const int i1 = min(i0 + chunk, n);
+  const int t = threadIdx.x;
+  const int ty = t >> 5, tx = t & 31;
+  const int jg = j0 + ty, kg = k0 + 2 * tx;
+  const int cc = (ty + 1) * RS + 2 * tx + 2;  // slot index of cell kg; cell kg + 1 at cc + 1
+  const size_t nn = (size_t)n * n;
+  size_t off[NE];
+  int pos[NE];
+#pragma unroll
+  for (int m = 0; m < NE; ++m) {
+    const int c = t + m * NT;
+    const int y = c / RW, x = c - y * RW;
+    off[m] = c < PE ? (size_t)wrapi(j0 + y - 1, n) * n + wrapi(k0 + x - 1, n) : 0;
+    pos[m] = c < PE ? y * RS + x + 1 : -1;
+  }
+  double pre[NE];
+  auto fetch = [&](int p) {
+    const int ig = p < 0 ? p + n : (p >= n ? p - n : p);
+    const double* base = u + (size_t)ig * nn;
+#pragma unroll
+    for (int m = 0; m < NE; ++m) pre[m] = pos[m] >= 0 ? base[off[m]] : 0.0;
+  };
+  auto commit = [&](int slot) {
+#pragma unroll
+    for (int m = 0; m < NE; ++m)
+      if (pos[m] >= 0) {
+        const ff uu = ff_from_double(pre[m]);
+        const ff w = ff_w<K>(uu);
+        s_w[slot][pos[m]] = make_float2(w.hi, w.lo);
+        s_u[slot][pos[m]] = make_float2(uu.hi, uu.lo);
+      }
+  };
+  auto lds4 = [](const float2* p) { return *reinterpret_cast<const float4*>(p); };
+  // the residual of one cell from its ring values (outer_residual_tile_ff's order)
+  auto cell = [&](ff uc, ff wc, ff wim, ff wip, ff wjm, ff wjp, ff wkm, ff wkp, float r) -> float {
+    ffacc La = acc_of(wim);
+    acc_add(La, wip);
+    acc_add(La, wjm);
+    acc_add(La, wjp);
+    acc_add(La, wkm);
+    acc_add(La, wkp);
+    {
+      const ff w6 = two_prod(wc.hi, -6.f);
+      acc_add(La, w6.hi, __fmaf_rn(wc.lo, -6.f, w6.lo));
+    }
+    const ff L = acc_ff(La);
+    if constexpr (is_fr(K)) {
+      ffacc v = acc_of(C.c0);
+      const ff p1 = two_prod(C.c1.hi, r);
+      acc_add(v, p1.hi, __fmaf_rn(C.c1.lo, r, p1.lo));
+      const ff p2 = two_prod(C.c2.hi, L.hi);
+      acc_add(v, -p2.hi, -__fmaf_rn(C.c2.hi, L.lo, __fmaf_rn(C.c2.lo, L.hi, p2.lo)));
+      const ff q = ff_div(C.K, uc);
+      acc_add(v, -q.hi, -q.lo);
+      return -acc_float(v);
+    } else {
+      const ff a = ff_sub(ff_mul(ff_mul_f(C.c1, r), C.rat3), ff{1.f, 0.f});
+      const ff b = ff_add(ff_mul(a, uc), ff_mul(ff_sqr(uc), uc));
+      return -ff_to_float(ff_sub(ff_mul(C.c2, L), ff_mul(C.msym, b)));
+    }
+  };
+  float acc = 0.f;
+  int sm = 0, sl = 1, sp = 2;  // ring slots of planes i - 1, i, i + 1
+  fetch(i0 - 1);
+  commit(sm);
+  fetch(i0);
+  commit(sl);
+  fetch(i0 + 1);
+  for (int i = i0; i < i1; ++i) {
+    commit(sp);
+    __syncthreads();
+    if (i + 2 <= i1) fetch(i + 2);
+    const size_t g = (size_t)i * nn + (size_t)jg * n + kg;
+    const float2 r2 = *reinterpret_cast<const float2*>(rho + g);
+    const float4 U = lds4(&s_u[sl][cc]);
+    const float4 Wc = lds4(&s_w[sl][cc]);
+    const float2 Wkm = s_w[sl][cc - 1], Wkp = s_w[sl][cc + 2];
+    const float4 Wjm = lds4(&s_w[sl][cc - RS]), Wjp = lds4(&s_w[sl][cc + RS]);
+    const float4 Wim = lds4(&s_w[sm][cc]), Wip = lds4(&s_w[sp][cc]);
+    const ff u0{U.x, U.y}, u1{U.z, U.w}, w0{Wc.x, Wc.y}, w1{Wc.z, Wc.w};
+    const float t0 = cell(u0, w0, ff{Wim.x, Wim.y}, ff{Wip.x, Wip.y}, ff{Wjm.x, Wjm.y}, ff{Wjp.x, Wjp.y},
+                          ff{Wkm.x, Wkm.y}, w1, r2.x);
+    const float t1 = cell(u1, w1, ff{Wim.z, Wim.w}, ff{Wip.z, Wip.w}, ff{Wjm.z, Wjm.w}, ff{Wjp.z, Wjp.w}, w0,
+                          ff{Wkp.x, Wkp.y}, r2.y);
+    long long o0, o1;  // the two cells in the level's layout
+    if constexpr (SPLIT) {
+      const long long H = (long long)nn * (n >> 1);
+      const long long idx = ((long long)i * n + jg) * (n >> 1) + (kg >> 1);
+      const int c0 = (i + jg) & 1;  // colour of the even cell kg
+      o0 = c0 ? H + idx : idx;
+      o1 = c0 ? idx : H + idx;
+    } else {
+      o0 = (long long)g;
+      o1 = o0 + 1;
+    }
+    ub[o0] = ff_to_float(u0);
+    ub[o1] = ff_to_float(u1);
+    tau[o0] = t0;
+    tau[o1] = t1;
+    if (zero_e) {
+      zero_e[o0] = 0.f;
+      zero_e[o1] = 0.f;
+    }
+    if (zero_q) {
+      zero_q[o0] = 0.f;
+      zero_q[o1] = 0.f;
+    }
+    acc += t0 * t0;
+    acc += t1 * t1;
+    __syncthreads();
+    const int s0 = sm;
+    sm = sl;
+    sl = sp;
+    sp = s0;
+  }
+  const double a = block_sum((double)acc);
+  if (t == 0) partials[blockIdx.x + blockIdx.y * gridDim.x] = a;
+}
+
 // skip (may be nullptr): set when k_background_residual_ff has already formed
 // this residual (the solve started from the background field).
 template <int K, int TJ, int TK, bool SPLIT = false>
@@ -828,6 +979,84 @@ __global__ void __launch_bounds__(256) k_background_residual_ff(const FFC* __res
       if (zero_q) zero_q[o] = 0.f;
       acc += tv * tv;
     }
+  }
+  const double a = block_sum((double)acc);
+  if (threadIdx.x == 0) partials[b] = a;
+}
+
+// k_background_residual_ff with four consecutive cells a thread (n % 4 == 0;
+// rho 16-byte and u 16-byte aligned): one 16-byte density load and two 16-byte
+// field stores a thread, and on a split level two 8-byte stores per colour
+// array (cells 4m, 4m + 2 and 4m + 1, 4m + 3 of a row sit at 2m, 2m + 1 of the
+// two colours).  Same per-cell arithmetic; grid as the general kernel's.
+template <int K, bool SPLIT>
+__global__ void __launch_bounds__(256) k_background_residual_ff4(const FFC* __restrict__ C, int n,
+                                                                 double* __restrict__ u, double ubar,
+                                                                 const float* __restrict__ rho,
+                                                                 float* __restrict__ ub, float* __restrict__ tau,
+                                                                 double* __restrict__ partials,
+                                                                 float* __restrict__ zero_e = nullptr,
+                                                                 float* __restrict__ zero_q = nullptr) {
+  static_assert(K != KCQ, "CQ keeps the FP64 residual");
+  if (!isnan(u[0])) return;
+  const FFC c = *C;
+  const ff uc = ff_from_double(ubar);
+  const float ubf = ff_to_float(uc);
+  const int nb = gridDim.x * gridDim.y;
+  const int b = blockIdx.x + blockIdx.y * gridDim.x;
+  const int rows = n * n, q = n >> 2, h = n >> 1;
+  const long long quads = (long long)rows * q, H = (long long)rows * h;
+  const ff Kdu = ff_div(c.K, uc);         // f(R): K / ubar, the same in every cell
+  const ff ub3 = ff_mul(ff_sqr(uc), uc);  // symmetron: ubar^3
+  auto resid = [&](float r) -> float {
+    if constexpr (is_fr(K)) {
+      ffacc v = acc_of(c.c0);
+      const ff p1 = two_prod(c.c1.hi, r);
+      acc_add(v, p1.hi, __fmaf_rn(c.c1.lo, r, p1.lo));
+      acc_add(v, -Kdu.hi, -Kdu.lo);
+      return -acc_float(v);
+    } else {
+      const ff a = ff_sub(ff_mul(ff_mul_f(c.c1, r), c.rat3), ff{1.f, 0.f});
+      return ff_to_float(ff_mul(c.msym, ff_add(ff_mul(a, uc), ub3)));
+    }
+  };
+  float acc = 0.f;
+  for (long long Q = (long long)b * blockDim.x + threadIdx.x; Q < quads; Q += (long long)nb * blockDim.x) {
+    const int row = (int)(Q / q), m = (int)(Q - (long long)row * q);
+    const long long t = (long long)row * n + 4 * m;
+    const float4 r4 = *reinterpret_cast<const float4*>(rho + t);
+    if (t != 0) {
+      *reinterpret_cast<double2*>(u + t) = make_double2(ubar, ubar);
+    } else {
+      u[1] = ubar;  // cell 0 is k_background_first's
+    }
+    *reinterpret_cast<double2*>(u + t + 2) = make_double2(ubar, ubar);
+    const float t0 = resid(r4.x), t1 = resid(r4.y), t2 = resid(r4.z), t3 = resid(r4.w);
+    if constexpr (SPLIT) {
+      const int i = row / n, j = row - i * n;
+      const long long idx = (long long)row * h + 2 * m;
+      const int c0 = (i + j) & 1;  // colour of cell 4m
+      const long long a = c0 ? H + idx : idx, o = c0 ? idx : H + idx;
+      *reinterpret_cast<float2*>(ub + idx) = make_float2(ubf, ubf);
+      *reinterpret_cast<float2*>(ub + H + idx) = make_float2(ubf, ubf);
+      *reinterpret_cast<float2*>(tau + a) = make_float2(t0, t2);
+      *reinterpret_cast<float2*>(tau + o) = make_float2(t1, t3);
+      if (zero_e) {
+        *reinterpret_cast<float2*>(zero_e + idx) = make_float2(0.f, 0.f);
+        *reinterpret_cast<float2*>(zero_e + H + idx) = make_float2(0.f, 0.f);
+      }
+      if (zero_q) {
+        *reinterpret_cast<float2*>(zero_q + idx) = make_float2(0.f, 0.f);
+        *reinterpret_cast<float2*>(zero_q + H + idx) = make_float2(0.f, 0.f);
+      }
+    } else {
+      *reinterpret_cast<float4*>(ub + t) = make_float4(ubf, ubf, ubf, ubf);
+      *reinterpret_cast<float4*>(tau + t) = make_float4(t0, t1, t2, t3);
+    }
+    acc += t0 * t0;
+    acc += t1 * t1;
+    acc += t2 * t2;
+    acc += t3 * t3;
   }
   const double a = block_sum((double)acc);
   if (threadIdx.x == 0) partials[b] = a;

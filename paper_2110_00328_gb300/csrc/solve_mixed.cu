@@ -813,16 +813,30 @@ static int launch_outer_residual_ff(const MixedCtx& C, double* field, int* block
   Level& F = ws->lev[0];
   const FFC* ffc = ffc_of(ws);
   if (bg_residual_tiled(F.n)) {
-    const long long tiles = (long long)(F.n / kRTK) * (F.n / kRTJ);
-    const int chunk = C.split ? march_chunk(F.n, tiles, (const void*)k_outer_residual_ff<K, kRTJ, kRTK, true>, kRTJ * kRTK)
-                              : march_chunk(F.n, tiles, (const void*)k_outer_residual_ff<K, kRTJ, kRTK>, kRTJ * kRTK);
-    dim3 grid((F.n / kRTK) * (F.n / kRTJ), (F.n + chunk - 1) / chunk);
+    // two cells a thread on 8 x 64 tiles where the side and the density's
+    // alignment allow (8-byte pair loads), else one on 8 x 32
+    const bool pair = F.n % 64 == 0 && (uintptr_t)C.rho % 8 == 0;
+    const long long tiles = (long long)(F.n / (pair ? 64 : kRTK)) * (F.n / kRTJ);
+    const void* kern = pair ? (C.split ? (const void*)k_outer_residual_ff2<K, kRTJ, true>
+                                       : (const void*)k_outer_residual_ff2<K, kRTJ, false>)
+                            : (C.split ? (const void*)k_outer_residual_ff<K, kRTJ, kRTK, true>
+                                       : (const void*)k_outer_residual_ff<K, kRTJ, kRTK>);
+    const int chunk = march_chunk(F.n, tiles, kern, kRTJ * (pair ? 32 : kRTK));
+    dim3 grid((unsigned)tiles, (F.n + chunk - 1) / chunk);
     *blocks = grid.x * grid.y;
     if (*blocks > kMaxReduceBlocks) return MGGLAM_ERR_SHAPE;
     const int* skip = nullptr;
     if (bg_first) {
       int* flag = reinterpret_cast<int*>(ws->scalars + SC_FLAG);
-      if (C.split)
+      // four cells a thread when the caller's density and field allow 16-byte accesses
+      const bool vec = ((uintptr_t)C.rho % 16 == 0) && ((uintptr_t)field % 16 == 0);
+      if (vec && C.split)
+        k_background_residual_ff4<K, true><<<grid, 256, 0, st>>>(ffc, F.n, field, C.m.ubar, C.rho, F.ub, F.S32,
+                                                                  ws->partials, F.e, C.qs);
+      else if (vec)
+        k_background_residual_ff4<K, false><<<grid, 256, 0, st>>>(ffc, F.n, field, C.m.ubar, C.rho, F.ub, F.S32,
+                                                                   ws->partials);
+      else if (C.split)
         k_background_residual_ff<K, true><<<grid, 256, 0, st>>>(ffc, F.n, field, C.m.ubar, C.rho, F.ub, F.S32,
                                                                  ws->partials, F.e, C.qs);
       else
@@ -832,7 +846,13 @@ static int launch_outer_residual_ff(const MixedCtx& C, double* field, int* block
       note_launch(2);
       skip = flag;
     }
-    if (C.split)
+    if (pair && C.split)
+      k_outer_residual_ff2<K, kRTJ, true><<<grid, kRTJ * 32, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub, F.S32,
+                                                                      ws->partials, skip, F.e, C.qs);
+    else if (pair)
+      k_outer_residual_ff2<K, kRTJ, false><<<grid, kRTJ * 32, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub, F.S32,
+                                                                       ws->partials, skip, nullptr, nullptr);
+    else if (C.split)
       k_outer_residual_ff<K, kRTJ, kRTK, true><<<grid, kRTJ * kRTK, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub,
                                                                              F.S32, ws->partials, skip, F.e, C.qs);
     else
