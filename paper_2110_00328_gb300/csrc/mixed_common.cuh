@@ -767,7 +767,7 @@ __device__ __forceinline__ double outer_residual_tile_ff(const FFC& C, int n, in
 // neighbour sum and the source terms of each cell are formed in the same order
 // as in outer_residual_tile_ff, so each cell's residual is the same float.
 template <int K, int TJ, bool SPLIT>
-__global__ void __launch_bounds__(TJ * 32) k_outer_residual_ff2(const FFC* __restrict__ Cp, int n, int chunk,
+__global__ void __launch_bounds__(TJ * 32, 5) k_outer_residual_ff2(const FFC* __restrict__ Cp, int n, int chunk,
                                                                const double* __restrict__ u,
                                                                const float* __restrict__ rho, float* __restrict__ ub,
                                                                float* __restrict__ tau, double* __restrict__ partials,
@@ -782,8 +782,8 @@ __global__ void __launch_bounds__(TJ * 32) k_outer_residual_ff2(const FFC* __res
   constexpr int PE = (TJ + 2) * RW;  // halo elements a plane
   constexpr int PS = (TJ + 2) * RS;
   constexpr int NE = (PE + NT - 1) / NT;
-  __shared__ __align__(16) float2 s_w[3][PS];
-  __shared__ __align__(16) float2 s_u[3][PS];
+  __shared__ __align__(16) float2 s_w[4][PS];
+  __shared__ __align__(16) float2 s_u[4][PS];
   const int tiles_k = n / TK;
   const int k0 = (blockIdx.x % tiles_k) * TK;
   const int j0 = (blockIdx.x / tiles_k) * TJ;
@@ -850,18 +850,32 @@ __global__ void __launch_bounds__(TJ * 32) k_outer_residual_ff2(const FFC* __res
     }
   };
   float acc = 0.f;
-  int sm = 0, sl = 1, sp = 2;  // ring slots of planes i - 1, i, i + 1
+  // four ring slots: plane p in slot p & 3, so the slot written for plane i + 1
+  // was last read two planes earlier and one barrier a plane suffices
+  const long long nh = (long long)n * (n >> 1);
+  const long long H = (long long)nn * (n >> 1);
+  long long o0, o1;  // the two cells of plane i0 in the level's layout
+  if constexpr (SPLIT) {
+    const long long idx = ((long long)i0 * n + jg) * (n >> 1) + (kg >> 1);
+    const bool c0 = ((i0 + jg) & 1) != 0;  // colour of the even cell kg
+    o0 = c0 ? H + idx : idx;
+    o1 = c0 ? idx : H + idx;
+  } else {
+    o0 = (long long)i0 * (long long)nn + (long long)jg * n + kg;
+    o1 = o0 + 1;
+  }
+  const float* rp = rho + (size_t)i0 * nn + (size_t)jg * n + kg;
   fetch(i0 - 1);
-  commit(sm);
+  commit((i0 - 1) & 3);
   fetch(i0);
-  commit(sl);
+  commit(i0 & 3);
   fetch(i0 + 1);
   for (int i = i0; i < i1; ++i) {
-    commit(sp);
+    commit((i + 1) & 3);
     __syncthreads();
     if (i + 2 <= i1) fetch(i + 2);
-    const size_t g = (size_t)i * nn + (size_t)jg * n + kg;
-    const float2 r2 = *reinterpret_cast<const float2*>(rho + g);
+    const int sm = (i - 1) & 3, sl = i & 3, sp = (i + 1) & 3;
+    const float2 r2 = *reinterpret_cast<const float2*>(rp);
     const float4 U = lds4(&s_u[sl][cc]);
     const float4 Wc = lds4(&s_w[sl][cc]);
     const float2 Wkm = s_w[sl][cc - 1], Wkp = s_w[sl][cc + 2];
@@ -872,17 +886,6 @@ __global__ void __launch_bounds__(TJ * 32) k_outer_residual_ff2(const FFC* __res
                           ff{Wkm.x, Wkm.y}, w1, r2.x);
     const float t1 = cell(u1, w1, ff{Wim.z, Wim.w}, ff{Wip.z, Wip.w}, ff{Wjm.z, Wjm.w}, ff{Wjp.z, Wjp.w}, w0,
                           ff{Wkp.x, Wkp.y}, r2.y);
-    long long o0, o1;  // the two cells in the level's layout
-    if constexpr (SPLIT) {
-      const long long H = (long long)nn * (n >> 1);
-      const long long idx = ((long long)i * n + jg) * (n >> 1) + (kg >> 1);
-      const int c0 = (i + jg) & 1;  // colour of the even cell kg
-      o0 = c0 ? H + idx : idx;
-      o1 = c0 ? idx : H + idx;
-    } else {
-      o0 = (long long)g;
-      o1 = o0 + 1;
-    }
     ub[o0] = ff_to_float(u0);
     ub[o1] = ff_to_float(u1);
     tau[o0] = t0;
@@ -897,11 +900,16 @@ __global__ void __launch_bounds__(TJ * 32) k_outer_residual_ff2(const FFC* __res
     }
     acc += t0 * t0;
     acc += t1 * t1;
-    __syncthreads();
-    const int s0 = sm;
-    sm = sl;
-    sl = sp;
-    sp = s0;
+    rp += nn;
+    if constexpr (SPLIT) {
+      // the next plane: one row block on, the colours of the two cells swapped
+      const long long a = o0;
+      o0 = o1 + nh;
+      o1 = a + nh;
+    } else {
+      o0 += (long long)nn;
+      o1 += (long long)nn;
+    }
   }
   const double a = block_sum((double)acc);
   if (t == 0) partials[blockIdx.x + blockIdx.y * gridDim.x] = a;
