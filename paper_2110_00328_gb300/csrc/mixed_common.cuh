@@ -934,9 +934,10 @@ __global__ void __launch_bounds__(TJ* TK) k_outer_residual_ff(const FFC* __restr
 }
 
 // The start from the background field (its first element NaN on entry): the
-// field is set to ubar everywhere but at cell 0 (k_background_first writes that
-// one, and the flag, after every CTA has read it) and the residual at the
-// uniform field is formed in the same pass.  There the six-neighbour sum of w
+// residual at the uniform field ubar is formed without reading or writing the
+// field, which keeps its NaN mark; the first correction writes ubar + e over it
+// (k_apply_correction<true>), or the solve fills it with ubar if it ends before
+// one.  k_background_first raises the flag, after every CTA has read cell 0.  There the six-neighbour sum of w
 // equals 6w exactly, so r = N(ubar) is the source term alone, which the
 // float-float operations of outer_residual_tile_ff give to the same accuracy:
 //   f(R): c1 rho + c0 - K/ubar;  symmetron: -msym ((rho/mean rat3 - 1) ubar + ubar^3).
@@ -945,7 +946,7 @@ __global__ void __launch_bounds__(TJ* TK) k_outer_residual_ff(const FFC* __restr
 // When the field is not NaN-marked it returns at once (the general kernel runs).
 template <int K, bool SPLIT>
 __global__ void __launch_bounds__(256) k_background_residual_ff(const FFC* __restrict__ C, int n,
-                                                                double* __restrict__ u, double ubar,
+                                                                const double* __restrict__ u, double ubar,
                                                                 const float* __restrict__ rho,
                                                                 float* __restrict__ ub, float* __restrict__ tau,
                                                                 double* __restrict__ partials,
@@ -967,7 +968,6 @@ __global__ void __launch_bounds__(256) k_background_residual_ff(const FFC* __res
     const int i = row / n, j = row - i * n;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
       const long long t = (long long)row * n + k;
-      if (t != 0) u[t] = ubar;
       const float r = rho[t];
       float tv;
       if constexpr (is_fr(K)) {
@@ -992,14 +992,14 @@ __global__ void __launch_bounds__(256) k_background_residual_ff(const FFC* __res
   if (threadIdx.x == 0) partials[b] = a;
 }
 
-// k_background_residual_ff with four consecutive cells a thread (n % 4 == 0;
-// rho 16-byte and u 16-byte aligned): one 16-byte density load and two 16-byte
-// field stores a thread, and on a split level two 8-byte stores per colour
+// k_background_residual_ff with four consecutive cells a thread (n % 4 == 0,
+// rho 16-byte aligned): one 16-byte density load a thread, and on a split
+// level two 8-byte stores per colour
 // array (cells 4m, 4m + 2 and 4m + 1, 4m + 3 of a row sit at 2m, 2m + 1 of the
 // two colours).  Same per-cell arithmetic; grid as the general kernel's.
 template <int K, bool SPLIT>
 __global__ void __launch_bounds__(256) k_background_residual_ff4(const FFC* __restrict__ C, int n,
-                                                                 double* __restrict__ u, double ubar,
+                                                                 const double* __restrict__ u, double ubar,
                                                                  const float* __restrict__ rho,
                                                                  float* __restrict__ ub, float* __restrict__ tau,
                                                                  double* __restrict__ partials,
@@ -1033,12 +1033,6 @@ __global__ void __launch_bounds__(256) k_background_residual_ff4(const FFC* __re
     const int row = (int)(Q / q), m = (int)(Q - (long long)row * q);
     const long long t = (long long)row * n + 4 * m;
     const float4 r4 = *reinterpret_cast<const float4*>(rho + t);
-    if (t != 0) {
-      *reinterpret_cast<double2*>(u + t) = make_double2(ubar, ubar);
-    } else {
-      u[1] = ubar;  // cell 0 is k_background_first's
-    }
-    *reinterpret_cast<double2*>(u + t + 2) = make_double2(ubar, ubar);
     const float t0 = resid(r4.x), t1 = resid(r4.y), t2 = resid(r4.z), t3 = resid(r4.w);
     if constexpr (SPLIT) {
       const int i = row / n, j = row - i * n;
@@ -1070,12 +1064,11 @@ __global__ void __launch_bounds__(256) k_background_residual_ff4(const FFC* __re
   if (threadIdx.x == 0) partials[b] = a;
 }
 
-// Cell 0 of the background start, and the flag that tells the general residual
-// kernel its work is done (flag = 0 when the caller gave an initial field).
-static __global__ void k_background_first(double* __restrict__ u, double ubar, int* __restrict__ flag) {
-  const bool bg = isnan(u[0]);
-  if (bg) u[0] = ubar;
-  *flag = bg ? 1 : 0;
+// The flag that tells the general residual kernel its work is done, and the
+// host that the field still holds the background mark (flag = 0 when the
+// caller gave an initial field).
+static __global__ void k_background_first(const double* __restrict__ u, int* __restrict__ flag) {
+  *flag = isnan(u[0]) ? 1 : 0;
 }
 
 template <int K, int TJ, int TK>

@@ -236,30 +236,59 @@ __global__ void __launch_bounds__(128) k_prolong_correct32(int nc, const float* 
 // FP64 outer-loop kernels (fine level)
 // ---------------------------------------------------------------------------
 
-// u64 += e with e in the split layout.
-// Rows (i, j) over the CTAs; thread m adds the pair k = 2m, 2m+1, whose
-// corrections sit at the same index row h + m of the two colour halves.
-__global__ void k_apply_correction_split(double* __restrict__ u, const float* __restrict__ e, int n) {
+// u64 += e with e in the split layout; BG: u64 = ubar + e (the first correction
+// of a solve from the background, whose field still holds only its NaN mark).
+// Thread w of row (i, j) takes cells 4w .. 4w+3 (h even), whose corrections sit
+// at row h + 2w, 2w+1 of the two colour halves: two 8-byte loads of e and two
+// 16-byte accesses of u (16-byte aligned) a thread, grid-stride over all rows.
+template <bool BG>
+__global__ void k_apply_correction_split(double* __restrict__ u, const float* __restrict__ e, int n, double ubar) {
+  const int h = n >> 1, q = h >> 1;
+  const long long H = (long long)n * n * h, items = (long long)n * n * q;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < items;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int row = (int)(t / q), w = (int)(t - (long long)row * q);
+    const int i = row / n, j = row - i * n;
+    const long long c0 = ((i + j) & 1) ? H : 0;  // colour half of the even-k cells
+    double2* ur = reinterpret_cast<double2*>(u + (long long)row * n) + 2 * w;
+    const float2 a = reinterpret_cast<const float2*>(e + c0 + (long long)row * h)[w];
+    const float2 b = reinterpret_cast<const float2*>(e + (H - c0) + (long long)row * h)[w];
+    double2 lo = BG ? make_double2(ubar, ubar) : ur[0], hi = BG ? make_double2(ubar, ubar) : ur[1];
+    lo.x += (double)a.x;
+    lo.y += (double)b.x;
+    hi.x += (double)a.y;
+    hi.y += (double)b.y;
+    ur[0] = lo;
+    ur[1] = hi;
+  }
+}
+
+// k_apply_correction_split for a field that is not 16-byte aligned: thread m
+// takes the pair k = 2m, 2m+1.
+template <bool BG>
+__global__ void k_apply_correction_split_scalar(double* __restrict__ u, const float* __restrict__ e, int n,
+                                                double ubar) {
   const int h = n >> 1, rows = n * n;
   const long long H = (long long)n * n * h;
   for (int row = blockIdx.x; row < rows; row += gridDim.x) {
     const int i = row / n, j = row - i * n;
-    const long long c0 = ((i + j) & 1) ? H : 0;  // colour half of the even-k cells
+    const long long c0 = ((i + j) & 1) ? H : 0;
     double* ur = u + (long long)row * n;
     const float* ev = e + c0 + (long long)row * h;
     const float* od = e + (H - c0) + (long long)row * h;
     for (int m = threadIdx.x; m < h; m += blockDim.x) {
-      ur[2 * m] += (double)ev[m];
-      ur[2 * m + 1] += (double)od[m];
+      ur[2 * m] = (BG ? ubar : ur[2 * m]) + (double)ev[m];
+      ur[2 * m + 1] = (BG ? ubar : ur[2 * m + 1]) + (double)od[m];
     }
   }
 }
 
-// u64 += e (the correction of one inner solve).
-__global__ void k_apply_correction(double* __restrict__ u, const float* __restrict__ e, long long n3) {
+// u64 += e (the correction of one inner solve); BG: u64 = ubar + e.
+template <bool BG>
+__global__ void k_apply_correction(double* __restrict__ u, const float* __restrict__ e, long long n3, double ubar) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n3;
        t += (long long)gridDim.x * blockDim.x)
-    u[t] += (double)e[t];
+    u[t] = (BG ? ubar : u[t]) + (double)e[t];
 }
 
 
@@ -296,6 +325,9 @@ struct MixedCtx {
   float* qs;          // split f(R) n = 1, 2: the finest level's stored neighbour quantity, else nullptr
   unsigned long long* guard;  // positivity-guard replacements of this solve (workspace scalar)
   const struct L2Window* l2 = nullptr;  // persisting L2 window over qs for the colour passes, or nullptr
+  // set: the finest level's e and q were not zeroed for the inner solve that
+  // starts next, and its first stored-q sweep takes them as zero (smooth32 clears it)
+  bool* fresh = nullptr;
 };
 
 static FFC* ffc_of(Workspace* ws) { return reinterpret_cast<FFC*>(ws->scalars + SC_FFC); }
@@ -430,6 +462,7 @@ static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
   const bool fused = use_fused(C, L.n);
   int passes = 0;  // stored-q colour passes launched so far in this call
   for (int s = 0; s < sweeps; ++s) {
+    const bool first_fresh = l == 0 && C.qs && C.fresh && *C.fresh;
     if (fused && L.e_alt) {
       switch (tk) {
         case 64: MG_DISPATCH32(C.m.kind, (launch_sweep_t<KK, 64>(C, l, rho, st))); break;
@@ -465,12 +498,15 @@ static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
             }
             const int pdl = passes++ > 0 ? 1 : 2;
             const float *ubc = L.ub, *Sc = L.S32, *no_rho = nullptr;
+            // the first sweep from e = 0: the first colour reads neither e nor the
+            // other colour's q, the second not its own e
+            const int fresh = first_fresh ? (parity == 0 ? 3 : 1) : 0;
             if (C.m.kind == KFR1)
               MG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_smooth32s<KFR1, true>, C.lf[l], L.n, L.e, ubc, no_rho, Sc, parity,
-                                             i0, np, C.qs, pdl));
+                                             i0, np, C.qs, pdl, fresh));
             else
               MG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_smooth32s<KFR2, true>, C.lf[l], L.n, L.e, ubc, no_rho, Sc, parity,
-                                             i0, np, C.qs, pdl));
+                                             i0, np, C.qs, pdl, fresh));
             note_launch(1);
             return MGGLAM_OK;
           }
@@ -503,6 +539,7 @@ static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
       for (int parity = 0; parity < 2; ++parity)
         MG_DISPATCH32(C.m.kind, (k_smooth32<KK><<<g, 64, 0, st>>>(C.lf[l], L.n, L.e, L.ub, rho, L.S32, parity)));
     }
+    if (first_fresh) *C.fresh = false;
   }
   return MGGLAM_OK;
 }
@@ -808,10 +845,13 @@ constexpr int kRTJ = 8, kRTK = 32;
 static bool bg_residual_tiled(int n) { return n % kRTK == 0 && n % kRTJ == 0; }
 
 template <int K>
-static int launch_outer_residual_ff(const MixedCtx& C, double* field, int* blocks, cudaStream_t st, bool bg_first) {
+static int launch_outer_residual_ff(const MixedCtx& C, double* field, int* blocks, cudaStream_t st, bool bg_first,
+                                    bool zero) {
   Workspace* ws = C.ws;
   Level& F = ws->lev[0];
   const FFC* ffc = ffc_of(ws);
+  float* ze = zero ? F.e : nullptr;   // the split kernels' zeroing of e and q
+  float* zq = zero ? C.qs : nullptr;
   if (bg_residual_tiled(F.n)) {
     // two cells a thread on 8 x 64 tiles where the side and the density's
     // alignment allow (8-byte pair loads), else one on 8 x 32
@@ -832,29 +872,29 @@ static int launch_outer_residual_ff(const MixedCtx& C, double* field, int* block
       const bool vec = ((uintptr_t)C.rho % 16 == 0) && ((uintptr_t)field % 16 == 0);
       if (vec && C.split)
         k_background_residual_ff4<K, true><<<grid, 256, 0, st>>>(ffc, F.n, field, C.m.ubar, C.rho, F.ub, F.S32,
-                                                                  ws->partials, F.e, C.qs);
+                                                                  ws->partials, ze, zq);
       else if (vec)
         k_background_residual_ff4<K, false><<<grid, 256, 0, st>>>(ffc, F.n, field, C.m.ubar, C.rho, F.ub, F.S32,
                                                                    ws->partials);
       else if (C.split)
         k_background_residual_ff<K, true><<<grid, 256, 0, st>>>(ffc, F.n, field, C.m.ubar, C.rho, F.ub, F.S32,
-                                                                 ws->partials, F.e, C.qs);
+                                                                 ws->partials, ze, zq);
       else
         k_background_residual_ff<K, false><<<grid, 256, 0, st>>>(ffc, F.n, field, C.m.ubar, C.rho, F.ub, F.S32,
                                                                   ws->partials);
-      k_background_first<<<1, 1, 0, st>>>(field, C.m.ubar, flag);
+      k_background_first<<<1, 1, 0, st>>>(field, flag);
       note_launch(2);
       skip = flag;
     }
     if (pair && C.split)
       k_outer_residual_ff2<K, kRTJ, true><<<grid, kRTJ * 32, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub, F.S32,
-                                                                      ws->partials, skip, F.e, C.qs);
+                                                                      ws->partials, skip, ze, zq);
     else if (pair)
       k_outer_residual_ff2<K, kRTJ, false><<<grid, kRTJ * 32, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub, F.S32,
                                                                        ws->partials, skip, nullptr, nullptr);
     else if (C.split)
       k_outer_residual_ff<K, kRTJ, kRTK, true><<<grid, kRTJ * kRTK, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub,
-                                                                             F.S32, ws->partials, skip, F.e, C.qs);
+                                                                             F.S32, ws->partials, skip, ze, zq);
     else
       k_outer_residual_ff<K, kRTJ, kRTK><<<grid, kRTJ * kRTK, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub, F.S32,
                                                                        ws->partials, skip);
@@ -874,11 +914,12 @@ static int launch_outer_residual_ff(const MixedCtx& C, double* field, int* block
 }
 
 template <int K>
-static int launch_outer_residual_t(const MixedCtx& C, double* field, int* blocks, cudaStream_t st, bool bg_first) {
+static int launch_outer_residual_t(const MixedCtx& C, double* field, int* blocks, cudaStream_t st, bool bg_first,
+                                   bool zero) {
   Workspace* ws = C.ws;
   Level& F = ws->lev[0];
   if constexpr (K != KCQ) {
-    if (C.ff_resid) return launch_outer_residual_ff<K>(C, field, blocks, st, bg_first);
+    if (C.ff_resid) return launch_outer_residual_ff<K>(C, field, blocks, st, bg_first, zero);
   }
   if (F.n % kRTK == 0 && F.n % kRTJ == 0) {
     const int chunk = march_chunk(F.n, (long long)(F.n / kRTK) * (F.n / kRTJ),
@@ -913,13 +954,15 @@ static bool residual_zeroes_e(const MixedCtx& C) { return C.split && C.ff_resid 
 // fused into it (fused_background_start); the field's background fill happens there.
 static bool fused_background_start(const MixedCtx& C) { return C.ff_resid && bg_residual_tiled(C.ws->lev[0].n); }
 
-static int outer_residual(const MixedCtx& C, double* field, cudaStream_t st, bool bg_first = false) {
+// zero: the split tiled residual also zeroes e and q for the next inner solve
+// (not needed when that solve's first sweep starts from e = 0 by itself).
+static int outer_residual(const MixedCtx& C, double* field, cudaStream_t st, bool bg_first, bool zero) {
   Workspace* ws = C.ws;
   Level& F = ws->lev[0];
   // bytes per cell: u (8) and the source (float-float: the FP32 density, 4; FP64: src64, 8) in, ub and tau (4 + 4) out
   prof_begin(PC_OUTER_RESID, st, (C.ff_resid ? 20.0 : 24.0) * F.n3);
   int g = 0, rc = MGGLAM_OK;
-  MG_DISPATCH32(C.m.kind, (rc = launch_outer_residual_t<KK>(C, field, &g, st, bg_first)));
+  MG_DISPATCH32(C.m.kind, (rc = launch_outer_residual_t<KK>(C, field, &g, st, bg_first, zero)));
   if (rc) return rc;
   k_finalize_sum32<<<1, 1024, 0, st>>>(ws->partials, g, ws->scalars + SC_SUMSQ);
   note_launch(1);
@@ -991,10 +1034,20 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
                                                                       ws->partials)));
   k_finalize_sum32<<<1, 1024, 0, st>>>(ws->partials, g, ws->scalars + SC_SRC);
   note_launch(1);
-  if ((rc = outer_residual(C, field, st, fused_bg))) return rc;
+  // The first stored-q sweep of an inner solve can take e = q = 0 by itself
+  // (split f(R) n = 1, 2 with pre-smoothing), so the residual passes need not
+  // zero them -- except before an FMG start, which restricts e before any sweep.
+  const bool fresh_ok = residual_zeroes_e(C) && C.qs && prm->nu1 >= 1;
+  const bool fmg_first = prm->fmg && C.m.kind != KCQ;
+  bool fresh = false;
+  C.fresh = &fresh;
+  if ((rc = outer_residual(C, field, st, fused_bg, !fresh_ok || fmg_first))) return rc;
   MG_CUDA_TRY(cudaMemcpyAsync(ws->h_scalars, ws->scalars, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
   MG_CUDA_TRY(cudaStreamSynchronize(st));
   MG_CUDA_TRY(cudaGetLastError());
+  // background start fused into the first residual: the field keeps its NaN mark
+  // until the first correction writes ubar + e (or the fill below, without one)
+  bool bg_pending = fused_bg && *reinterpret_cast<const int*>(ws->h_scalars + SC_FLAG) != 0;
   const double src = sqrt(ws->h_scalars[SC_SRC] / (double)n3);
   const double snorm = source_norm(C.m, src);
   double eps = sqrt(ws->h_scalars[SC_SUMSQ] / (double)n3) / snorm;
@@ -1027,15 +1080,28 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
       MG_CUDA_TRY(cudaMemsetAsync(F.e, 0, F.n3 * sizeof(float), st));
       if (C.qs) MG_CUDA_TRY(cudaMemsetAsync(C.qs, 0, F.n3 * sizeof(float), st));  // Delta w(u, 0) = 0
     }
+    fresh = fresh_ok && !fmg;
     for (int c = 0; c < inner && cyc < prm->max_cycles; ++c, ++cyc, ++done)
       if ((rc = (fmg && c == 0) ? fmg_start32(C, st) : vcycle32(C, 0, st, C.prm->cycle))) return rc;
     prof_begin(PC_APPLY_CORR, st, 20.0 * n3);
-    if (C.split) k_apply_correction_split<<<kStreamBlocks, 128, 0, st>>>(field, F.e, F.n);
-    else k_apply_correction<<<stream_grid(n3), kThreads, 0, st>>>(field, F.e, n3);
+    const bool vec = C.split && (uintptr_t)field % 16 == 0;  // the split layout has n % 32 == 0
+    if (vec && bg_pending)
+      k_apply_correction_split<true><<<kStreamBlocks, kThreads, 0, st>>>(field, F.e, F.n, C.m.ubar);
+    else if (vec)
+      k_apply_correction_split<false><<<kStreamBlocks, kThreads, 0, st>>>(field, F.e, F.n, C.m.ubar);
+    else if (C.split && bg_pending)
+      k_apply_correction_split_scalar<true><<<kStreamBlocks, 128, 0, st>>>(field, F.e, F.n, C.m.ubar);
+    else if (C.split)
+      k_apply_correction_split_scalar<false><<<kStreamBlocks, 128, 0, st>>>(field, F.e, F.n, C.m.ubar);
+    else if (bg_pending)
+      k_apply_correction<true><<<stream_grid(n3), kThreads, 0, st>>>(field, F.e, n3, C.m.ubar);
+    else
+      k_apply_correction<false><<<stream_grid(n3), kThreads, 0, st>>>(field, F.e, n3, C.m.ubar);
     note_launch(1);
+    bg_pending = false;
     prof_end(st);
     ++outer;
-    if ((rc = outer_residual(C, field, st))) return rc;
+    if ((rc = outer_residual(C, field, st, false, !fresh_ok))) return rc;
     MG_CUDA_TRY(cudaMemcpyAsync(ws->h_scalars + SC_SUMSQ, ws->scalars + SC_SUMSQ, sizeof(double),
                                 cudaMemcpyDeviceToHost, st));
     MG_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1051,6 +1117,8 @@ int solve_mixed(const mgglam_params* prm, double a, const float* rho, int N, dou
     }
   }
   if (status == MGGLAM_OK && !isfinite(eps)) status = MGGLAM_ERR_NONFINITE;
+  // no correction was applied to a background start: the solution is ubar
+  if (bg_pending && (rc = launch_init_background(C.m, field, F.n3, st))) return rc;
   MG_CUDA_TRY(cudaMemcpyAsync(ws->h_scalars + SC_GUARD, C.guard, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                               st));
   MG_CUDA_TRY(cudaStreamSynchronize(st));

@@ -481,7 +481,8 @@ template <int K, bool QS = false>
 __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __restrict__ e,
                                              const float* __restrict__ ub, const float* __restrict__ rho,
                                              const float* __restrict__ S, int i, int j, int seg, bool act,
-                                             int colour, int lane, float* __restrict__ q = nullptr, int pdl = 0) {
+                                             int colour, int lane, float* __restrict__ q = nullptr, int pdl = 0,
+                                             int fresh = 0) {
   constexpr bool FR = is_fr(K);
   static_assert(!QS || K == KFR1 || K == KFR2, "the stored neighbour quantity differs from e for f(R) n = 1, 2 only");
   constexpr bool RHO = (K == KSYM) || (K == KCQ);
@@ -507,17 +508,30 @@ __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __re
     // when its own early loads run, every kernel before this one has finished.
     // The colour's own e (the Newton start of update_e_warm) is written only by
     // passes of this colour and by the prolongation, both finished by then.
+    // fresh (the first sweep of an inner solve, whose correction starts at
+    // zero): bit 0, this colour's e is zero and is not read; bit 1, the other
+    // colour's q = Delta w(u, 0) is zero too and is not read.  The result is the
+    // one the zero arrays would give.
     const float* q1 = q + (long long)(colour ^ 1) * H + r0;  // other colour's q
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (pdl == 2) asm volatile("griddepcontrol.wait;" ::: "memory");
-    const float4 U = ld4(uo), Sv = ld4(S + (long long)colour * H + r0), E = ld4(eo);
+    const float4 U = ld4(uo), Sv = ld4(S + (long long)colour * H + r0), E = (fresh & 1) ? z4 : ld4(eo);
     if (pdl == 1) asm volatile("griddepcontrol.wait;" ::: "memory");
     if (pdl) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const float4 Q = ld4(q1);
-    const float4 Qjp = ld4(q1 + djp), Qjm = ld4(q1 + djm), Qip = ld4(q1 + dip), Qim = ld4(q1 + dim);
+    float4 Q = z4, Qjp = z4, Qjm = z4, Qip = z4, Qim = z4;
+    if (!(fresh & 2)) {
+      Q = ld4(q1);
+      Qjp = ld4(q1 + djp);
+      Qjm = ld4(q1 + djm);
+      Qip = ld4(q1 + dip);
+      Qim = ld4(q1 + dim);
+    }
     float qm = __shfl_up_sync(0xffffffffu, Q.w, 1);
     float qp = __shfl_down_sync(0xffffffffu, Q.x, 1);
-    if (p == 0 && (seg == 0 || lane == 0)) qm = q1[m0 == 0 ? h - 1 : -1];
-    if (p == 1 && (seg == nq - 1 || lane == 31)) qp = q1[m0 + 4 == h ? 4 - h : 4];
+    if (!(fresh & 2)) {
+      if (p == 0 && (seg == 0 || lane == 0)) qm = q1[m0 == 0 ? h - 1 : -1];
+      if (p == 1 && (seg == nq - 1 || lane == 31)) qp = q1[m0 + 4 == h ? 4 - h : 4];
+    }
     const float k0s = p ? Q.x + Q.y : qm + Q.x;
     const float k1s = p ? Q.y + Q.z : Q.x + Q.y;
     const float k2s = p ? Q.z + Q.w : Q.y + Q.z;
@@ -592,7 +606,7 @@ template <int K, bool QS = false>
 __global__ void __launch_bounds__(128, QS ? 10 : 1) k_smooth32s(LevelF f, int n, float* __restrict__ e,
                                                    const float* __restrict__ ub, const float* __restrict__ rho,
                                                    const float* __restrict__ S, int colour, int i0, int np,
-                                                   float* __restrict__ q, int pdl) {
+                                                   float* __restrict__ q, int pdl, int fresh = 0) {
   const int lane = threadIdx.x;
   const long long warp = (long long)blockIdx.x * 4 + threadIdx.y;
   long long r;
@@ -604,7 +618,7 @@ __global__ void __launch_bounds__(128, QS ? 10 : 1) k_smooth32s(LevelF f, int n,
   int i = i0 + (int)(pow2 ? r >> sh : r / n);
   if (i >= n) i -= n;
   const int j = (int)(pow2 ? r & (n - 1) : r % n);
-  smooth_split<K, QS>(f, n, e, ub, rho, S, i, j, seg, act, colour, lane, q, pdl);
+  smooth_split<K, QS>(f, n, e, ub, rho, S, i, j, seg, act, colour, lane, q, pdl, fresh);
 }
 
 }  // namespace mg
