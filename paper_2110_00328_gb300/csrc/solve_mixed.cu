@@ -501,12 +501,13 @@ static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
             // the first sweep from e = 0: the first colour reads neither e nor the
             // other colour's q, the second not its own e
             const int fresh = first_fresh ? (parity == 0 ? 3 : 1) : 0;
-            if (C.m.kind == KFR1)
-              MG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_smooth32s<KFR1, true>, C.lf[l], L.n, L.e, ubc, no_rho, Sc, parity,
-                                             i0, np, C.qs, pdl, fresh));
-            else
-              MG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_smooth32s<KFR2, true>, C.lf[l], L.n, L.e, ubc, no_rho, Sc, parity,
-                                             i0, np, C.qs, pdl, fresh));
+            auto go = [&](auto kern) {
+              return cudaLaunchKernelEx(&cfg, kern, C.lf[l], L.n, L.e, ubc, no_rho, Sc, parity, i0, np, C.qs, pdl);
+            };
+            const bool f1 = C.m.kind == KFR1;
+            if (fresh == 3) MG_CUDA_TRY(f1 ? go(k_smooth32s<KFR1, true, 3>) : go(k_smooth32s<KFR2, true, 3>));
+            else if (fresh == 1) MG_CUDA_TRY(f1 ? go(k_smooth32s<KFR1, true, 1>) : go(k_smooth32s<KFR2, true, 1>));
+            else MG_CUDA_TRY(f1 ? go(k_smooth32s<KFR1, true>) : go(k_smooth32s<KFR2, true>));
             note_launch(1);
             return MGGLAM_OK;
           }

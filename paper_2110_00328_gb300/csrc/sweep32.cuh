@@ -477,12 +477,11 @@ struct SplitLayout {
 // (q written beside e).  q is formed by the same expression from the same
 // values, so the sweep computes what it computes without it, up to where the
 // compiler fuses a product into the neighbouring sum.
-template <int K, bool QS = false>
+template <int K, bool QS = false, int FRESH = 0>
 __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __restrict__ e,
                                              const float* __restrict__ ub, const float* __restrict__ rho,
                                              const float* __restrict__ S, int i, int j, int seg, bool act,
-                                             int colour, int lane, float* __restrict__ q = nullptr, int pdl = 0,
-                                             int fresh = 0) {
+                                             int colour, int lane, float* __restrict__ q = nullptr, int pdl = 0) {
   constexpr bool FR = is_fr(K);
   static_assert(!QS || K == KFR1 || K == KFR2, "the stored neighbour quantity differs from e for f(R) n = 1, 2 only");
   constexpr bool RHO = (K == KSYM) || (K == KCQ);
@@ -508,18 +507,18 @@ __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __re
     // when its own early loads run, every kernel before this one has finished.
     // The colour's own e (the Newton start of update_e_warm) is written only by
     // passes of this colour and by the prolongation, both finished by then.
-    // fresh (the first sweep of an inner solve, whose correction starts at
+    // FRESH (the first sweep of an inner solve, whose correction starts at
     // zero): bit 0, this colour's e is zero and is not read; bit 1, the other
     // colour's q = Delta w(u, 0) is zero too and is not read.  The result is the
     // one the zero arrays would give.
     const float* q1 = q + (long long)(colour ^ 1) * H + r0;  // other colour's q
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (pdl == 2) asm volatile("griddepcontrol.wait;" ::: "memory");
-    const float4 U = ld4(uo), Sv = ld4(S + (long long)colour * H + r0), E = (fresh & 1) ? z4 : ld4(eo);
+    const float4 U = ld4(uo), Sv = ld4(S + (long long)colour * H + r0), E = (FRESH & 1) ? z4 : ld4(eo);
     if (pdl == 1) asm volatile("griddepcontrol.wait;" ::: "memory");
     if (pdl) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     float4 Q = z4, Qjp = z4, Qjm = z4, Qip = z4, Qim = z4;
-    if (!(fresh & 2)) {
+    if constexpr (!(FRESH & 2)) {
       Q = ld4(q1);
       Qjp = ld4(q1 + djp);
       Qjm = ld4(q1 + djm);
@@ -528,7 +527,7 @@ __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __re
     }
     float qm = __shfl_up_sync(0xffffffffu, Q.w, 1);
     float qp = __shfl_down_sync(0xffffffffu, Q.x, 1);
-    if (!(fresh & 2)) {
+    if constexpr (!(FRESH & 2)) {
       if (p == 0 && (seg == 0 || lane == 0)) qm = q1[m0 == 0 ? h - 1 : -1];
       if (p == 1 && (seg == nq - 1 || lane == 31)) qp = q1[m0 + 4 == h ? 4 - h : 4];
     }
@@ -602,11 +601,11 @@ __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __re
 // per warp, a long row over several warps), four cells per lane; block (32, 4),
 // 1D grid over warps.
 // QS: f(R) n = 1, 2 with the neighbour quantity q stored beside e (smooth_split).
-template <int K, bool QS = false>
+template <int K, bool QS = false, int FRESH = 0>
 __global__ void __launch_bounds__(128, QS ? 10 : 1) k_smooth32s(LevelF f, int n, float* __restrict__ e,
                                                    const float* __restrict__ ub, const float* __restrict__ rho,
                                                    const float* __restrict__ S, int colour, int i0, int np,
-                                                   float* __restrict__ q, int pdl, int fresh = 0) {
+                                                   float* __restrict__ q, int pdl) {
   const int lane = threadIdx.x;
   const long long warp = (long long)blockIdx.x * 4 + threadIdx.y;
   long long r;
@@ -618,7 +617,7 @@ __global__ void __launch_bounds__(128, QS ? 10 : 1) k_smooth32s(LevelF f, int n,
   int i = i0 + (int)(pow2 ? r >> sh : r / n);
   if (i >= n) i -= n;
   const int j = (int)(pow2 ? r & (n - 1) : r % n);
-  smooth_split<K, QS>(f, n, e, ub, rho, S, i, j, seg, act, colour, lane, q, pdl, fresh);
+  smooth_split<K, QS, FRESH>(f, n, e, ub, rho, S, i, j, seg, act, colour, lane, q, pdl);
 }
 
 }  // namespace mg
