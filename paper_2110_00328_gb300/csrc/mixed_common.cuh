@@ -1012,8 +1012,9 @@ __global__ void __launch_bounds__(256) k_background_residual_ff4(const FFC* __re
   const float ubf = ff_to_float(uc);
   const int nb = gridDim.x * gridDim.y;
   const int b = blockIdx.x + blockIdx.y * gridDim.x;
-  const int rows = n * n, q = n >> 2, h = n >> 1;
-  const long long quads = (long long)rows * q, H = (long long)rows * h;
+  const int rows = n * n, h = n >> 1;
+  const unsigned q = (unsigned)(n >> 2), quads = (unsigned)rows * q;  // 32-bit index: <= 2^30 for n <= 2048
+  const long long H = (long long)rows * h;
   const ff Kdu = ff_div(c.K, uc);         // f(R): K / ubar, the same in every cell
   const ff ub3 = ff_mul(ff_sqr(uc), uc);  // symmetron: ubar^3
   auto resid = [&](float r) -> float {
@@ -1029,8 +1030,8 @@ __global__ void __launch_bounds__(256) k_background_residual_ff4(const FFC* __re
     }
   };
   float acc = 0.f;
-  for (long long Q = (long long)b * blockDim.x + threadIdx.x; Q < quads; Q += (long long)nb * blockDim.x) {
-    const int row = (int)(Q / q), m = (int)(Q - (long long)row * q);
+  for (unsigned Q = (unsigned)b * blockDim.x + threadIdx.x; Q < quads; Q += (unsigned)nb * blockDim.x) {
+    const int row = (int)(Q / q), m = (int)(Q - (unsigned)row * q);
     const long long t = (long long)row * n + 4 * m;
     const float4 r4 = *reinterpret_cast<const float4*>(rho + t);
     const float t0 = resid(r4.x), t1 = resid(r4.y), t2 = resid(r4.z), t3 = resid(r4.w);

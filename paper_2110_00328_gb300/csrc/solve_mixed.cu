@@ -243,11 +243,11 @@ __global__ void __launch_bounds__(128) k_prolong_correct32(int nc, const float* 
 // 16-byte accesses of u (16-byte aligned) a thread, grid-stride over all rows.
 template <bool BG>
 __global__ void k_apply_correction_split(double* __restrict__ u, const float* __restrict__ e, int n, double ubar) {
-  const int h = n >> 1, q = h >> 1;
-  const long long H = (long long)n * n * h, items = (long long)n * n * q;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < items;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int row = (int)(t / q), w = (int)(t - (long long)row * q);
+  const int h = n >> 1;
+  const unsigned q = (unsigned)(h >> 1), items = (unsigned)n * (unsigned)n * q;  // <= 2^31 for n <= 2048
+  const long long H = (long long)n * n * h;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < items; t += gridDim.x * blockDim.x) {
+    const int row = (int)(t / q), w = (int)(t - (unsigned)row * q);
     const int i = row / n, j = row - i * n;
     const long long c0 = ((i + j) & 1) ? H : 0;  // colour half of the even-k cells
     double2* ur = reinterpret_cast<double2*>(u + (long long)row * n) + 2 * w;
