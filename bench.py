@@ -86,9 +86,9 @@ def measured_peaks():
 
 
 # DRAM bytes per fine-level sweep of the smoother at 256^3: dram__bytes_read.sum +
-# dram__bytes_write.sum of both colour launches of a cycle-7 sweep (the warm
-# path), from one ncu capture; valid while the kernel's sources hash to the
-# value recorded with it.
+# dram__bytes_write.sum of both colour launches of a warm sweep (cycle 6, the
+# path every pass after an inner solve's first sweep takes), from one ncu
+# capture; valid while the kernel's sources hash to the value recorded with it.
 SMOOTHER_TRAFFIC = {"bytes_per_sweep": (134.504192 + 43.478784 + 134.505984 + 38.387456) * 1e6,
                     "source_sha256_16": "65b555489526bdd0"}
 
