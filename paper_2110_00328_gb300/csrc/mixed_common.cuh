@@ -454,7 +454,9 @@ __device__ __forceinline__ void prolong_quad(int nc, const float* __restrict__ e
 // Each fine row's second-colour pair is corrected (and its q written) exactly
 // as prolong_quad<true, SplitLayout, QK, true> does it.  Grid as the
 // restriction's: (ceil(nf/128), nc [J], ceil(nc/4) [I]), block (32, 4).
-template <int QK>
+// DD: eH holds the coarse difference eH - Re itself (written by the coarse
+// level's last post-smoothing pass, smooth_quad's WD), and Re is not read.
+template <int QK, bool DD = false>
 __device__ __forceinline__ void prolong_split2x2_second(int nc, const float* __restrict__ eH,
                                                         const float* __restrict__ Re, const float* __restrict__ ub,
                                                         float* __restrict__ ef, int I, int J, int tq, int lane,
@@ -476,10 +478,16 @@ __device__ __forceinline__ void prolong_split2x2_second(int nc, const float* __r
 #pragma unroll
     for (int y = 0; y < 3; ++y) {
       const long long r = ((long long)Iv[x] * nc + Jv[y]) * nc;
-      const float2 a = ld2(eH + r + K0), b = ld2(Re + r + K0);
-      d[x][y] = make_float2(a.x - b.x, a.y - b.y);
-      dm[x][y] = edge_m ? eH[r + Km] - Re[r + Km] : 0.f;
-      dp[x][y] = edge_p ? eH[r + Kp] - Re[r + Kp] : 0.f;
+      if constexpr (DD) {
+        d[x][y] = ld2(eH + r + K0);
+        dm[x][y] = edge_m ? eH[r + Km] : 0.f;
+        dp[x][y] = edge_p ? eH[r + Kp] : 0.f;
+      } else {
+        const float2 a = ld2(eH + r + K0), b = ld2(Re + r + K0);
+        d[x][y] = make_float2(a.x - b.x, a.y - b.y);
+        dm[x][y] = edge_m ? eH[r + Km] - Re[r + Km] : 0.f;
+        dp[x][y] = edge_p ? eH[r + Kp] - Re[r + Kp] : 0.f;
+      }
     }
   constexpr float w = 1.f / 64.f;
   const long long H = (long long)nf * nf * h;

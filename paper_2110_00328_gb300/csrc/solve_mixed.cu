@@ -61,15 +61,18 @@ __global__ void __launch_bounds__(64) k_smooth32(LevelF f, int n, float* __restr
 
 // Quad version (levels with n % 4 == 0) on the planes i0 .. i0+np-1 (mod n):
 // block (32, 4) = four rows (i, j), grid (ceil(n/128), n, ceil(np/4)).
-template <int K>
+template <int K, bool WD = false>
 __global__ void __launch_bounds__(128) k_smooth32q(LevelF f, int n, float* __restrict__ e,
                                                    const float* __restrict__ ub, const float* __restrict__ rho,
-                                                   const float* __restrict__ S, int parity, int i0, int np) {
+                                                   const float* __restrict__ S, int parity, int i0, int np,
+                                                   const float* __restrict__ Re = nullptr,
+                                                   float* __restrict__ D = nullptr) {
   const int z = blockIdx.z * 4 + threadIdx.y;
   if (z >= np) return;  // whole warps: z is uniform in a warp
   int i = i0 + z;
   if (i >= n) i -= n;
-  smooth_quad<K>(f, n, e, ub, rho, S, i, blockIdx.y, blockIdx.x * 32 + threadIdx.x, threadIdx.x, parity);
+  smooth_quad<K, WD>(f, n, e, ub, rho, S, i, blockIdx.y, blockIdx.x * 32 + threadIdx.x, threadIdx.x, parity, Re,
+                     D);
 }
 
 template <int K>
@@ -156,15 +159,15 @@ __global__ void __launch_bounds__(128) k_prolong_correct32q(int nc, const float*
 
 // Second-colour prolongation on a split finest level with stored q, four fine
 // rows per lane (prolong_split2x2_second); grid as the restriction's.
-template <int QK>
+template <int QK, bool DD = false>
 __global__ void __launch_bounds__(128) k_prolong32_split2x2(int nc, const float* __restrict__ eH,
                                                             const float* __restrict__ Re, const float* __restrict__ ub,
                                                             float* __restrict__ ef, unsigned long long* guard,
                                                             float* __restrict__ qf) {
   const int I = blockIdx.z * 4 + threadIdx.y;
   if (I >= nc) return;  // whole warps
-  prolong_split2x2_second<QK>(nc, eH, Re, ub, ef, I, blockIdx.y, blockIdx.x * 32 + threadIdx.x, threadIdx.x, guard,
-                              qf);
+  prolong_split2x2_second<QK, DD>(nc, eH, Re, ub, ef, I, blockIdx.y, blockIdx.x * 32 + threadIdx.x, threadIdx.x,
+                                  guard, qf);
 }
 
 // Restriction after pre-smoothing on a split finest level with stored q, the
@@ -455,7 +458,9 @@ struct L2Scope {
   }
 };
 
-static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
+// wd: the last sweep's passes also store D = e - Re (smooth_quad's WD) in the
+// level's second buffer, for the finest level's prolongation (fine_reads_d).
+static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st, bool wd = false) {
   Level& L = C.ws->lev[l];
   const float* rho = C.need_rho ? L.rho32 : nullptr;
   const int tk = sweep_tile_k(L.n);
@@ -516,8 +521,13 @@ static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
           return MGGLAM_OK;
         }
         const dim3 g((L.n / 4 + 31) / 32, L.n, (np + 3) / 4);
-        MG_DISPATCH32(C.m.kind, (k_smooth32q<KK><<<g, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, rho, L.S32,
-                                                                            parity, i0, np)));
+        if (wd && s == sweeps - 1) {
+          MG_DISPATCH32(C.m.kind, (k_smooth32q<KK, true><<<g, dim3(32, 4), 0, st>>>(
+                                       C.lf[l], L.n, L.e, L.ub, rho, L.S32, parity, i0, np, L.Re, L.e_alt)));
+        } else {
+          MG_DISPATCH32(C.m.kind, (k_smooth32q<KK><<<g, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, rho, L.S32,
+                                                                              parity, i0, np)));
+        }
         return MGGLAM_OK;
       };
       if (P <= 0) {
@@ -546,6 +556,18 @@ static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st) {
 }
 
 static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode);
+
+// Whether the finest level's second-colour prolongation reads the coarse
+// difference eH - Re that level 1's last post-smoothing sweep stores in its
+// second buffer (unused there: the split layout excludes the fused sweep): a
+// split f(R) n = 1, 2 finest level with post-smoothing, whose level 1 is smoothed
+// by the quad kernel (neither the coarsest, a tail, nor slab-scheduled).
+static bool fine_reads_d(const MixedCtx& C) {
+  const Workspace* ws = C.ws;
+  if (!(C.split && C.qs && C.prm->nu2 >= 1 && ws->nlev > 2 && C.tail_level != 1)) return false;
+  const int n1 = ws->lev[1].n;
+  return n1 % 4 == 0 && n1 >= 16 && !use_fused(C, n1) && slab_planes(C, n1) == 0 && ws->lev[1].e_alt;
+}
 
 // The FAS source on level l (natural layout).
 static int fas_source(const MixedCtx& C, int l, cudaStream_t st) {
@@ -747,7 +769,12 @@ static int prolong_level(const MixedCtx& C, int l, cudaStream_t st, bool both = 
     // with post-smoothing the first colour's corrections would be overwritten unread (prolong_quad)
     const bool second_only = !both && C.prm->nu2 >= 1;
     const dim3 g2((L.n / 4 + 31) / 32, H.n, (H.n + 3) / 4);
-    if (C.qs && C.m.kind == KFR1 && second_only)
+    const bool dd = second_only && fine_reads_d(C);  // H.e_alt holds eH - Re
+    if (C.qs && C.m.kind == KFR1 && dd)
+      k_prolong32_split2x2<KFR1, true><<<g2, dim3(32, 4), 0, st>>>(H.n, H.e_alt, H.Re, L.ub, L.e, C.guard, C.qs);
+    else if (C.qs && C.m.kind == KFR2 && dd)
+      k_prolong32_split2x2<KFR2, true><<<g2, dim3(32, 4), 0, st>>>(H.n, H.e_alt, H.Re, L.ub, L.e, C.guard, C.qs);
+    else if (C.qs && C.m.kind == KFR1 && second_only)
       k_prolong32_split2x2<KFR1><<<g2, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard, C.qs);
     else if (C.qs && C.m.kind == KFR2 && second_only)
       k_prolong32_split2x2<KFR2><<<g2, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard, C.qs);
@@ -805,7 +832,7 @@ static int vcycle32(const MixedCtx& C, int l, cudaStream_t st, int mode) {
   if (l == 0) { prof_end(st); prof_begin(PC_PROLONG32_FINE, st, (C.qs && C.prm->nu2 >= 1 ? 9.0 : 13.0) * L.n3); }
   if ((rc = prolong_level(C, l, st))) return rc;
   if (l == 0) { prof_end(st); prof_begin(PC_SMOOTH32_FINE, st, 16.0 * L.n3 * C.prm->nu2); }
-  rc = smooth32(C, l, C.prm->nu2, st);
+  rc = smooth32(C, l, C.prm->nu2, st, l == 1 && fine_reads_d(C));
   if (l == 0) prof_end(st);
   return rc;
 }

@@ -283,11 +283,14 @@ __device__ __forceinline__ float update_quad(const LevelF& f, float u, float e, 
   else return update_e_fast<K>(f, u, e, rho, s, Lnb);
 }
 
-template <int K>
+// WD: also store D = e - Re at the cells this pass updates (the coarse difference
+// that the finest level's prolongation then reads in place of e and Re).
+template <int K, bool WD = false>
 __device__ __forceinline__ void smooth_quad(const LevelF& f, int n, float* __restrict__ e,
                                             const float* __restrict__ ub, const float* __restrict__ rho,
                                             const float* __restrict__ S, int i, int j, int tq, int lane,
-                                            int parity) {
+                                            int parity, const float* __restrict__ Re = nullptr,
+                                            float* __restrict__ D = nullptr) {
   constexpr bool FR = is_fr(K);
   constexpr bool RHO = (K == KSYM) || (K == KCQ);
   const int nq = n >> 2;
@@ -314,6 +317,8 @@ __device__ __forceinline__ void smooth_quad(const LevelF& f, int n, float* __res
   if constexpr (RHO) {
     if (rho) R = ld4(rho + c0);  // CQ without the exponential coupling passes no density
   }
+  float4 Rq = make_float4(0.f, 0.f, 0.f, 0.f);
+  if constexpr (WD) Rq = ld4(Re + c0);
   if (((i + j + parity) & 1) == 0) {
     // cells k0 (x) and k0+2 (z); k-neighbours k0-1 (previous lane's w), y, w
     const float qy = nbq<K>(U.y, E.y), qw = nbq<K>(U.w, E.w);
@@ -331,6 +336,10 @@ __device__ __forceinline__ void smooth_quad(const LevelF& f, int n, float* __res
     if (act) {
       e0[0] = eA;
       e0[2] = eB;
+      if constexpr (WD) {
+        D[c0] = eA - Rq.x;
+        D[c0 + 2] = eB - Rq.z;
+      }
     }
   } else {
     // cells k0+1 (y) and k0+3 (w); k-neighbours x, z, k0+4 (next lane's x)
@@ -349,6 +358,10 @@ __device__ __forceinline__ void smooth_quad(const LevelF& f, int n, float* __res
     if (act) {
       e0[1] = eA;
       e0[3] = eB;
+      if constexpr (WD) {
+        D[c0 + 1] = eA - Rq.y;
+        D[c0 + 3] = eB - Rq.w;
+      }
     }
   }
 }
