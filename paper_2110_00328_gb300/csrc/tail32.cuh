@@ -42,17 +42,40 @@ static inline size_t tail_smem_bytes(const TailArgs& A) {
   return cells * sizeof(float);
 }
 
+// nb_sum_g's sum (same terms, same order) with 32-bit shared-memory offsets.
+template <int K>
+__device__ __forceinline__ float tail_nb_sum(const float* e, const float* ub, int n, int i, int j, int k) {
+  const int nn = n * n, c = (i * n + j) * n + k;
+  const int ip = i + 1 < n ? nn : nn - n * nn, im = i > 0 ? -nn : n * nn - nn;
+  const int jp = j + 1 < n ? n : n - nn, jm = j > 0 ? -n : nn - n;
+  const int kp = k + 1 < n ? 1 : 1 - n, km = k > 0 ? -1 : n - 1;
+  const int c0 = c + ip, c1 = c + im, c2 = c + jp, c3 = c + jm, c4 = c + kp, c5 = c + km;
+  if constexpr (is_fr(K)) {
+    return dw<K>(ub[c0], e[c0]) + dw<K>(ub[c1], e[c1]) + dw<K>(ub[c2], e[c2]) + dw<K>(ub[c3], e[c3]) +
+           dw<K>(ub[c4], e[c4]) + dw<K>(ub[c5], e[c5]);
+  } else {
+    return e[c0] + e[c1] + e[c2] + e[c3] + e[c4] + e[c5];
+  }
+}
+
 template <int K>
 __device__ __forceinline__ void tail_smooth(const LevelF& f, int n, float* e, const float* ub, const float* rho,
                                             const float* S, int sweeps) {
   const int h = n >> 1, half = h * n * n;
+  const bool p2 = (n & (n - 1)) == 0;  // power-of-two side: index by shifts
+  const int sh = __ffs(n) - 1;
   for (int s = 0; s < sweeps; ++s)
     for (int parity = 0; parity < 2; ++parity) {
       for (int t = threadIdx.x; t < half; t += blockDim.x) {
-        const int kk = t % h, r = t / h, j = r % n, i = r / n;
+        int kk, r, j, i;
+        if (p2) {
+          kk = t & (h - 1), r = t >> (sh - 1), j = r & (n - 1), i = r >> sh;
+        } else {
+          kk = t % h, r = t / h, j = r % n, i = r / n;
+        }
         const int k = 2 * kk + ((i + j + parity) & 1);
         const int c = (i * n + j) * n + k;
-        const float Lnb = nb_sum_g<K>(e, ub, n, i, j, k);
+        const float Lnb = tail_nb_sum<K>(e, ub, n, i, j, k);
         if constexpr (K == KFR1 || K == KFR2)
           e[c] = update_e_warm<K>(f, ub[c], e[c], S[c], Lnb, __activemask());  // the lanes still in the loop
         else
@@ -79,7 +102,7 @@ __device__ __forceinline__ void tail_restrict(const LevelF& f, int nf, const flo
           const float ec = e[c], uc = ub[c];
           se += ec;
           su += uc;
-          sd += local_M<K>(f, uc, ec, rho ? rho[c] : 1.f, nb_sum_g<K>(e, ub, nf, i, j, k)) - S[c];
+          sd += local_M<K>(f, uc, ec, rho ? rho[c] : 1.f, tail_nb_sum<K>(e, ub, nf, i, j, k)) - S[c];
         }
     Re[t] = 0.125f * se;
     eH[t] = 0.125f * se;
@@ -96,7 +119,7 @@ __device__ __forceinline__ void tail_fas(const LevelF& f, int n, const float* Re
   const int n3 = n * n * n;
   for (int t = threadIdx.x; t < n3; t += blockDim.x) {
     const int k = t % n, j = (t / n) % n, i = t / (n * n);
-    S[t] = local_M<K>(f, ub[t], Re[t], rho ? rho[t] : 1.f, nb_sum_g<K>(Re, ub, n, i, j, k)) - S[t];
+    S[t] = local_M<K>(f, ub[t], Re[t], rho ? rho[t] : 1.f, tail_nb_sum<K>(Re, ub, n, i, j, k)) - S[t];
   }
   __syncthreads();
 }
