@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(64) k_smooth32(LevelF f, int n, float* __restr
 
 // Quad version (levels with n % 4 == 0) on the planes i0 .. i0+np-1 (mod n):
 // block (32, 4) = four rows (i, j), grid (ceil(n/128), n, ceil(np/4)).
-template <int K, bool WD = false>
+template <int K, bool WD = false, typename IT = long long>
 __global__ void __launch_bounds__(128) k_smooth32q(LevelF f, int n, float* __restrict__ e,
                                                    const float* __restrict__ ub, const float* __restrict__ rho,
                                                    const float* __restrict__ S, int parity, int i0, int np,
@@ -71,8 +71,8 @@ __global__ void __launch_bounds__(128) k_smooth32q(LevelF f, int n, float* __res
   if (z >= np) return;  // whole warps: z is uniform in a warp
   int i = i0 + z;
   if (i >= n) i -= n;
-  smooth_quad<K, WD>(f, n, e, ub, rho, S, i, blockIdx.y, blockIdx.x * 32 + threadIdx.x, threadIdx.x, parity, Re,
-                     D);
+  smooth_quad<K, WD, IT>(f, n, e, ub, rho, S, i, blockIdx.y, blockIdx.x * 32 + threadIdx.x, threadIdx.x, parity,
+                         Re, D);
 }
 
 template <int K>
@@ -521,9 +521,13 @@ static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st, bool 
           return MGGLAM_OK;
         }
         const dim3 g((L.n / 4 + 31) / 32, L.n, (np + 3) / 4);
+        const bool i32 = L.n <= 1024;  // n^3 <= 2^30: 32-bit cell offsets
         if (wd && s == sweeps - 1) {
-          MG_DISPATCH32(C.m.kind, (k_smooth32q<KK, true><<<g, dim3(32, 4), 0, st>>>(
+          MG_DISPATCH32(C.m.kind, (k_smooth32q<KK, true, int><<<g, dim3(32, 4), 0, st>>>(
                                        C.lf[l], L.n, L.e, L.ub, rho, L.S32, parity, i0, np, L.Re, L.e_alt)));
+        } else if (i32) {
+          MG_DISPATCH32(C.m.kind, (k_smooth32q<KK, false, int><<<g, dim3(32, 4), 0, st>>>(
+                                       C.lf[l], L.n, L.e, L.ub, rho, L.S32, parity, i0, np)));
         } else {
           MG_DISPATCH32(C.m.kind, (k_smooth32q<KK><<<g, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, rho, L.S32,
                                                                               parity, i0, np)));

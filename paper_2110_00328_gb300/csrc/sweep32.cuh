@@ -285,7 +285,9 @@ __device__ __forceinline__ float update_quad(const LevelF& f, float u, float e, 
 
 // WD: also store D = e - Re at the cells this pass updates (the coarse difference
 // that the finest level's prolongation then reads in place of e and Re).
-template <int K, bool WD = false>
+// IT: the index type (int where n^3 < 2^31, which shortens the address
+// arithmetic every lane runs before its first load).
+template <int K, bool WD = false, typename IT = long long>
 __device__ __forceinline__ void smooth_quad(const LevelF& f, int n, float* __restrict__ e,
                                             const float* __restrict__ ub, const float* __restrict__ rho,
                                             const float* __restrict__ S, int i, int j, int tq, int lane,
@@ -296,12 +298,12 @@ __device__ __forceinline__ void smooth_quad(const LevelF& f, int n, float* __res
   const int nq = n >> 2;
   const bool act = tq < nq;
   const int k0 = 4 * (act ? tq : nq - 1);
-  const long long nn = (long long)n * n;
-  const long long c0 = (long long)i * nn + (long long)j * n + k0;
-  const long long djp = (j + 1 < n) ? (long long)n : -(long long)(n - 1) * n;
-  const long long djm = (j > 0) ? -(long long)n : (long long)(n - 1) * n;
-  const long long dip = (i + 1 < n) ? nn : -(long long)(n - 1) * nn;
-  const long long dim = (i > 0) ? -nn : (long long)(n - 1) * nn;
+  const IT nn = (IT)n * n;
+  const IT c0 = (IT)i * nn + (IT)j * n + k0;
+  const IT djp = (j + 1 < n) ? (IT)n : -(IT)(n - 1) * n;
+  const IT djm = (j > 0) ? -(IT)n : (IT)(n - 1) * n;
+  const IT dip = (i + 1 < n) ? nn : -(IT)(n - 1) * nn;
+  const IT dim = (i > 0) ? -nn : (IT)(n - 1) * nn;
   float* e0 = e + c0;
   const float* u0 = ub + c0;
   const float4 E = ld4(e0), U = ld4(u0), Sv = ld4(S + c0);
@@ -324,7 +326,7 @@ __device__ __forceinline__ void smooth_quad(const LevelF& f, int n, float* __res
     const float qy = nbq<K>(U.y, E.y), qw = nbq<K>(U.w, E.w);
     float qm = __shfl_up_sync(0xffffffffu, qw, 1);
     if (lane == 0) {
-      const long long cm = c0 + (k0 == 0 ? n - 1 : -1);
+      const IT cm = c0 + (k0 == 0 ? n - 1 : -1);
       qm = nbq<K>(FR ? ub[cm] : 0.f, e[cm]);
     }
     const float LA = (qm + qy) + (nbq<K>(Ujp.x, Ejp.x) + nbq<K>(Ujm.x, Ejm.x)) +
@@ -346,7 +348,7 @@ __device__ __forceinline__ void smooth_quad(const LevelF& f, int n, float* __res
     const float qx = nbq<K>(U.x, E.x), qz = nbq<K>(U.z, E.z);
     float qp = __shfl_down_sync(0xffffffffu, qx, 1);
     if (lane == 31 || tq + 1 >= nq) {
-      const long long cp = c0 + (k0 + 4 == n ? 4 - n : 4);
+      const IT cp = c0 + (k0 + 4 == n ? 4 - n : 4);
       qp = nbq<K>(FR ? ub[cp] : 0.f, e[cp]);
     }
     const float LA = (qx + qz) + (nbq<K>(Ujp.y, Ejp.y) + nbq<K>(Ujm.y, Ejm.y)) +
