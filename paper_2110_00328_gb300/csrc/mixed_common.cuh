@@ -124,7 +124,7 @@ __device__ __forceinline__ void restrict_quad(const LevelF& f, int nf, const flo
     }
   };
   auto q1 = [&](int i, int j, int k) {
-    const long long c = FL::idx(nf, i, j, k);
+    const typename FL::index_t c = FL::idx(nf, i, j, k);
     return nbq<K>(FR ? ub[c] : 0.f, e[c]);
   };
   // own rows (a, b) and their quads
@@ -191,7 +191,8 @@ __device__ __forceinline__ void restrict_quad(const LevelF& f, int nf, const flo
       sd1 += dz + dv;
     }
   if (act) {
-    const long long t = ((long long)I * nc + J) * nc + (k0 >> 1);
+    using IT = typename FL::index_t;
+    const IT t = ((IT)I * nc + J) * nc + (k0 >> 1);
     const float2 me = make_float2(0.125f * se0, 0.125f * se1);
     *reinterpret_cast<float2*>(Re + t) = me;
     *reinterpret_cast<float2*>(eH + t) = me;
@@ -210,7 +211,7 @@ __device__ __forceinline__ void restrict_quad(const LevelF& f, int nf, const flo
 // two k-neighbours outside the quad from the adjacent lanes.  All 32 lanes of a
 // warp take part; lanes past the row end work on a clamped quad and store
 // nothing.
-template <int K>
+template <int K, typename IT = long long>
 __device__ __forceinline__ void fas_quad(const LevelF& f, int n, const float* __restrict__ Re,
                                          const float* __restrict__ ub, const float* __restrict__ rho,
                                          float* __restrict__ S, int i, int j, int tq, int lane) {
@@ -219,13 +220,13 @@ __device__ __forceinline__ void fas_quad(const LevelF& f, int n, const float* __
   const int nq = n >> 2;
   const bool act = tq < nq;
   const int k0 = 4 * (act ? tq : nq - 1);
-  const long long nn = (long long)n * n;
-  const long long c0 = (long long)i * nn + (long long)j * n + k0;
-  const long long djp = (j + 1 < n) ? (long long)n : -(long long)(n - 1) * n;
-  const long long djm = (j > 0) ? -(long long)n : (long long)(n - 1) * n;
-  const long long dip = (i + 1 < n) ? nn : -(long long)(n - 1) * nn;
-  const long long dim = (i > 0) ? -nn : (long long)(n - 1) * nn;
-  auto q4 = [&](long long c) {
+  const IT nn = (IT)n * n;
+  const IT c0 = (IT)i * nn + (IT)j * n + k0;
+  const IT djp = (j + 1 < n) ? (IT)n : -(IT)(n - 1) * n;
+  const IT djm = (j > 0) ? -(IT)n : (IT)(n - 1) * n;
+  const IT dip = (i + 1 < n) ? nn : -(IT)(n - 1) * nn;
+  const IT dim = (i > 0) ? -nn : (IT)(n - 1) * nn;
+  auto q4 = [&](IT c) {
     const float4 E = ld4(Re + c);
     if constexpr (FR) {
       const float4 U = ld4(ub + c);
@@ -244,11 +245,11 @@ __device__ __forceinline__ void fas_quad(const LevelF& f, int n, const float* __
   float qm = __shfl_up_sync(0xffffffffu, q.w, 1);
   float qp = __shfl_down_sync(0xffffffffu, q.x, 1);
   if (lane == 0) {
-    const long long c = c0 + (k0 == 0 ? n - 1 : -1);
+    const IT c = c0 + (k0 == 0 ? n - 1 : -1);
     qm = nbq<K>(FR ? ub[c] : 0.f, Re[c]);
   }
   if (lane == 31 || tq + 1 >= nq) {
-    const long long c = c0 + (k0 + 4 == n ? 4 - n : 4);
+    const IT c = c0 + (k0 + 4 == n ? 4 - n : 4);
     qp = nbq<K>(FR ? ub[c] : 0.f, Re[c]);
   }
   float4 out;
@@ -378,13 +379,14 @@ __device__ __forceinline__ void prolong_quad(int nc, const float* __restrict__ e
   int I2 = I + ((i & 1) ? 1 : -1), J2 = J + ((j & 1) ? 1 : -1);
   I2 = I2 < 0 ? nc - 1 : (I2 >= nc ? 0 : I2);
   J2 = J2 < 0 ? nc - 1 : (J2 >= nc ? 0 : J2);
-  const long long rA = ((long long)I * nc + J) * nc, rB = ((long long)I2 * nc + J) * nc,
-                  rC = ((long long)I * nc + J2) * nc, rD = ((long long)I2 * nc + J2) * nc;
-  auto d2 = [&](long long r) {
+  using IT = typename FL::index_t;  // the coarse level is the fine one's half: the same index range fits
+  const IT rA = ((IT)I * nc + J) * nc, rB = ((IT)I2 * nc + J) * nc, rC = ((IT)I * nc + J2) * nc,
+           rD = ((IT)I2 * nc + J2) * nc;
+  auto d2 = [&](IT r) {
     const float2 a = ld2(eH + r + K0), b = ld2(Re + r + K0);
     return make_float2(a.x - b.x, a.y - b.y);
   };
-  auto d1 = [&](long long r, int Kc) { return eH[r + Kc] - Re[r + Kc]; };
+  auto d1 = [&](IT r, int Kc) { return eH[r + Kc] - Re[r + Kc]; };
   const float2 A = d2(rA), B = d2(rB), C = d2(rC), D = d2(rD);
   const float Rx = 9.f * A.x + 3.f * (B.x + C.x) + D.x;
   const float Ry = 9.f * A.y + 3.f * (B.y + C.y) + D.y;

@@ -185,11 +185,11 @@ __global__ void __launch_bounds__(128) k_restrict32_split_zr(LevelF f, int nf, c
 }
 
 // FAS source, four cells per lane (n % 4 == 0, n >= 8): grid (ceil(n/128), n, n/4).
-template <int K>
+template <int K, typename IT = long long>
 __global__ void __launch_bounds__(128) k_fas_source32q(LevelF f, int n, const float* __restrict__ Re,
                                                        const float* __restrict__ ub, const float* __restrict__ rho,
                                                        float* __restrict__ S) {
-  fas_quad<K>(f, n, Re, ub, rho, S, blockIdx.z * 4 + threadIdx.y, blockIdx.y, blockIdx.x * 32 + threadIdx.x,
+  fas_quad<K, IT>(f, n, Re, ub, rho, S, blockIdx.z * 4 + threadIdx.y, blockIdx.y, blockIdx.x * 32 + threadIdx.x,
               threadIdx.x);
 }
 
@@ -579,7 +579,12 @@ static int fas_source(const MixedCtx& C, int l, cudaStream_t st) {
   const float* rhoH = C.need_rho ? H.rho32 : nullptr;
   if (H.n % 4 == 0 && H.n >= 8) {
     const dim3 g((H.n / 4 + 31) / 32, H.n, H.n / 4);
-    MG_DISPATCH32(C.m.kind, (k_fas_source32q<KK><<<g, dim3(32, 4), 0, st>>>(C.lf[l], H.n, H.Re, H.ub, rhoH, H.S32)));
+    if (H.n <= 1024) {  // 32-bit cell offsets
+      MG_DISPATCH32(C.m.kind,
+                    (k_fas_source32q<KK, int><<<g, dim3(32, 4), 0, st>>>(C.lf[l], H.n, H.Re, H.ub, rhoH, H.S32)));
+    } else {
+      MG_DISPATCH32(C.m.kind, (k_fas_source32q<KK><<<g, dim3(32, 4), 0, st>>>(C.lf[l], H.n, H.Re, H.ub, rhoH, H.S32)));
+    }
   } else {
     const int bh = bx_for(H.n);
     MG_DISPATCH32(C.m.kind, (k_fas_source32<KK><<<grid3(H.n, H.n, H.n, bh), bh, 0, st>>>(C.lf[l], H.n, H.Re, H.ub,
@@ -703,6 +708,23 @@ static void tail_allow_smem() {
   cudaFuncSetAttribute(k_tail32<KCQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+// The natural-layout restriction after pre-smoothing (ZR), per model kind.
+template <class FL, bool ZR>
+static void launch_restrict_nat(const MixedCtx& C, int l, const float* rho, dim3 g, cudaStream_t st) {
+  Level& L = C.ws->lev[l];
+  Level& H = C.ws->lev[l + 1];
+  switch (C.m.kind) {
+    case KFR0: k_residual_restrict32q<KFR0, FL, false, ZR><<<g, dim3(32, 4), 0, st>>>(
+                   C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32, nullptr); break;
+    case KFR1: k_residual_restrict32q<KFR1, FL, false, ZR><<<g, dim3(32, 4), 0, st>>>(
+                   C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32, nullptr); break;
+    case KFR2: k_residual_restrict32q<KFR2, FL, false, ZR><<<g, dim3(32, 4), 0, st>>>(
+                   C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32, nullptr); break;
+    default: k_residual_restrict32q<KSYM, FL, false, ZR><<<g, dim3(32, 4), 0, st>>>(
+                   C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32, nullptr); break;
+  }
+}
+
 // Residual and restriction from level l to l+1: H.Re = R e, H.e = R e (the coarse
 // start), H.ub = R ub, H.S32 = R (M(e) - S); the FAS source follows (fas_source).
 // relaxed: the level's second colour was the last one relaxed (pre-smoothing
@@ -738,21 +760,19 @@ static int restrict_level(const MixedCtx& C, int l, cudaStream_t st, bool relaxe
     }
   } else if (L.n % 4 == 0 && L.n >= 8) {
     const dim3 g((L.n / 4 + 31) / 32, H.n, (H.n + 3) / 4);
+    // 32-bit cell offsets where n^3 < 2^31
     if (relaxed && C.m.kind != KCQ) {
-      switch (C.m.kind) {
-        case KFR0: k_residual_restrict32q<KFR0, NatLayout, false, true><<<g, dim3(32, 4), 0, st>>>(
-                       C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32, nullptr); break;
-        case KFR1: k_residual_restrict32q<KFR1, NatLayout, false, true><<<g, dim3(32, 4), 0, st>>>(
-                       C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32, nullptr); break;
-        case KFR2: k_residual_restrict32q<KFR2, NatLayout, false, true><<<g, dim3(32, 4), 0, st>>>(
-                       C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32, nullptr); break;
-        default: k_residual_restrict32q<KSYM, NatLayout, false, true><<<g, dim3(32, 4), 0, st>>>(
-                       C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32, nullptr); break;
-      }
+      if (L.n <= 1024) launch_restrict_nat<NatLayout32, true>(C, l, rho, g, st);
+      else launch_restrict_nat<NatLayout, true>(C, l, rho, g, st);
       note_launch(1);
     } else {
-      MG_DISPATCH32(C.m.kind, (k_residual_restrict32q<KK><<<g, dim3(32, 4), 0, st>>>(
-                                   C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32, nullptr)));
+      if (L.n <= 1024) {
+        MG_DISPATCH32(C.m.kind, (k_residual_restrict32q<KK, NatLayout32><<<g, dim3(32, 4), 0, st>>>(
+                                     C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32, nullptr)));
+      } else {
+        MG_DISPATCH32(C.m.kind, (k_residual_restrict32q<KK><<<g, dim3(32, 4), 0, st>>>(
+                                     C.lf[l], L.n, L.e, L.ub, rho, L.S32, H.Re, H.e, H.ub, H.S32, nullptr)));
+      }
     }
   } else {
     MG_DISPATCH32(C.m.kind, (k_residual_restrict32<KK><<<grid3(H.n, H.n, H.n, bh), bh, 0, st>>>(
@@ -793,8 +813,15 @@ static int prolong_level(const MixedCtx& C, int l, cudaStream_t st, bool both = 
     else k_prolong_correct32q<false, SplitLayout><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard);
   } else if (L.n % 4 == 0 && L.n >= 8) {
     const dim3 g((L.n / 4 + 31) / 32, L.n, L.n / 4);
-    if (is_fr(C.m.kind)) k_prolong_correct32q<true><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard);
-    else k_prolong_correct32q<false><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard);
+    const bool i32 = L.n <= 1024;  // 32-bit cell offsets
+    if (is_fr(C.m.kind) && i32)
+      k_prolong_correct32q<true, NatLayout32><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard);
+    else if (is_fr(C.m.kind))
+      k_prolong_correct32q<true><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard);
+    else if (i32)
+      k_prolong_correct32q<false, NatLayout32><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard);
+    else
+      k_prolong_correct32q<false><<<g, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard);
   } else if (is_fr(C.m.kind)) {
     k_prolong_correct32<true><<<grid3(L.n, L.n, L.n, bf), bf, 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard);
   } else {

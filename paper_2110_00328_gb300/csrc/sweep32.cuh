@@ -455,6 +455,7 @@ static inline long long split_warps(int n, int np) {
 
 // Access to a level as interleaved quads: natural layout or red-black split.
 struct NatLayout {
+  using index_t = long long;
   static __device__ __forceinline__ float4 q(const float* a, int n, int i, int j, int k0) {
     return ld4(a + ((long long)i * n + j) * n + k0);
   }
@@ -463,7 +464,19 @@ struct NatLayout {
   }
   static __device__ __forceinline__ long long idx(int n, int i, int j, int k) { return ((long long)i * n + j) * n + k; }
 };
+// NatLayout with 32-bit offsets, for levels with n^3 < 2^31 (n <= 1024 here).
+struct NatLayout32 {
+  using index_t = int;
+  static __device__ __forceinline__ float4 q(const float* a, int n, int i, int j, int k0) {
+    return ld4(a + (i * n + j) * n + k0);
+  }
+  static __device__ __forceinline__ void st(float* a, int n, int i, int j, int k0, float4 v) {
+    *reinterpret_cast<float4*>(a + (i * n + j) * n + k0) = v;
+  }
+  static __device__ __forceinline__ int idx(int n, int i, int j, int k) { return (i * n + j) * n + k; }
+};
 struct SplitLayout {
+  using index_t = long long;
   static __device__ __forceinline__ float4 q(const float* a, int n, int i, int j, int k0) {
     return ld4_split(a, n, i, j, k0);
   }
