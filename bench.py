@@ -89,8 +89,8 @@ def measured_peaks():
 # dram__bytes_write.sum of both colour launches of a warm sweep (cycle 6, the
 # path every pass after an inner solve's first sweep takes), from one ncu
 # capture; valid while the kernel's sources hash to the value recorded with it.
-SMOOTHER_TRAFFIC = {"bytes_per_sweep": (134.501376 + 43.358976 + 134.504448 + 38.751488) * 1e6,
-                    "source_sha256_16": "49428eddad48236d"}
+SMOOTHER_TRAFFIC = {"bytes_per_sweep": (134.520576 + 43.065344 + 134.503680 + 38.631680) * 1e6,
+                    "source_sha256_16": "255035e13679efa1"}
 
 
 def smoother_traffic_per_sweep():

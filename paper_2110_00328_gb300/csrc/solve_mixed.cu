@@ -509,10 +509,16 @@ static int smooth32(const MixedCtx& C, int l, int sweeps, cudaStream_t st, bool 
             auto go = [&](auto kern) {
               return cudaLaunchKernelEx(&cfg, kern, C.lf[l], L.n, L.e, ubc, no_rho, Sc, parity, i0, np, C.qs, pdl);
             };
-            const bool f1 = C.m.kind == KFR1;
-            if (fresh == 3) MG_CUDA_TRY(f1 ? go(k_smooth32s<KFR1, true, 3>) : go(k_smooth32s<KFR2, true, 3>));
-            else if (fresh == 1) MG_CUDA_TRY(f1 ? go(k_smooth32s<KFR1, true, 1>) : go(k_smooth32s<KFR2, true, 1>));
-            else MG_CUDA_TRY(f1 ? go(k_smooth32s<KFR1, true>) : go(k_smooth32s<KFR2, true>));
+            const bool f1 = C.m.kind == KFR1, i32 = L.n <= 1024;  // 32-bit cell offsets where n^3 <= 2^30
+            if (fresh == 3)
+              MG_CUDA_TRY(f1 ? go(i32 ? k_smooth32s<KFR1, true, 3, int> : k_smooth32s<KFR1, true, 3>)
+                             : go(i32 ? k_smooth32s<KFR2, true, 3, int> : k_smooth32s<KFR2, true, 3>));
+            else if (fresh == 1)
+              MG_CUDA_TRY(f1 ? go(i32 ? k_smooth32s<KFR1, true, 1, int> : k_smooth32s<KFR1, true, 1>)
+                             : go(i32 ? k_smooth32s<KFR2, true, 1, int> : k_smooth32s<KFR2, true, 1>));
+            else
+              MG_CUDA_TRY(f1 ? go(i32 ? k_smooth32s<KFR1, true, 0, int> : k_smooth32s<KFR1, true>)
+                             : go(i32 ? k_smooth32s<KFR2, true, 0, int> : k_smooth32s<KFR2, true>));
             note_launch(1);
             return MGGLAM_OK;
           }

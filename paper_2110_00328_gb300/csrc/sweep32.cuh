@@ -505,7 +505,8 @@ struct SplitLayout {
 // (q written beside e).  q is formed by the same expression from the same
 // values, so the sweep computes what it computes without it, up to where the
 // compiler fuses a product into the neighbouring sum.
-template <int K, bool QS = false, int FRESH = 0>
+// IT: the index type of the cell offsets (int where 2 n^2 (n/2) < 2^31).
+template <int K, bool QS = false, int FRESH = 0, typename IT = long long>
 __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __restrict__ e,
                                              const float* __restrict__ ub, const float* __restrict__ rho,
                                              const float* __restrict__ S, int i, int j, int seg, bool act,
@@ -515,18 +516,18 @@ __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __re
   constexpr bool RHO = (K == KSYM) || (K == KCQ);
   const int h = n >> 1, nq = h >> 2;
   const int m0 = 4 * seg;
-  const long long H = (long long)n * n * h;
-  const long long r0 = ((long long)i * n + j) * h + m0;
-  const long long djp = (j + 1 < n) ? (long long)h : -(long long)(n - 1) * h;
-  const long long djm = (j > 0) ? -(long long)h : (long long)(n - 1) * h;
-  const long long nh = (long long)n * h;
-  const long long dip = (i + 1 < n) ? nh : -(long long)(n - 1) * nh;
-  const long long dim = (i > 0) ? -nh : (long long)(n - 1) * nh;
+  const IT H = (IT)n * n * h;
+  const IT r0 = ((IT)i * n + j) * h + m0;
+  const IT djp = (j + 1 < n) ? (IT)h : -(IT)(n - 1) * h;
+  const IT djm = (j > 0) ? -(IT)h : (IT)(n - 1) * h;
+  const IT nh = (IT)n * h;
+  const IT dip = (i + 1 < n) ? nh : -(IT)(n - 1) * nh;
+  const IT dim = (i > 0) ? -nh : (IT)(n - 1) * nh;
   const int p = (i + j + colour) & 1;
-  float* eo = e + (long long)colour * H + r0;               // own colour
-  const float* e1 = e + (long long)(colour ^ 1) * H + r0;   // other colour
-  const float* uo = ub + (long long)colour * H + r0;
-  const float* u1 = ub + (long long)(colour ^ 1) * H + r0;
+  float* eo = e + (IT)colour * H + r0;               // own colour
+  const float* e1 = e + (IT)(colour ^ 1) * H + r0;   // other colour
+  const float* uo = ub + (IT)colour * H + r0;
+  const float* u1 = ub + (IT)(colour ^ 1) * H + r0;
   if constexpr (QS) {
     // pdl (programmatic dependent launch): 1 = the previous kernel is a colour
     // pass, which writes only its own colour's e and q, so this colour's u and S
@@ -539,10 +540,10 @@ __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __re
     // zero): bit 0, this colour's e is zero and is not read; bit 1, the other
     // colour's q = Delta w(u, 0) is zero too and is not read.  The result is the
     // one the zero arrays would give.
-    const float* q1 = q + (long long)(colour ^ 1) * H + r0;  // other colour's q
+    const float* q1 = q + (IT)(colour ^ 1) * H + r0;  // other colour's q
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (pdl == 2) asm volatile("griddepcontrol.wait;" ::: "memory");
-    const float4 U = ld4(uo), Sv = ld4(S + (long long)colour * H + r0), E = (FRESH & 1) ? z4 : ld4(eo);
+    const float4 U = ld4(uo), Sv = ld4(S + (IT)colour * H + r0), E = (FRESH & 1) ? z4 : ld4(eo);
     if (pdl == 1) asm volatile("griddepcontrol.wait;" ::: "memory");
     if (pdl) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     float4 Q = z4, Qjp = z4, Qjm = z4, Qip = z4, Qim = z4;
@@ -574,17 +575,17 @@ __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __re
     out.w = update_e_warm<K>(f, U.w, E.w, Sv.w, L3);
     if (act) {
       *reinterpret_cast<float4*>(eo) = out;
-      *reinterpret_cast<float4*>(q + (long long)colour * H + r0) =
+      *reinterpret_cast<float4*>(q + (IT)colour * H + r0) =
           make_float4(nbq<K>(U.x, out.x), nbq<K>(U.y, out.y), nbq<K>(U.z, out.z), nbq<K>(U.w, out.w));
     }
     return;
   }
-  const float4 U = ld4(uo), Sv = ld4(S + (long long)colour * H + r0);
+  const float4 U = ld4(uo), Sv = ld4(S + (IT)colour * H + r0);
   float4 E = make_float4(0.f, 0.f, 0.f, 0.f);
   if constexpr (!FR) E = ld4(eo);
   float4 R = make_float4(1.f, 1.f, 1.f, 1.f);
   if constexpr (RHO) {
-    if (rho) R = ld4(rho + (long long)colour * H + r0);
+    if (rho) R = ld4(rho + (IT)colour * H + r0);
   }
   const float4 Er = ld4(e1);
   const float4 Ejp = ld4(e1 + djp), Ejm = ld4(e1 + djm), Eip = ld4(e1 + dip), Eim = ld4(e1 + dim);
@@ -600,12 +601,12 @@ __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __re
   float qm = __shfl_up_sync(0xffffffffu, Q.w, 1);    // other colour at m0 - 1
   float qp = __shfl_down_sync(0xffffffffu, Q.x, 1);  // other colour at m0 + 4
   if (p == 0 && (seg == 0 || lane == 0)) {
-    const long long c = r0 + (m0 == 0 ? h - 1 : -1);
-    qm = nbq<K>(FR ? ub[(long long)(colour ^ 1) * H + c] : 0.f, e[(long long)(colour ^ 1) * H + c]);
+    const IT c = r0 + (m0 == 0 ? h - 1 : -1);
+    qm = nbq<K>(FR ? ub[(IT)(colour ^ 1) * H + c] : 0.f, e[(IT)(colour ^ 1) * H + c]);
   }
   if (p == 1 && (seg == nq - 1 || lane == 31)) {
-    const long long c = r0 + (m0 + 4 == h ? 4 - h : 4);
-    qp = nbq<K>(FR ? ub[(long long)(colour ^ 1) * H + c] : 0.f, e[(long long)(colour ^ 1) * H + c]);
+    const IT c = r0 + (m0 + 4 == h ? 4 - h : 4);
+    qp = nbq<K>(FR ? ub[(IT)(colour ^ 1) * H + c] : 0.f, e[(IT)(colour ^ 1) * H + c]);
   }
   // the two k-neighbours of own cell t: other-colour m0+t-1+p and m0+t+p
   const float k0s = p ? Q.x + Q.y : qm + Q.x;
@@ -629,7 +630,7 @@ __device__ __forceinline__ void smooth_split(const LevelF& f, int n, float* __re
 // per warp, a long row over several warps), four cells per lane; block (32, 4),
 // 1D grid over warps.
 // QS: f(R) n = 1, 2 with the neighbour quantity q stored beside e (smooth_split).
-template <int K, bool QS = false, int FRESH = 0>
+template <int K, bool QS = false, int FRESH = 0, typename IT = long long>
 __global__ void __launch_bounds__(128, QS ? 10 : 1) k_smooth32s(LevelF f, int n, float* __restrict__ e,
                                                    const float* __restrict__ ub, const float* __restrict__ rho,
                                                    const float* __restrict__ S, int colour, int i0, int np,
@@ -645,7 +646,7 @@ __global__ void __launch_bounds__(128, QS ? 10 : 1) k_smooth32s(LevelF f, int n,
   int i = i0 + (int)(pow2 ? r >> sh : r / n);
   if (i >= n) i -= n;
   const int j = (int)(pow2 ? r & (n - 1) : r % n);
-  smooth_split<K, QS, FRESH>(f, n, e, ub, rho, S, i, j, seg, act, colour, lane, q, pdl);
+  smooth_split<K, QS, FRESH, IT>(f, n, e, ub, rho, S, i, j, seg, act, colour, lane, q, pdl);
 }
 
 }  // namespace mg
