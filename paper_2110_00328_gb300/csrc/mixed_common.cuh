@@ -273,7 +273,8 @@ __device__ __forceinline__ void fas_quad(const LevelF& f, int n, const float* __
 // all six neighbours of a first-colour cell are second-colour cells, whose
 // stored q lies in the second colour's half at the same index (the i and j
 // neighbours) or the adjacent ones (the k neighbours).
-template <int K>
+// IT: the index type of the cell offsets (int where the fine level has < 2^31 cells).
+template <int K, typename IT = long long>
 __device__ __forceinline__ void restrict_split_zr(const LevelF& f, int nf, const float* __restrict__ e,
                                                   const float* __restrict__ ub, const float* __restrict__ S,
                                                   const float* __restrict__ qf, float* __restrict__ Re,
@@ -283,11 +284,11 @@ __device__ __forceinline__ void restrict_split_zr(const LevelF& f, int nf, const
   const int nc = nf >> 1, nq = nf >> 2, h = nf >> 1;
   const bool act = tq < nq;
   const int m0 = 2 * (act ? tq : nq - 1);  // index of the quad in a colour half-row
-  const long long H = (long long)nf * nf * h;
+  const IT H = (IT)nf * nf * h;
   const int i0 = 2 * I, j0 = 2 * J;
   const int iA = i0 == 0 ? nf - 1 : i0 - 1, iB = i0 + 2 == nf ? 0 : i0 + 2;
   const int jA = j0 == 0 ? nf - 1 : j0 - 1, jB = j0 + 2 == nf ? 0 : j0 + 2;
-  auto row = [&](int i, int j) { return ((long long)i * nf + j) * h + m0; };
+  auto row = [&](int i, int j) { return ((IT)i * nf + j) * h + m0; };
   const float* q1 = qf + H;  // second-colour half of q
   // second-colour q of the own rows and of the halo rows around them
   float2 Q[2][2], qi[2][2], qj[2][2];
@@ -310,7 +311,7 @@ __device__ __forceinline__ void restrict_split_zr(const LevelF& f, int nf, const
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
-      const long long r = row(i0 + a, j0 + b);
+      const IT r = row(i0 + a, j0 + b);
       const float2 E0 = ld2(e + r), E1 = ld2(e + H + r), U0 = ld2(ub + r), U1 = ld2(ub + H + r);
       const float2 S0 = ld2(S + r);
       se0 += E0.x + E1.x;
@@ -336,7 +337,7 @@ __device__ __forceinline__ void restrict_split_zr(const LevelF& f, int nf, const
       sd1 += dy;
     }
   if (act) {
-    const long long t = ((long long)I * nc + J) * nc + m0;
+    const IT t = ((IT)I * nc + J) * nc + m0;
     const float2 me = make_float2(0.125f * se0, 0.125f * se1);
     *reinterpret_cast<float2*>(Re + t) = me;
     *reinterpret_cast<float2*>(eH + t) = me;
@@ -458,7 +459,7 @@ __device__ __forceinline__ void prolong_quad(int nc, const float* __restrict__ e
 // restriction's: (ceil(nf/128), nc [J], ceil(nc/4) [I]), block (32, 4).
 // DD: eH holds the coarse difference eH - Re itself (written by the coarse
 // level's last post-smoothing pass, smooth_quad's WD), and Re is not read.
-template <int QK, bool DD = false>
+template <int QK, bool DD = false, typename IT = long long>
 __device__ __forceinline__ void prolong_split2x2_second(int nc, const float* __restrict__ eH,
                                                         const float* __restrict__ Re, const float* __restrict__ ub,
                                                         float* __restrict__ ef, int I, int J, int tq, int lane,
@@ -479,7 +480,7 @@ __device__ __forceinline__ void prolong_split2x2_second(int nc, const float* __r
   for (int x = 0; x < 3; ++x)
 #pragma unroll
     for (int y = 0; y < 3; ++y) {
-      const long long r = ((long long)Iv[x] * nc + Jv[y]) * nc;
+      const IT r = ((IT)Iv[x] * nc + Jv[y]) * nc;
       if constexpr (DD) {
         d[x][y] = ld2(eH + r + K0);
         dm[x][y] = edge_m ? eH[r + Km] : 0.f;
@@ -492,7 +493,7 @@ __device__ __forceinline__ void prolong_split2x2_second(int nc, const float* __r
       }
     }
   constexpr float w = 1.f / 64.f;
-  const long long H = (long long)nf * nf * h;
+  const IT H = (IT)nf * nf * h;
   unsigned ng = 0;
 #pragma unroll
   for (int a = 0; a < 2; ++a)
@@ -510,7 +511,7 @@ __device__ __forceinline__ void prolong_split2x2_second(int nc, const float* __r
       const float cA = odd ? (3.f * Rx + Rm) * w : (3.f * Rx + Ry) * w;
       const float cB = odd ? (3.f * Ry + Rx) * w : (3.f * Ry + Rp) * w;
       const int i = 2 * I + a, j = 2 * J + b;
-      const long long o1 = H + ((long long)i * nf + j) * h + (k0 >> 1);
+      const IT o1 = H + ((IT)i * nf + j) * h + (k0 >> 1);
       const float2 old = ld2(ef + o1), u = ld2(ub + o1);
       float vA = old.x + cA, vB = old.y + cB;
       const bool gA = !(u.x + vA > 0.f), gB = !(u.y + vB > 0.f);
@@ -776,7 +777,8 @@ __device__ __forceinline__ double outer_residual_tile_ff(const FFC& C, int n, in
 // 2m + 1 of a row sit at the same k/2 of the two colour arrays).  The six-
 // neighbour sum and the source terms of each cell are formed in the same order
 // as in outer_residual_tile_ff, so each cell's residual is the same float.
-template <int K, int TJ, bool SPLIT>
+// IT: the index type of the cell offsets (int where n^3 < 2^31).
+template <int K, int TJ, bool SPLIT, typename IT = long long>
 __global__ void __launch_bounds__(TJ * 32, 5) k_outer_residual_ff2(const FFC* __restrict__ Cp, int n, int chunk,
                                                                const double* __restrict__ u,
                                                                const float* __restrict__ rho, float* __restrict__ ub,
@@ -803,20 +805,20 @@ __global__ void __launch_bounds__(TJ * 32, 5) k_outer_residual_ff2(const FFC* __
   const int ty = t >> 5, tx = t & 31;
   const int jg = j0 + ty, kg = k0 + 2 * tx;
   const int cc = (ty + 1) * RS + 2 * tx + 2;  // slot index of cell kg; cell kg + 1 at cc + 1
-  const size_t nn = (size_t)n * n;
-  size_t off[NE];
+  const IT nn = (IT)n * n;
+  IT off[NE];
   int pos[NE];
 #pragma unroll
   for (int m = 0; m < NE; ++m) {
     const int c = t + m * NT;
     const int y = c / RW, x = c - y * RW;
-    off[m] = c < PE ? (size_t)wrapi(j0 + y - 1, n) * n + wrapi(k0 + x - 1, n) : 0;
+    off[m] = c < PE ? (IT)wrapi(j0 + y - 1, n) * n + wrapi(k0 + x - 1, n) : 0;
     pos[m] = c < PE ? y * RS + x + 1 : -1;
   }
   double pre[NE];
   auto fetch = [&](int p) {
     const int ig = p < 0 ? p + n : (p >= n ? p - n : p);
-    const double* base = u + (size_t)ig * nn;
+    const double* base = u + (IT)ig * nn;
 #pragma unroll
     for (int m = 0; m < NE; ++m) pre[m] = pos[m] >= 0 ? base[off[m]] : 0.0;
   };
@@ -862,19 +864,19 @@ __global__ void __launch_bounds__(TJ * 32, 5) k_outer_residual_ff2(const FFC* __
   float acc = 0.f;
   // four ring slots: plane p in slot p & 3, so the slot written for plane i + 1
   // was last read two planes earlier and one barrier a plane suffices
-  const long long nh = (long long)n * (n >> 1);
-  const long long H = (long long)nn * (n >> 1);
-  long long o0, o1;  // the two cells of plane i0 in the level's layout
+  const IT nh = (IT)n * (n >> 1);
+  const IT H = (IT)nn * (n >> 1);
+  IT o0, o1;  // the two cells of plane i0 in the level's layout
   if constexpr (SPLIT) {
-    const long long idx = ((long long)i0 * n + jg) * (n >> 1) + (kg >> 1);
+    const IT idx = ((IT)i0 * n + jg) * (n >> 1) + (kg >> 1);
     const bool c0 = ((i0 + jg) & 1) != 0;  // colour of the even cell kg
     o0 = c0 ? H + idx : idx;
     o1 = c0 ? idx : H + idx;
   } else {
-    o0 = (long long)i0 * (long long)nn + (long long)jg * n + kg;
+    o0 = (IT)i0 * (IT)nn + (IT)jg * n + kg;
     o1 = o0 + 1;
   }
-  const float* rp = rho + (size_t)i0 * nn + (size_t)jg * n + kg;
+  const float* rp = rho + (IT)i0 * nn + (IT)jg * n + kg;
   fetch(i0 - 1);
   commit((i0 - 1) & 3);
   fetch(i0);
@@ -913,12 +915,12 @@ __global__ void __launch_bounds__(TJ * 32, 5) k_outer_residual_ff2(const FFC* __
     rp += nn;
     if constexpr (SPLIT) {
       // the next plane: one row block on, the colours of the two cells swapped
-      const long long a = o0;
+      const IT a = o0;
       o0 = o1 + nh;
       o1 = a + nh;
     } else {
-      o0 += (long long)nn;
-      o1 += (long long)nn;
+      o0 += (IT)nn;
+      o1 += (IT)nn;
     }
   }
   const double a = block_sum((double)acc);

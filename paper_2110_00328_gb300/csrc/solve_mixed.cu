@@ -159,20 +159,20 @@ __global__ void __launch_bounds__(128) k_prolong_correct32q(int nc, const float*
 
 // Second-colour prolongation on a split finest level with stored q, four fine
 // rows per lane (prolong_split2x2_second); grid as the restriction's.
-template <int QK, bool DD = false>
+template <int QK, bool DD = false, typename IT = long long>
 __global__ void __launch_bounds__(128) k_prolong32_split2x2(int nc, const float* __restrict__ eH,
                                                             const float* __restrict__ Re, const float* __restrict__ ub,
                                                             float* __restrict__ ef, unsigned long long* guard,
                                                             float* __restrict__ qf) {
   const int I = blockIdx.z * 4 + threadIdx.y;
   if (I >= nc) return;  // whole warps
-  prolong_split2x2_second<QK, DD>(nc, eH, Re, ub, ef, I, blockIdx.y, blockIdx.x * 32 + threadIdx.x, threadIdx.x,
-                                  guard, qf);
+  prolong_split2x2_second<QK, DD, IT>(nc, eH, Re, ub, ef, I, blockIdx.y, blockIdx.x * 32 + threadIdx.x,
+                                      threadIdx.x, guard, qf);
 }
 
 // Restriction after pre-smoothing on a split finest level with stored q, the
 // defect formed at the first colour only (restrict_split_zr); grid as above.
-template <int K>
+template <int K, typename IT = long long>
 __global__ void __launch_bounds__(128) k_restrict32_split_zr(LevelF f, int nf, const float* __restrict__ e,
                                                              const float* __restrict__ ub,
                                                              const float* __restrict__ S, const float* __restrict__ qf,
@@ -180,8 +180,8 @@ __global__ void __launch_bounds__(128) k_restrict32_split_zr(LevelF f, int nf, c
                                                              float* __restrict__ ubH, float* __restrict__ SH) {
   const int I = blockIdx.z * 4 + threadIdx.y;
   if (I >= (nf >> 1)) return;  // whole warps
-  restrict_split_zr<K>(f, nf, e, ub, S, qf, Re, eH, ubH, SH, I, blockIdx.y, blockIdx.x * 32 + threadIdx.x,
-                       threadIdx.x);
+  restrict_split_zr<K, IT>(f, nf, e, ub, S, qf, Re, eH, ubH, SH, I, blockIdx.y, blockIdx.x * 32 + threadIdx.x,
+                           threadIdx.x);
 }
 
 // FAS source, four cells per lane (n % 4 == 0, n >= 8): grid (ceil(n/128), n, n/4).
@@ -745,12 +745,10 @@ static int restrict_level(const MixedCtx& C, int l, cudaStream_t st, bool relaxe
   if (l == 0 && C.split) {
     const dim3 g((L.n / 4 + 31) / 32, H.n, (H.n + 3) / 4);
     if (C.qs && relaxed) {
-      if (C.m.kind == KFR1)
-        k_restrict32_split_zr<KFR1><<<g, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, L.S32, C.qs, H.Re, H.e, H.ub,
-                                                                H.S32);
-      else
-        k_restrict32_split_zr<KFR2><<<g, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, L.S32, C.qs, H.Re, H.e, H.ub,
-                                                                H.S32);
+      // 32-bit cell offsets where the level has at most 2^30 cells
+      auto kern = C.m.kind == KFR1 ? (L.n <= 1024 ? k_restrict32_split_zr<KFR1, int> : k_restrict32_split_zr<KFR1>)
+                                   : (L.n <= 1024 ? k_restrict32_split_zr<KFR2, int> : k_restrict32_split_zr<KFR2>);
+      kern<<<g, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, L.S32, C.qs, H.Re, H.e, H.ub, H.S32);
       note_launch(1);
     } else if (C.qs && C.m.kind == KFR1) {
       k_residual_restrict32q<KFR1, SplitLayout, true><<<g, dim3(32, 4), 0, st>>>(C.lf[l], L.n, L.e, L.ub, rho, L.S32,
@@ -800,10 +798,13 @@ static int prolong_level(const MixedCtx& C, int l, cudaStream_t st, bool both = 
     const bool second_only = !both && C.prm->nu2 >= 1;
     const dim3 g2((L.n / 4 + 31) / 32, H.n, (H.n + 3) / 4);
     const bool dd = second_only && fine_reads_d(C);  // H.e_alt holds eH - Re
+    const bool i32 = L.n <= 1024;  // 32-bit cell offsets
     if (C.qs && C.m.kind == KFR1 && dd)
-      k_prolong32_split2x2<KFR1, true><<<g2, dim3(32, 4), 0, st>>>(H.n, H.e_alt, H.Re, L.ub, L.e, C.guard, C.qs);
+      (i32 ? k_prolong32_split2x2<KFR1, true, int> : k_prolong32_split2x2<KFR1, true>)<<<g2, dim3(32, 4), 0, st>>>(
+          H.n, H.e_alt, H.Re, L.ub, L.e, C.guard, C.qs);
     else if (C.qs && C.m.kind == KFR2 && dd)
-      k_prolong32_split2x2<KFR2, true><<<g2, dim3(32, 4), 0, st>>>(H.n, H.e_alt, H.Re, L.ub, L.e, C.guard, C.qs);
+      (i32 ? k_prolong32_split2x2<KFR2, true, int> : k_prolong32_split2x2<KFR2, true>)<<<g2, dim3(32, 4), 0, st>>>(
+          H.n, H.e_alt, H.Re, L.ub, L.e, C.guard, C.qs);
     else if (C.qs && C.m.kind == KFR1 && second_only)
       k_prolong32_split2x2<KFR1><<<g2, dim3(32, 4), 0, st>>>(H.n, H.e, H.Re, L.ub, L.e, C.guard, C.qs);
     else if (C.qs && C.m.kind == KFR2 && second_only)
@@ -922,8 +923,10 @@ static int launch_outer_residual_ff(const MixedCtx& C, double* field, int* block
     // alignment allow (8-byte pair loads), else one on 8 x 32
     const bool pair = F.n % 64 == 0 && (uintptr_t)C.rho % 8 == 0;
     const long long tiles = (long long)(F.n / (pair ? 64 : kRTK)) * (F.n / kRTJ);
-    const void* kern = pair ? (C.split ? (const void*)k_outer_residual_ff2<K, kRTJ, true>
-                                       : (const void*)k_outer_residual_ff2<K, kRTJ, false>)
+    const bool i32 = F.n <= 1024;  // 32-bit cell offsets
+    auto pk_split = i32 ? k_outer_residual_ff2<K, kRTJ, true, int> : k_outer_residual_ff2<K, kRTJ, true>;
+    auto pk_nat = i32 ? k_outer_residual_ff2<K, kRTJ, false, int> : k_outer_residual_ff2<K, kRTJ, false>;
+    const void* kern = pair ? (C.split ? (const void*)pk_split : (const void*)pk_nat)
                             : (C.split ? (const void*)k_outer_residual_ff<K, kRTJ, kRTK, true>
                                        : (const void*)k_outer_residual_ff<K, kRTJ, kRTK>);
     const int chunk = march_chunk(F.n, tiles, kern, kRTJ * (pair ? 32 : kRTK));
@@ -952,10 +955,10 @@ static int launch_outer_residual_ff(const MixedCtx& C, double* field, int* block
       skip = flag;
     }
     if (pair && C.split)
-      k_outer_residual_ff2<K, kRTJ, true><<<grid, kRTJ * 32, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub, F.S32,
+      pk_split<<<grid, kRTJ * 32, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub, F.S32,
                                                                       ws->partials, skip, ze, zq);
     else if (pair)
-      k_outer_residual_ff2<K, kRTJ, false><<<grid, kRTJ * 32, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub, F.S32,
+      pk_nat<<<grid, kRTJ * 32, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub, F.S32,
                                                                        ws->partials, skip, nullptr, nullptr);
     else if (C.split)
       k_outer_residual_ff<K, kRTJ, kRTK, true><<<grid, kRTJ * kRTK, 0, st>>>(ffc, F.n, chunk, field, C.rho, F.ub,
