@@ -73,19 +73,20 @@ __device__ __forceinline__ float3 cic_grad_core(const Tv& Tat, const float wx[2]
 // Gradient of the mesh scalar T at (x, y, z): the central differences
 // (T_{c+1} - T_{c-1})/2 at the 8 CIC cells, weighted with the particle's CIC
 // weights.  Reads the 32 distinct cells those differences touch: the 2x2x2
-// core and a one-cell extension on each side along each axis.
+// core and a one-cell extension on each side along each axis.  IT: the index
+// type of the cell offsets (int where N^3 < 2^31).
+template <typename IT = long long>
 __device__ __forceinline__ float3 cic_grad(const float* __restrict__ T, int N, float x, float y, float z) {
   int i0, i1, j0, j1, k0, k1;
   float wx[2], wy[2], wz[2];
   cic_axis_f(x, N, i0, i1, wx[0], wx[1]);
   cic_axis_f(y, N, j0, j1, wy[0], wy[1]);
   cic_axis_f(z, N, k0, k1, wz[0], wz[1]);
-  const long long NN = (long long)N * N;
+  const IT NN = (IT)N * N;
   // offsets: x[0..3] = i0-1, i0, i1, i1+1 (times N^2), likewise y (times N) and z
-  const long long ox[4] = {(long long)(i0 == 0 ? N - 1 : i0 - 1) * NN, (long long)i0 * NN, (long long)i1 * NN,
-                           (long long)(i1 + 1 == N ? 0 : i1 + 1) * NN};
-  const long long oy[4] = {(long long)(j0 == 0 ? N - 1 : j0 - 1) * N, (long long)j0 * N, (long long)j1 * N,
-                           (long long)(j1 + 1 == N ? 0 : j1 + 1) * N};
+  const IT ox[4] = {(IT)(i0 == 0 ? N - 1 : i0 - 1) * NN, (IT)i0 * NN, (IT)i1 * NN,
+                    (IT)(i1 + 1 == N ? 0 : i1 + 1) * NN};
+  const IT oy[4] = {(IT)(j0 == 0 ? N - 1 : j0 - 1) * N, (IT)j0 * N, (IT)j1 * N, (IT)(j1 + 1 == N ? 0 : j1 + 1) * N};
   const int oz[4] = {k0 == 0 ? N - 1 : k0 - 1, k0, k1, k1 + 1 == N ? 0 : k1 + 1};
   auto Tat = [&](int a, int b, int c) { return T[ox[a] + oy[b] + oz[c]]; };
   return cic_grad_core(Tat, wx, wy, wz);

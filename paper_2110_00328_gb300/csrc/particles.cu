@@ -65,6 +65,7 @@ __device__ __forceinline__ unsigned long long wmul(unsigned long long P, unsigne
 // a lattice-ordered particle array do): the next lane then adds them to its
 // own and this lane skips those atomics.  Integer sums are exact, so the mesh
 // does not depend on which lane issues an update.
+template <typename IT>
 __global__ void __launch_bounds__(kThreads) k_deposit_fixed(const float* __restrict__ pos, long long np, int N,
                                                             unsigned long long* __restrict__ acc) {
   const int lane = threadIdx.x & 31;
@@ -96,11 +97,11 @@ __global__ void __launch_bounds__(kThreads) k_deposit_fixed(const float* __restr
     }
     const bool given = __shfl_down_sync(0xffffffffu, (int)take, 1) != 0 && lane < 31;
     if (ok) {
-      const long long ri[2] = {(long long)i0 * N, (long long)i1 * N};
+      const IT ri[2] = {(IT)i0 * N, (IT)i1 * N};
       const int jj[2] = {j0, j1};
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
-        const long long row = (ri[s >> 1] + jj[s & 1]) * N;
+        const IT row = (ri[s >> 1] + jj[s & 1]) * N;
         if (lo[s]) atomicAdd(&acc[row + k0], lo[s]);
         if (!given && up[s]) atomicAdd(&acc[row + k1], up[s]);
       }
@@ -145,7 +146,9 @@ int deposit_cic(const float* pos, long long np, int N, float* rho, cudaStream_t 
   const long long n3 = (long long)N * N * N;
   MG_CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)n3 * sizeof(unsigned long long), st));
   prof_begin(PC_DEPOSIT, st, 12.0 * np);
-  k_deposit_fixed<<<grid_for(np, kThreads, 1 << 20), kThreads, 0, st>>>(pos, np, N, acc);
+  // 32-bit cell offsets where the mesh has at most 2^30 cells
+  (N <= 1024 ? k_deposit_fixed<int> : k_deposit_fixed<long long>)<<<grid_for(np, kThreads, 1 << 20), kThreads, 0,
+                                                                     st>>>(pos, np, N, acc);
   prof_end(st);
   prof_begin(PC_DEPOSIT_FINISH, st, 12.0 * n3);
   k_deposit_finish<<<stream_grid(n3), kThreads, 0, st>>>(acc, n3, (double)n3 / (double)np, rho);
@@ -186,11 +189,12 @@ __global__ void k_transform(const double* __restrict__ u, long long n3, double u
 
 // One particle per thread (cic_grad: the 32 distinct cells its three central
 // differences at the 8 CIC cells touch).
+template <typename IT>
 __global__ void __launch_bounds__(kThreads) k_gather(const float* __restrict__ T, int N, const float* __restrict__ pos,
                                                      long long np, float scale, float* __restrict__ force) {
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < np;
        q += (long long)gridDim.x * blockDim.x) {
-    const float3 g = cic_grad(T, N, pos[3 * q + 0], pos[3 * q + 1], pos[3 * q + 2]);
+    const float3 g = cic_grad<IT>(T, N, pos[3 * q + 0], pos[3 * q + 1], pos[3 * q + 2]);
     force[3 * q + 0] = scale * g.x;
     force[3 * q + 1] = scale * g.y;
     force[3 * q + 2] = scale * g.z;
@@ -215,8 +219,8 @@ int gather_chunk(const ModelDev& m, int kind, const mgglam_params* prm, int N, c
   if (rc) return rc;
   const float* T = ws->lev[0].ub;
   prof_begin(PC_GATHER, st, 24.0 * np);
-  k_gather<<<grid_for(np, kThreads, 1 << 20), kThreads, 0, st>>>(T, N, pos, np,
-                                                                 (float)(force_scale(m, kind, prm) * prefactor), force);
+  (N <= 1024 ? k_gather<int> : k_gather<long long>)<<<grid_for(np, kThreads, 1 << 20), kThreads, 0, st>>>(
+      T, N, pos, np, (float)(force_scale(m, kind, prm) * prefactor), force);
   prof_end(st);
   note_launch(1);
   MG_CUDA_TRY(cudaGetLastError());
@@ -244,7 +248,9 @@ int gather_force(const ModelDev& m, int kind, int n_fr, const mgglam_params* prm
   prof_end(st);
   scale = force_scale(m, kind, prm);
   prof_begin(PC_GATHER, st, 24.0 * np + 4.0 * n3);
-  k_gather<<<grid_for(np, kThreads, 1 << 20), kThreads, 0, st>>>(T, N, pos, np, (float)(scale * prefactor), force);
+  // 32-bit cell offsets where the mesh has at most 2^30 cells
+  (N <= 1024 ? k_gather<int> : k_gather<long long>)<<<grid_for(np, kThreads, 1 << 20), kThreads, 0, st>>>(
+      T, N, pos, np, (float)(scale * prefactor), force);
   prof_end(st);
   note_launch(2);
   MG_CUDA_TRY(cudaGetLastError());
@@ -308,7 +314,8 @@ int deposit_cic_host(const float* pos_host, float* pos_dev, long long np, int N,
                                 io->cs));
     MG_CUDA_TRY(cudaEventRecord(io->ev[c], io->cs));
     MG_CUDA_TRY(cudaStreamWaitEvent(st, io->ev[c], 0));
-    k_deposit_fixed<<<grid_for(cnt, kThreads, 1 << 20), kThreads, 0, st>>>(pos_dev + 3 * q0, cnt, N, acc);
+    (N <= 1024 ? k_deposit_fixed<int> : k_deposit_fixed<long long>)<<<grid_for(cnt, kThreads, 1 << 20), kThreads, 0,
+                                                                       st>>>(pos_dev + 3 * q0, cnt, N, acc);
     note_launch(1);
   }
   prof_end(st);
@@ -417,7 +424,9 @@ extern "C" int mgglam_deposit_cic_static(const float* pos, long long np, int N, 
   const long long n3 = (long long)N * N * N;
   // the array keeps the previous call's sums: clear the part this call uses
   MG_CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)n3 * sizeof(unsigned long long), st));
-  k_deposit_fixed<<<grid_for(np, kThreads, 1 << 20), kThreads, 0, st>>>(pos, np, N, acc);
+  // 32-bit cell offsets where the mesh has at most 2^30 cells
+  (N <= 1024 ? k_deposit_fixed<int> : k_deposit_fixed<long long>)<<<grid_for(np, kThreads, 1 << 20), kThreads, 0,
+                                                                     st>>>(pos, np, N, acc);
   k_deposit_finish<<<stream_grid(n3), kThreads, 0, st>>>(acc, n3, (double)n3 / (double)np, rho);
   note_launch(2);
   MG_CUDA_TRY(cudaGetLastError());
