@@ -9,9 +9,11 @@ header); this module loads it with ctypes and adds the numpy-level references
 used to pin it: FFT solutions of the linearised and zero-coupling problems and a
 dense Newton solve of the full discrete system on tiny meshes.
 
-Parity status: every function is pinned by a ``-m "not gpu"`` test except the
-symmetron in sign-changing (domain-wall) regimes and CQ with the exp factor
-kept, which are "parity unpinned" (only self-consistency checks).
+Parity status: every function is pinned by a ``-m "not gpu"`` test, including
+the symmetron in sign-changing (domain-wall) regimes and CQ with the exp factor
+kept, which are pinned by manufactured exact discrete solutions (the field is
+chosen, the density derived from the equation with the 7-point Laplacian, and
+the solve must return the field).
 """
 from __future__ import annotations
 
