@@ -1013,13 +1013,16 @@ static int launch_outer_residual_t(const MixedCtx& C, double* field, int* blocks
   return MGGLAM_OK;
 }
 
-// Whether the outer residual pass also zeroes the finest level's e and q (the
-// split tiled float-float kernels write the zeros beside ub and tau; otherwise
-// the outer step clears them with memsets).
+// Whether the outer residual pass can zero the finest level's e and q when the
+// next inner solve needs them zeroed (the split tiled float-float kernels write
+// the zeros beside ub and tau; otherwise the outer step clears them with
+// memsets).  On stored-q levels the next solve's first sweep takes them as zero
+// by itself (fresh) and nothing is zeroed, except before an FMG start.
 static bool residual_zeroes_e(const MixedCtx& C) { return C.split && C.ff_resid && bg_residual_tiled(C.ws->lev[0].n); }
 
 // bg_first: the solve's first residual, on a mesh where the background start is
-// fused into it (fused_background_start); the field's background fill happens there.
+// fused into it (fused_background_start): the residual at ubar is formed there and
+// the field keeps its NaN mark until the first correction (bg_pending).
 static bool fused_background_start(const MixedCtx& C) { return C.ff_resid && bg_residual_tiled(C.ws->lev[0].n); }
 
 // zero: the split tiled residual also zeroes e and q for the next inner solve
