@@ -218,8 +218,9 @@ int mgglam_deposit_cic_static(const float* pos, long long np, int N, float* rho,
  *   stats  host, may be NULL.
  * Returns MGGLAM_OK when converged, MGGLAM_ERR_NOT_CONVERGED if max_cycles was
  * reached first (field holds the last iterate), MGGLAM_ERR_NONFINITE if the
- * residual became NaN/Inf, or an argument/CUDA/allocation error.  Synchronises
- * 'stream' once per convergence check.
+ * residual became NaN/Inf, or an argument/CUDA/allocation error (after which
+ * the field's contents are unspecified).  Synchronises 'stream' once per
+ * convergence check.
  */
 int mgglam_solve_scalar(const mgglam_params* prm, double a, const float* rho, int N,
                         double* field, double tol, mgglam_stats* stats, void* stream);
